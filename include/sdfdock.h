@@ -1,0 +1,209 @@
+/*
+ * sdfdock.h - C ABI of the skeletal-density (SDF) shape-complementarity library.
+ *
+ * The library scores rigid poses of a moving solid S2 against a fixed solid S1
+ * (Behandish & Ilies, "Shape Complementarity Analysis for Objects of Arbitrary
+ * Shape"): each solid's skeletal density function rho (Section 4, Eq. 13 with
+ * the kernel of Eq. 15) is sampled at query points, the samples carry Gaussians,
+ * and the score f(tau) = integral of rho1(p) rho2(tau^-1 p) dv (Eq. 1 / Eq. 8)
+ * is searched over rotations x translations with one FFT per rotation
+ * (Section 5), using a nonequispaced FFT for the scattered samples.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All functions return an int: SD_OK (0) or a negative SD_ERR_* code.  The
+ *   message of the last failure is in sd_last_error(ctx).  No call aborts the
+ *   process or throws across the ABI.
+ * - "real" means float for a context created with precision SD_F32 and double
+ *   for SD_F64.  Complex numbers are (re, im) pairs of real.
+ * - Points are stored as 4 reals (x, y, z, unused); 2D contexts ignore z.
+ * - Pointers marked "device" are CUDA device pointers on the context's device;
+ *   "host" pointers are ordinary memory.  The caller keeps ownership of every
+ *   buffer it passes.  Calls are asynchronous on `stream` (a cudaStream_t, NULL
+ *   for the legacy default stream) unless stated otherwise.
+ * - Quaternions are (w, x, y, z), Hamilton product, acting as the active
+ *   rotation p -> q p q*; they need not be normalised.  A pose (R, t) moves S2 as
+ *   x -> R x + t about S2's frame origin.
+ * - Translations of the score grid are t_m = (i - N/2) * h, h = L / N, for
+ *   i in [0, N) per axis; the flat index of a translation is
+ *   (iz * N + iy) * N + ix (3D) or iy * N + ix (2D).
+ */
+#ifndef SDFDOCK_H
+#define SDFDOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SD_OK 0
+#define SD_ERR_ARG (-1)           /* invalid argument or unsupported size           */
+#define SD_ERR_OOM (-2)           /* device allocation failed                       */
+#define SD_ERR_CUDA (-3)          /* a CUDA runtime call or kernel launch failed    */
+#define SD_ERR_TIMEOUT (-4)       /* reserved: a bounded device wait gave up        */
+#define SD_ERR_UNIMPLEMENTED (-5) /* a valid request this build does not support    */
+#define SD_ERR_NONFINITE (-6)     /* a result was NaN or infinite                   */
+
+#define SD_F32 0
+#define SD_F64 1
+
+typedef struct sd_ctx sd_ctx;
+typedef struct sd_shape sd_shape;
+
+/* Parameters of a context.  sd_default_params() fills the paper's validation
+ * values (Section 6): lambda1 = 1, lambda2 = 3, sigma_t = 0.5, eps = 1.5. */
+typedef struct sd_params {
+    int dim;          /* 2 or 3                                                        */
+    int precision;    /* SD_F32 or SD_F64: the arithmetic of every kernel              */
+    double lambda1;   /* Eq. 16c: weight outside the solid (+lambda1)                  */
+    double lambda2;   /* Eq. 16c: weight inside the solid (-lambda2)                   */
+    double sigma_t;   /* Eq. 15: thickness factor of the medial Gaussian               */
+    double eps;       /* Eq. 17t: truncation; INFINITY keeps every boundary sample     */
+    double sigma_g;   /* width of the Gaussian carried by each SDF sample              */
+    int w;            /* spreading width in grid cells of the oversampled grid (2..16) */
+    int alpha;        /* oversampling factor of the nonequispaced FFT (only 2)         */
+    double beta;      /* shape of the exponential-of-semicircle kernel; <= 0: 2.30*w   */
+} sd_params;
+
+/* Translation grid: N points per axis on a periodic box of side L. */
+typedef struct sd_grid {
+    int N;            /* one of 8, 16, 24, 32, 48, 64, 96, 128, 192, 256 */
+    double L;
+} sd_grid;
+
+/* Per-rotation best translation (16 bytes). */
+typedef struct sd_cand {
+    double score;     /* Re f_N at the best translation of this rotation */
+    int32_t rot;      /* rotation index in the call's quaternion list    */
+    int32_t idx;      /* flat translation index                          */
+} sd_cand;
+
+/* A ranked pose. */
+typedef struct sd_pose {
+    double score;         /* Re f_N from the FFT search                          */
+    double score_fp64;    /* Re f_c from FP64 direct pair sums (0 if not asked)  */
+    double score_fp64_im; /* Im f_c, a diagnostic                                */
+    int32_t rot;
+    int32_t idx;
+    double t[3];          /* translation of the pose (t[2] = 0 in 2D)            */
+} sd_pose;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Fill *p with defaults for the given dimension and precision. */
+int sd_default_params(sd_params* p, int dim, int precision);
+
+/* Create a context on CUDA device `device`.  Validates *p (SD_ERR_ARG). */
+int sd_create(sd_ctx** out, int device, const sd_params* p);
+
+/* Free a context, its workspace and its cached plans.  Shapes made with it
+ * must be freed first; NULL is accepted. */
+int sd_destroy(sd_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context.  A NULL ctx returns the message of the last failed
+ * sd_create. */
+const char* sd_last_error(const sd_ctx* ctx);
+
+/* Set a tuning option: "batch" (rotations per batch, 0 = automatic),
+ * "graph" (1: replay the batched launch sequence from a captured CUDA graph),
+ * "plain" (1: one rotation at a time, unfused passes, no graph). */
+int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
+
+/* ---- shapes: the sampled SDF (Section 4, Eq. 10A-17t) ------------------- */
+
+/* Build a shape's sampled SDF from oriented boundary samples.
+ *   bnd   device, n_b x 4 real: boundary sample positions q_j
+ *   nrm   device, n_b x 4 real: unit outward normals n_j
+ *   area  device, n_b real: boundary measure a_j carried by each sample
+ *   qry   device, m x 4 real: query points p_i
+ *   vol   device, m real: cell volume v_i of each query point
+ *   pmc_override  device, m int8 (+1 outside, -1 inside) or NULL to use the
+ *         winding-number membership of the samples
+ *   out   receives a new shape holding p_i and c_i = rho(p_i) v_i
+ *   rho_out  device, m x 2 real, or NULL: receives rho(p_i)
+ * rho follows Eq. 13 with Eq. 15/16c and the truncation of Eq. 17t, xi from
+ * Eq. 10A (nearest sample, ties to the lowest index), zeta = xi + i eta (Eq. 11),
+ * cos(theta) from Eq. 12a; in 2D each element is weighted by its planar angle
+ * over 2 pi.  Synchronises `stream` before returning (the shape's bounding
+ * radius is read back). */
+int sd_sdf_build(sd_ctx* ctx, const void* bnd, const void* nrm, const void* area, int64_t n_b,
+                 const void* qry, const void* vol, int64_t m, const int8_t* pmc_override,
+                 sd_shape** out, void* rho_out, void* stream);
+
+/* Make a shape directly from weighted samples (p_i device m x 4 real,
+ * c_i device m x 2 real).  Copies them.  Synchronises `stream`. */
+int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m,
+                          sd_shape** out, void* stream);
+
+/* Number of samples and the largest |p_i| of a shape. */
+int sd_shape_info(const sd_shape* s, int64_t* m, double* radius);
+
+/* Free a shape and its cached spectra; NULL is accepted. */
+int sd_shape_free(sd_shape* s);
+
+/* ---- search over rotations x translations (Section 5) ------------------ */
+
+/* For each rotation r, the best translation of Re f_N(R_r, t) over the grid.
+ *   quats     device, n_r x 4 double
+ *   k_r       candidates per rotation; only 1 is supported
+ *   cand_out  device, n_r x k_r sd_cand, ordered by rotation
+ * f_N is the band-limited periodic score: the pair sum of c1_i c2_j times the
+ * Fourier series of the Gaussian of width sigma_g*sqrt(2) on the box, modes
+ * |kappa_d| < N/2.  Computed per rotation as: rotate S2's samples, spread them
+ * onto the oversampled grid, forward FFT (type-1 nonuniform FFT), multiply by
+ * the fixed shape's table, inverse FFT, argmax (ties to the lowest index). */
+int sd_score_rotations(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving,
+                       const double* quats, int64_t n_r, const sd_grid* g, int k_r,
+                       sd_cand* cand_out, void* stream);
+
+/* The complex score maps f_N for each rotation, for inspection and testing.
+ *   map_out   device, n_r x N^dim x 2 real, flat translation order. */
+int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving,
+                  const double* quats, int64_t n_r, const sd_grid* g, void* map_out,
+                  void* stream);
+
+/* Global top-k over per-rotation candidates, ordered by score descending,
+ * then rotation ascending, then translation index ascending; optionally each
+ * pose is re-scored in FP64 by direct pair sums of the continuous score
+ * f_c = sum_ij c1_i c2_j G_{sigma_g sqrt 2}(R p2_j + t - p1_i) (pairs farther
+ * than 8 sigma_g sqrt 2 are skipped).
+ *   cand   device, n_cand sd_cand (1 <= n_cand <= 2^22)
+ *   quats  device, the quaternion list the candidates index
+ *   out    host, k sd_pose
+ * Synchronises `stream`. */
+int sd_top_k_poses(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int rescore_fp64,
+                   const sd_shape* fixed, const sd_shape* moving, const double* quats,
+                   const sd_grid* g, sd_pose* out, void* stream);
+
+/* ---- score and gradient at arbitrary poses (Section 6, gradient search) -- */
+
+/* Re f_N and its gradient at P poses, by a type-2 gather of the band-limited
+ * field Phi(x) = sum_i c1_i K_N(x - p1_i) and its gradient at R p2_j + t.
+ *   quats  device, P x 4 real (raw quaternions)
+ *   trans  device, P x 3 real (2D: z ignored)
+ *   score  device, P real
+ *   dq     device, P x 4 real: d score / d q through R(q/|q|) (orthogonal to q)
+ *   dt     device, P x 3 real: d score / d t (2D: dt[2] = 0) */
+int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g,
+                  const void* quats, const void* trans, int64_t P, void* score, void* dq,
+                  void* dt, void* stream);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+
+/* Runs, on the host in FP64, the same sequence of mixed-radix Stockham stages
+ * that the device line FFTs execute, for one line of `len` points (a supported
+ * length: 8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512).  Forward
+ * (inverse = 0) is X_k = sum_j x_j exp(-2 pi i jk/len); inverse uses +i and is
+ * unnormalised.  in, out: host, len x 2 double.  Needs no GPU. */
+int sd_host_line_fft(int len, int inverse, const double* in, double* out);
+
+/* Library version string (static storage). */
+const char* sd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFDOCK_H */

@@ -1,0 +1,1022 @@
+// C ABI of the SDF complementarity library: contexts, shapes, plans and the
+// per-call pipelines.  See include/sdfdock.h for the contract of every entry.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sdfdock.h"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+using namespace sd;
+
+// ---------------------------------------------------------------------------
+// context and shapes
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Prep {  // fixed-shape tables for one grid
+    int N = 0;
+    double L = 0;
+    void* B1 = nullptr;  // N^d: spread + forward FFT of the fixed samples (deconvolution pending)
+    void* W = nullptr;   // N^d: the product table of the search
+    void* G = nullptr;   // n^d x 4: Phi and its gradient on the oversampled grid
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct sd_ctx {
+    int device = 0;
+    sd_params p{};
+    std::string err;
+    int64_t opt_batch = 0;
+    int opt_graph = 0;
+    int opt_plain = 0;
+    DevBuf ws[6];
+    std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
+    std::map<std::tuple<int, int, int, double>, double*> deconv;
+    double* gl_x = nullptr;
+    double* gl_w = nullptr;
+    int nq = 0;
+    std::map<std::string, GraphEntry> graphs;
+    std::map<std::string, int> seen;
+};
+
+struct sd_shape {
+    sd_ctx* ctx = nullptr;
+    int64_t m = 0;
+    void* pos = nullptr;  // m x 4 real
+    void* c = nullptr;    // m x 2 real
+    double radius = 0.0;
+    std::vector<Prep> preps;
+};
+
+static std::string g_create_err;
+
+static int fail(sd_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CK(ctx, x)                                                                            \
+    do {                                                                                      \
+        cudaError_t e_ = (x);                                                                 \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SD_ERR_OOM : SD_ERR_CUDA,      \
+                        "%s failed: %s", #x, cudaGetErrorString(e_));                         \
+    } while (0)
+
+#define CKI(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != SD_OK) return r_; \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static size_t real_size(const sd_ctx* ctx) { return ctx->p.precision == SD_F64 ? 8 : 4; }
+
+static int ws_get(sd_ctx* ctx, int slot, size_t bytes, void** out) {
+    DevBuf& b = ctx->ws[slot];
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        size_t want = bytes + bytes / 8 + 256;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SD_ERR_OOM, "workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return SD_OK;
+}
+
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    // roots of P_n by Newton's method; weights 2 / ((1 - x^2) P_n'(x)^2)
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            const double p2 = p1;
+            p1 = p0;
+            p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+        }
+        dp = n * (z * p0 - p1) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static int get_twiddles(sd_ctx* ctx, int len, void** out, cudaStream_t st) {
+    auto key = std::make_pair(len, ctx->p.precision);
+    auto it = ctx->twiddles.find(key);
+    if (it != ctx->twiddles.end()) {
+        *out = it->second;
+        return SD_OK;
+    }
+    void* p = nullptr;
+    CK(ctx, cudaMalloc(&p, (size_t)len * 2 * real_size(ctx)));
+    if (ctx->p.precision == SD_F64) CK(ctx, launch_twiddles<double>((double2*)p, len, st));
+    else CK(ctx, launch_twiddles<float>((float2*)p, len, st));
+    ctx->twiddles[key] = p;
+    *out = p;
+    return SD_OK;
+}
+
+static int get_deconv(sd_ctx* ctx, int N, int n, double** out, cudaStream_t st) {
+    auto key = std::make_tuple(N, n, ctx->p.w, ctx->p.beta);
+    auto it = ctx->deconv.find(key);
+    if (it != ctx->deconv.end()) {
+        *out = it->second;
+        return SD_OK;
+    }
+    if (!ctx->gl_x) {
+        std::vector<double> x, w;
+        const int nq = 96;
+        gauss_legendre(nq, x, w);
+        for (int i = 0; i < nq; ++i) {  // map [-1, 1] -> [0, pi/2]
+            x[i] = (x[i] + 1.0) * (M_PI / 4.0);
+            w[i] *= M_PI / 4.0;
+        }
+        CK(ctx, cudaMalloc(&ctx->gl_x, nq * sizeof(double)));
+        CK(ctx, cudaMalloc(&ctx->gl_w, nq * sizeof(double)));
+        CK(ctx, cudaMemcpy(ctx->gl_x, x.data(), nq * sizeof(double), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(ctx->gl_w, w.data(), nq * sizeof(double), cudaMemcpyHostToDevice));
+        ctx->nq = nq;
+    }
+    double* D = nullptr;
+    CK(ctx, cudaMalloc(&D, N * sizeof(double)));
+    CK(ctx, launch_deconv(D, N, n, ctx->p.w, ctx->p.beta, ctx->gl_x, ctx->gl_w, ctx->nq, st));
+    ctx->deconv[key] = D;
+    *out = D;
+    return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// geometry of one search: grid sizes and the moving shape's sub-box
+// ---------------------------------------------------------------------------
+
+struct Geo {
+    int dim, N, n;
+    double L, inv_h;
+    int s, s_h;
+    int64_t cells_box;  // s^d
+};
+
+static bool grid_ok(int N) {
+    switch (N) {
+        case 8: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192: case 256: return true;
+        default: return false;
+    }
+}
+
+static int make_geo(sd_ctx* ctx, const sd_grid* g, double radius, Geo* out) {
+    if (!g) return fail(ctx, SD_ERR_ARG, "grid is NULL");
+    if (!grid_ok(g->N)) return fail(ctx, SD_ERR_ARG, "unsupported grid size N=%d", g->N);
+    if (!(g->L > 0.0) || !isfinite(g->L)) return fail(ctx, SD_ERR_ARG, "box side L must be positive and finite");
+    Geo G;
+    G.dim = ctx->p.dim;
+    G.N = g->N;
+    G.n = ctx->p.alpha * g->N;
+    G.L = g->L;
+    G.inv_h = (double)G.n / g->L;
+    const double reach = radius * G.inv_h + 0.5 * ctx->p.w;
+    if (reach > 1.5 * G.n) return fail(ctx, SD_ERR_ARG, "shape radius %.6g exceeds the periodic box", radius);
+    int s_h = (int)floor(reach) + 2;
+    if (2 * s_h >= G.n) s_h = G.n / 2;
+    G.s_h = s_h;
+    G.s = 2 * s_h;
+    G.cells_box = (G.dim == 2) ? (int64_t)G.s * G.s : (int64_t)G.s * G.s * G.s;
+    *out = G;
+    return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// forward transform of a spread sub-box: box -> N^d modes (kappa mod N order)
+// ---------------------------------------------------------------------------
+//
+// 3D: box (s,s,s) -x-> (s,s,N) -y-> (s,N,N) -z-> (N,N,N)   (last step FWD or FUSED)
+// 2D: box (s,s)   -x-> (s,N)   -y-> (N,N)
+
+template <typename T>
+struct Tw {
+    const cplx<T>* n;
+    const cplx<T>* N;
+};
+
+template <typename T>
+static int get_tw(sd_ctx* ctx, const Geo& G, Tw<T>* tw, cudaStream_t st) {
+    void *a, *b;
+    CKI(get_twiddles(ctx, G.n, &a, st));
+    CKI(get_twiddles(ctx, G.N, &b, st));
+    tw->n = (const cplx<T>*)a;
+    tw->N = (const cplx<T>*)b;
+    return SD_OK;
+}
+
+// x pass: rows of the box
+template <typename T>
+static cudaError_t pass_x_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
+                              int64_t out_rs, int batch, cudaStream_t st) {
+    RowArgs<T> r{};
+    r.in = in;
+    r.out = out;
+    r.in_rot_stride = in_rs;
+    r.out_rot_stride = out_rs;
+    r.nrows = (G.dim == 2) ? G.s : G.s * G.s;
+    r.in_row_stride = G.s;
+    r.out_row_stride = G.N;
+    r.len_in = G.s;
+    r.s_h = G.s_h;
+    r.N = G.N;
+    r.n = G.n;
+    r.tw = tw.n;
+    return launch_rows<T>(ROW_FWD, r, batch, nullptr, st);
+}
+
+// y pass (3D): (s,s,N) -> (s,N,N)
+template <typename T>
+static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
+                              int64_t out_rs, int batch, cudaStream_t st) {
+    ColArgs<T> c{};
+    c.in = in;
+    c.out = out;
+    c.in_rot_stride = in_rs;
+    c.out_rot_stride = out_rs;
+    c.ncols = G.N;
+    c.nouter = G.s;
+    c.in_outer_stride = (int64_t)G.s * G.N;
+    c.out_outer_stride = (int64_t)G.N * G.N;
+    c.len_in = G.s;
+    c.s_h = G.s_h;
+    c.N = G.N;
+    c.n = G.n;
+    c.twF = tw.n;
+    c.twI = tw.N;
+    return launch_cols<T>(COL_FWD, c, batch, st);
+}
+
+// last axis (z in 3D, y in 2D): FWD (modes) or FUSED (product with W, inverse)
+template <typename T>
+static cudaError_t pass_last(int mode, const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs,
+                             cplx<T>* out, int64_t out_rs, const cplx<T>* W, int batch, cudaStream_t st) {
+    ColArgs<T> c{};
+    c.in = in;
+    c.out = out;
+    c.in_rot_stride = in_rs;
+    c.out_rot_stride = out_rs;
+    c.ncols = (G.dim == 2) ? G.N : G.N * G.N;
+    c.nouter = 1;
+    c.in_outer_stride = 0;
+    c.out_outer_stride = 0;
+    c.len_in = G.s;
+    c.s_h = G.s_h;
+    c.N = G.N;
+    c.n = G.n;
+    c.twF = tw.n;
+    c.twI = tw.N;
+    c.W = W;
+    return launch_cols<T>(mode, c, batch, st);
+}
+
+// inverse y (3D): (N,N,N) in place
+template <typename T>
+static cudaError_t pass_y_inv(const Geo& G, const Tw<T>& tw, cplx<T>* buf, int64_t rs, int batch, cudaStream_t st) {
+    ColArgs<T> c{};
+    c.in = buf;
+    c.out = buf;
+    c.in_rot_stride = rs;
+    c.out_rot_stride = rs;
+    c.ncols = G.N;
+    c.nouter = G.N;
+    c.in_outer_stride = (int64_t)G.N * G.N;
+    c.out_outer_stride = (int64_t)G.N * G.N;
+    c.len_in = G.N;
+    c.s_h = 0;
+    c.N = G.N;
+    c.n = G.n;
+    c.twF = tw.N;
+    c.twI = tw.N;
+    return launch_cols<T>(COL_INV, c, batch, st);
+}
+
+// ---------------------------------------------------------------------------
+// fixed-shape preparation for a grid
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, cudaStream_t st) {
+    for (auto& p : fx->preps)
+        if (p.N == g->N && p.L == g->L) {
+            *out = &p;
+            return SD_OK;
+        }
+    using C = cplx<T>;
+    Geo G;
+    CKI(make_geo(ctx, g, fx->radius, &G));
+    Tw<T> tw;
+    CKI(get_tw<T>(ctx, G, &tw, st));
+    double* D = nullptr;
+    CKI(get_deconv(ctx, G.N, G.n, &D, st));
+    const int64_t Nd = (G.dim == 2) ? (int64_t)G.N * G.N : (int64_t)G.N * G.N * G.N;
+    const int64_t sz0 = G.cells_box;
+    const int64_t sz1 = (G.dim == 2) ? (int64_t)G.s * G.N : (int64_t)G.s * G.s * G.N;
+    const int64_t sz2 = (G.dim == 2) ? 0 : (int64_t)G.s * G.N * G.N;
+    C *b0 = nullptr, *b1 = nullptr, *b2 = nullptr, *B1 = nullptr, *W = nullptr;
+    CK(ctx, cudaMalloc(&b0, sz0 * sizeof(C)));
+    CK(ctx, cudaMalloc(&b1, sz1 * sizeof(C)));
+    if (sz2) CK(ctx, cudaMalloc(&b2, sz2 * sizeof(C)));
+    CK(ctx, cudaMalloc(&B1, Nd * sizeof(C)));
+    CK(ctx, cudaMalloc(&W, Nd * sizeof(C)));
+    CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
+    SpreadArgs<T> sa{};
+    sa.pos = (const vec4<T>*)fx->pos;
+    sa.c = (const C*)fx->c;
+    sa.m = fx->m;
+    sa.quats = nullptr;
+    sa.rot0 = 0;
+    sa.sign = T(1);
+    sa.inv_h = (T)G.inv_h;
+    sa.beta = (T)ctx->p.beta;
+    sa.w = ctx->p.w;
+    sa.s = G.s;
+    sa.s_h = G.s_h;
+    sa.out = b0;
+    sa.out_rot_stride = 0;
+    CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
+    CK(ctx, pass_x_fwd<T>(G, tw, b0, 0, b1, 0, 1, st));
+    if (G.dim == 3) {
+        CK(ctx, pass_y_fwd<T>(G, tw, b1, 0, b2, 0, 1, st));
+        CK(ctx, pass_last<T>(COL_FWD, G, tw, b2, 0, B1, 0, nullptr, 1, st));
+    } else {
+        CK(ctx, pass_last<T>(COL_FWD, G, tw, b1, 0, B1, 0, nullptr, 1, st));
+    }
+    CK(ctx, launch_wtable<T>(B1, D, G.N, G.dim, G.L, ctx->p.sigma_g, 1, -1, W, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    cudaFree(b0);
+    cudaFree(b1);
+    if (b2) cudaFree(b2);
+    Prep p;
+    p.N = g->N;
+    p.L = g->L;
+    p.B1 = B1;
+    p.W = W;
+    fx->preps.push_back(p);
+    *out = &fx->preps.back();
+    return SD_OK;
+}
+
+// Phi and its gradient on the oversampled grid (type-2 tables)
+template <typename T>
+static int prep_fields(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, cudaStream_t st) {
+    Prep* p = nullptr;
+    CKI(prep_fixed<T>(ctx, fx, g, &p, st));
+    if (p->G) {
+        *out = p;
+        return SD_OK;
+    }
+    using C = cplx<T>;
+    Geo G;
+    CKI(make_geo(ctx, g, fx->radius, &G));
+    Tw<T> tw;
+    CKI(get_tw<T>(ctx, G, &tw, st));
+    double* D = nullptr;
+    CKI(get_deconv(ctx, G.N, G.n, &D, st));
+    const int N = G.N, n = G.n;
+    const int64_t Nd = (G.dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    const int64_t nd = (G.dim == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+    const int64_t sx = (G.dim == 2) ? (int64_t)N * n : (int64_t)N * N * n;
+    const int64_t sy = (G.dim == 2) ? 0 : (int64_t)N * n * n;
+    C *F = nullptr, *X = nullptr, *Y = nullptr, *Z = nullptr, *Gf = nullptr;
+    CK(ctx, cudaMalloc(&F, Nd * sizeof(C)));
+    CK(ctx, cudaMalloc(&X, sx * sizeof(C)));
+    if (sy) CK(ctx, cudaMalloc(&Y, sy * sizeof(C)));
+    CK(ctx, cudaMalloc(&Z, nd * sizeof(C)));
+    CK(ctx, cudaMalloc(&Gf, 4 * nd * sizeof(C)));
+    CK(ctx, cudaMemsetAsync(Gf, 0, 4 * nd * sizeof(C), st));
+    for (int f = 0; f <= G.dim; ++f) {
+        CK(ctx, launch_wtable<T>((const C*)p->B1, D, N, G.dim, G.L, ctx->p.sigma_g, 0, f - 1, F, st));
+        RowArgs<T> r{};
+        r.in = F;
+        r.out = X;
+        r.nrows = (G.dim == 2) ? N : N * N;
+        r.in_row_stride = N;
+        r.out_row_stride = n;
+        r.len_in = N;
+        r.N = N;
+        r.n = n;
+        r.tw = tw.n;
+        CK(ctx, launch_rows<T>(ROW_EXPAND, r, 1, nullptr, st));
+        ColArgs<T> c{};
+        c.N = N;
+        c.n = n;
+        c.twF = tw.n;
+        c.twI = tw.n;
+        c.len_in = N;
+        if (G.dim == 3) {
+            c.in = X;
+            c.out = Y;
+            c.ncols = n;
+            c.nouter = N;
+            c.in_outer_stride = (int64_t)N * n;
+            c.out_outer_stride = (int64_t)n * n;
+            CK(ctx, launch_cols<T>(COL_EXPAND, c, 1, st));
+            c.in = Y;
+            c.out = Z;
+            c.ncols = n * n;
+            c.nouter = 1;
+            c.in_outer_stride = 0;
+            c.out_outer_stride = 0;
+            CK(ctx, launch_cols<T>(COL_EXPAND, c, 1, st));
+        } else {
+            c.in = X;
+            c.out = Z;
+            c.ncols = n;
+            c.nouter = 1;
+            CK(ctx, launch_cols<T>(COL_EXPAND, c, 1, st));
+        }
+        CK(ctx, launch_interleave<T>(Z, Gf, nd, f, st));
+    }
+    CK(ctx, cudaStreamSynchronize(st));
+    cudaFree(F);
+    cudaFree(X);
+    if (Y) cudaFree(Y);
+    cudaFree(Z);
+    p->G = Gf;
+    *out = p;
+    return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// search pipeline
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static int64_t per_rot_elems(const Geo& G, int64_t* e0, int64_t* e1) {
+    const int64_t N = G.N, s = G.s;
+    if (G.dim == 2) {
+        *e0 = std::max(s * s, N * N);
+        *e1 = s * N;
+    } else {
+        *e0 = std::max(s * s * s, s * N * N);
+        *e1 = std::max(s * s * N, N * N * N);
+    }
+    return *e0 + *e1;
+}
+
+template <typename T>
+static int choose_batch(sd_ctx* ctx, const Geo& G, int64_t n_r) {
+    int64_t e0, e1;
+    const int64_t per = per_rot_elems<T>(G, &e0, &e1) * (int64_t)sizeof(cplx<T>);
+    int64_t b = ctx->opt_batch > 0 ? ctx->opt_batch : std::max<int64_t>(1, ((int64_t)1 << 30) / per);
+    if (ctx->opt_plain) b = 1;
+    b = std::min<int64_t>(b, 64);
+    b = std::min<int64_t>(b, std::max<int64_t>(n_r, 1));
+    return (int)b;
+}
+
+// Runs the batched passes for rotations [0, n_r).  mode 0: argmax candidates; 1: maps.
+template <typename T>
+static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
+                      const sd_grid* g, void* out, int maps, cudaStream_t st) {
+    using C = cplx<T>;
+    Prep* prep = nullptr;
+    CKI(prep_fixed<T>(ctx, const_cast<sd_shape*>(fixed), g, &prep, st));
+    Geo G;
+    CKI(make_geo(ctx, g, moving->radius, &G));
+    Tw<T> tw;
+    CKI(get_tw<T>(ctx, G, &tw, st));
+    const int B = choose_batch<T>(ctx, G, n_r);
+    int64_t e0, e1;
+    per_rot_elems<T>(G, &e0, &e1);
+    void *b0v, *b1v, *psv, *piv;
+    CKI(ws_get(ctx, 0, (size_t)B * e0 * sizeof(C), &b0v));
+    CKI(ws_get(ctx, 1, (size_t)B * e1 * sizeof(C), &b1v));
+    const int64_t rows_last = (G.dim == 2) ? G.N : (int64_t)G.N * G.N;
+    const int64_t max_parts = rows_last;  // at most one partial per row
+    CKI(ws_get(ctx, 2, (size_t)B * max_parts * sizeof(double), &psv));
+    CKI(ws_get(ctx, 3, (size_t)B * max_parts * sizeof(int), &piv));
+    C* b0 = (C*)b0v;
+    C* b1 = (C*)b1v;
+    const C* W = (const C*)prep->W;
+    const int64_t Nd = (G.dim == 2) ? (int64_t)G.N * G.N : (int64_t)G.N * G.N * G.N;
+
+    // One launch sequence per batch; optionally replayed from a captured graph.
+    auto enqueue = [&](cudaStream_t s) -> int {
+        for (int64_t r0 = 0; r0 < n_r; r0 += B) {
+            const int b = (int)std::min<int64_t>(B, n_r - r0);
+            CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
+            SpreadArgs<T> sa{};
+            sa.pos = (const vec4<T>*)moving->pos;
+            sa.c = (const C*)moving->c;
+            sa.m = moving->m;
+            sa.quats = quats;
+            sa.rot0 = r0;
+            sa.sign = T(-1);
+            sa.inv_h = (T)G.inv_h;
+            sa.beta = (T)ctx->p.beta;
+            sa.w = ctx->p.w;
+            sa.s = G.s;
+            sa.s_h = G.s_h;
+            sa.out = b0;
+            sa.out_rot_stride = e0;
+            CK(ctx, launch_spread<T>(sa, G.dim, b, s));
+            CK(ctx, pass_x_fwd<T>(G, tw, b0, e0, b1, e1, b, s));
+            C* fin;
+            int64_t fin_rs;
+            if (G.dim == 3) {
+                CK(ctx, pass_y_fwd<T>(G, tw, b1, e1, b0, e0, b, s));
+                CK(ctx, pass_last<T>(COL_FUSED, G, tw, b0, e0, b1, e1, W, b, s));
+                CK(ctx, pass_y_inv<T>(G, tw, b1, e1, b, s));
+                fin = b1;
+                fin_rs = e1;
+            } else {
+                CK(ctx, pass_last<T>(COL_FUSED, G, tw, b1, e1, b0, e0, W, b, s));
+                fin = b0;
+                fin_rs = e0;
+            }
+            RowArgs<T> r{};
+            r.in = fin;
+            r.in_rot_stride = fin_rs;
+            r.nrows = (int)rows_last;
+            r.in_row_stride = G.N;
+            r.out_row_stride = G.N;
+            r.len_in = G.N;
+            r.N = G.N;
+            r.n = G.n;
+            r.tw = tw.N;
+            if (maps) {
+                r.out = (C*)out + r0 * Nd;
+                r.out_rot_stride = Nd;
+                CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
+            } else {
+                int nparts = 0;
+                r.part_score = (double*)psv;
+                r.part_idx = (int*)piv;
+                CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
+                CK(ctx, launch_reduce_argmax((const double*)psv, (const int*)piv, nparts, b, r0, out, s));
+            }
+        }
+        return SD_OK;
+    };
+
+    if (ctx->opt_graph && !ctx->opt_plain && st != nullptr) {
+        char key[256];
+        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d", (const void*)fixed, (const void*)moving,
+                 (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, B);
+        std::string k(key);
+        auto it = ctx->graphs.find(k);
+        if (it == ctx->graphs.end()) {
+            if (ctx->seen[k]++ == 0) return enqueue(st);  // first call runs eagerly (sets kernel attributes)
+            cudaGraph_t graph;
+            CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue(st);
+            cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (rc != SD_OK) return rc;
+            CK(ctx, ec);
+            GraphEntry ge;
+            ec = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ctx, ec);
+            it = ctx->graphs.emplace(k, ge).first;
+        }
+        CK(ctx, cudaGraphLaunch(it->second.exec, st));
+        return SD_OK;
+    }
+    return enqueue(st);
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+
+// Entry points (C linkage from the declarations in sdfdock.h).
+
+int sd_default_params(sd_params* p, int dim, int precision) {
+    if (!p) return SD_ERR_ARG;
+    memset(p, 0, sizeof *p);
+    p->dim = dim;
+    p->precision = precision;
+    p->lambda1 = 1.0;
+    p->lambda2 = 3.0;
+    p->sigma_t = 0.5;
+    p->eps = 1.5;
+    p->sigma_g = 0.03;
+    p->w = 6;
+    p->alpha = 2;
+    p->beta = 0.0;
+    return SD_OK;
+}
+
+int sd_create(sd_ctx** out, int device, const sd_params* p) {
+    if (!out || !p) return fail(nullptr, SD_ERR_ARG, "sd_create: NULL argument");
+    *out = nullptr;
+    if (p->dim != 2 && p->dim != 3) return fail(nullptr, SD_ERR_ARG, "dim must be 2 or 3");
+    if (p->precision != SD_F32 && p->precision != SD_F64) return fail(nullptr, SD_ERR_ARG, "bad precision");
+    if (p->alpha != 2) return fail(nullptr, SD_ERR_UNIMPLEMENTED, "only oversampling alpha = 2 is supported");
+    const int ws[] = {4, 5, 6, 7, 8, 10, 12, 16};
+    bool wok = false;
+    for (int w : ws) wok |= (p->w == w);
+    if (!wok) return fail(nullptr, SD_ERR_ARG, "spreading width w=%d not supported (4-8, 10, 12, 16)", p->w);
+    if (!(p->sigma_t > 0) || !(p->sigma_g > 0) || !(p->lambda1 >= 0) || !(p->lambda2 >= 0) || isnan(p->eps))
+        return fail(nullptr, SD_ERR_ARG, "sigma_t, sigma_g must be > 0; lambdas >= 0; eps not NaN");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, SD_ERR_CUDA, "CUDA device %d not available", device);
+    }
+    sd_ctx* c = new sd_ctx();
+    c->device = device;
+    c->p = *p;
+    if (!(c->p.beta > 0)) c->p.beta = 2.30 * c->p.w;
+    *out = c;
+    return SD_OK;
+}
+
+int sd_destroy(sd_ctx* ctx) {
+    if (!ctx) return SD_OK;
+    DeviceGuard dg(ctx->device);
+    for (auto& b : ctx->ws)
+        if (b.p) cudaFree(b.p);
+    for (auto& kv : ctx->twiddles) cudaFree(kv.second);
+    for (auto& kv : ctx->deconv) cudaFree(kv.second);
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (ctx->gl_x) cudaFree(ctx->gl_x);
+    if (ctx->gl_w) cudaFree(ctx->gl_w);
+    delete ctx;
+    return SD_OK;
+}
+
+const char* sd_last_error(const sd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
+    if (!ctx || !key) return SD_ERR_ARG;
+    if (!strcmp(key, "batch")) ctx->opt_batch = value;
+    else if (!strcmp(key, "graph")) ctx->opt_graph = (int)value;
+    else if (!strcmp(key, "plain")) ctx->opt_plain = (int)value;
+    else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
+    return SD_OK;
+}
+
+template <typename T>
+static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void* area, int64_t n_b, const void* qry,
+                       const void* vol, int64_t m, const int8_t* pmc_override, sd_shape** out, void* rho_out,
+                       cudaStream_t st) {
+    sd_shape* s = new sd_shape();
+    s->ctx = ctx;
+    s->m = m;
+    std::unique_ptr<sd_shape> guard(s);
+    T* xi = nullptr;
+    int8_t* pm = nullptr;
+    double* rad = nullptr;
+    auto cleanup = [&]() {
+        if (xi) cudaFree(xi);
+        if (pm) cudaFree(pm);
+        if (rad) cudaFree(rad);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&s->pos, (size_t)std::max<int64_t>(m, 1) * sizeof(vec4<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&s->c, (size_t)std::max<int64_t>(m, 1) * sizeof(cplx<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&xi, (size_t)std::max<int64_t>(m, 1) * sizeof(T))) != cudaSuccess ||
+        (e = cudaMalloc(&pm, (size_t)std::max<int64_t>(m, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&rad, sizeof(double))) != cudaSuccess) {
+        cleanup();
+        if (s->pos) cudaFree(s->pos);
+        if (s->c) cudaFree(s->c);
+        s->pos = s->c = nullptr;
+        return fail(ctx, SD_ERR_OOM, "sdf_build allocation failed: %s", cudaGetErrorString(e));
+    }
+    SdfArgs<T> a{};
+    a.bnd = (const vec4<T>*)bnd;
+    a.nrm = (const vec4<T>*)nrm;
+    a.area = (const T*)area;
+    a.n_b = n_b;
+    a.qry = (const vec4<T>*)qry;
+    a.vol = (const T*)vol;
+    a.m = m;
+    a.pmc_override = pmc_override;
+    a.lam1 = (T)ctx->p.lambda1;
+    a.lam2 = (T)ctx->p.lambda2;
+    a.sigma = (T)ctx->p.sigma_t;
+    a.eps = isinf(ctx->p.eps) ? T(-1) : (T)ctx->p.eps;
+    a.xi_abs = xi;
+    a.pmc = pm;
+    a.c_out = (cplx<T>*)s->c;
+    a.rho_out = (cplx<T>*)rho_out;
+    a.pos_out = (vec4<T>*)s->pos;
+    e = launch_sdf<T>(a, ctx->p.dim, st);
+    if (e == cudaSuccess) e = launch_radius<T>((const vec4<T>*)s->pos, m, ctx->p.dim, rad, st);
+    double r2 = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r2, rad, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        cudaFree(s->pos);
+        cudaFree(s->c);
+        s->pos = s->c = nullptr;
+        return fail(ctx, SD_ERR_CUDA, "sdf_build: %s", cudaGetErrorString(e));
+    }
+    if (!isfinite(r2)) return fail(ctx, SD_ERR_NONFINITE, "sdf_build: non-finite query point");
+    s->radius = sqrt(r2);
+    *out = guard.release();
+    return SD_OK;
+}
+
+int sd_sdf_build(sd_ctx* ctx, const void* bnd, const void* nrm, const void* area, int64_t n_b, const void* qry,
+                 const void* vol, int64_t m, const int8_t* pmc_override, sd_shape** out, void* rho_out,
+                 void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    if (!out) return fail(ctx, SD_ERR_ARG, "sdf_build: out is NULL");
+    *out = nullptr;
+    if (n_b <= 0 || m < 0) return fail(ctx, SD_ERR_ARG, "sdf_build: need n_b > 0 and m >= 0");
+    if (!bnd || !nrm || !area || (m > 0 && (!qry || !vol)))
+        return fail(ctx, SD_ERR_ARG, "sdf_build: NULL input pointer");
+    if (m > (int64_t)INT32_MAX || n_b > (int64_t)INT32_MAX) return fail(ctx, SD_ERR_ARG, "sdf_build: size too large");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64)
+        return sdf_build_t<double>(ctx, bnd, nrm, area, n_b, qry, vol, m, pmc_override, out, rho_out, st);
+    return sdf_build_t<float>(ctx, bnd, nrm, area, n_b, qry, vol, m, pmc_override, out, rho_out, st);
+}
+
+int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m, sd_shape** out, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    if (!out || (m > 0 && (!pos || !c)) || m < 0) return fail(ctx, SD_ERR_ARG, "shape_from_samples: bad arguments");
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rs = real_size(ctx);
+    sd_shape* s = new sd_shape();
+    s->ctx = ctx;
+    s->m = m;
+    std::unique_ptr<sd_shape> guard(s);
+    double* rad = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->pos, std::max<int64_t>(m, 1) * 4 * rs)) != cudaSuccess ||
+        (e = cudaMalloc(&s->c, std::max<int64_t>(m, 1) * 2 * rs)) != cudaSuccess ||
+        (e = cudaMalloc(&rad, sizeof(double))) != cudaSuccess) {
+        if (s->pos) cudaFree(s->pos);
+        if (s->c) cudaFree(s->c);
+        s->pos = s->c = nullptr;
+        return fail(ctx, SD_ERR_OOM, "shape_from_samples: %s", cudaGetErrorString(e));
+    }
+    double r2 = 0.0;
+    e = cudaMemcpyAsync(s->pos, pos, m * 4 * rs, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->c, c, m * 2 * rs, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = (ctx->p.precision == SD_F64) ? launch_radius<double>((const double4_32a*)s->pos, m, ctx->p.dim, rad, st)
+                                         : launch_radius<float>((const float4*)s->pos, m, ctx->p.dim, rad, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r2, rad, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(rad);
+    if (e != cudaSuccess) {
+        cudaFree(s->pos);
+        cudaFree(s->c);
+        s->pos = s->c = nullptr;
+        return fail(ctx, SD_ERR_CUDA, "shape_from_samples: %s", cudaGetErrorString(e));
+    }
+    if (!isfinite(r2)) return fail(ctx, SD_ERR_NONFINITE, "shape_from_samples: non-finite position");
+    s->radius = sqrt(r2);
+    *out = guard.release();
+    return SD_OK;
+}
+
+int sd_shape_info(const sd_shape* s, int64_t* m, double* radius) {
+    if (!s) return SD_ERR_ARG;
+    if (m) *m = s->m;
+    if (radius) *radius = s->radius;
+    return SD_OK;
+}
+
+int sd_shape_free(sd_shape* s) {
+    if (!s) return SD_OK;
+    DeviceGuard dg(s->ctx ? s->ctx->device : 0);
+    if (s->pos) cudaFree(s->pos);
+    if (s->c) cudaFree(s->c);
+    for (auto& p : s->preps) {
+        if (p.B1) cudaFree(p.B1);
+        if (p.W) cudaFree(p.W);
+        if (p.G) cudaFree(p.G);
+    }
+    delete s;
+    return SD_OK;
+}
+
+static int check_pair(sd_ctx* ctx, const sd_shape* a, const sd_shape* b) {
+    if (!a || !b) return fail(ctx, SD_ERR_ARG, "shape is NULL");
+    if (a->ctx != ctx || b->ctx != ctx) return fail(ctx, SD_ERR_ARG, "shape belongs to another context");
+    if (a->m == 0 || b->m == 0) return fail(ctx, SD_ERR_ARG, "shape has no samples");
+    return SD_OK;
+}
+
+int sd_score_rotations(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
+                       const sd_grid* g, int k_r, sd_cand* cand_out, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    CKI(check_pair(ctx, fixed, moving));
+    if (n_r < 0 || n_r > (int64_t)INT32_MAX) return fail(ctx, SD_ERR_ARG, "score_rotations: bad rotation count");
+    if (n_r == 0) return SD_OK;
+    if (!quats || !cand_out) return fail(ctx, SD_ERR_ARG, "score_rotations: NULL pointer");
+    if (k_r != 1) return fail(ctx, SD_ERR_UNIMPLEMENTED, "score_rotations: only k_r = 1 is supported");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64)
+        return run_search<double>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st);
+    return run_search<float>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st);
+}
+
+int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
+                  const sd_grid* g, void* map_out, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    CKI(check_pair(ctx, fixed, moving));
+    if (n_r < 0 || n_r > (int64_t)INT32_MAX) return fail(ctx, SD_ERR_ARG, "score_maps: bad rotation count");
+    if (n_r == 0) return SD_OK;
+    if (!quats || !map_out) return fail(ctx, SD_ERR_ARG, "score_maps: NULL pointer");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64) return run_search<double>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
+    return run_search<float>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
+}
+
+template <typename T>
+static int top_k_t(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int rescore, const sd_shape* fixed,
+                   const sd_shape* moving, const double* quats, const sd_grid* g, sd_pose* out, cudaStream_t st) {
+    void *flags, *top, *res;
+    CKI(ws_get(ctx, 4, (size_t)((n_cand + 31) / 32) * 4 + 256, &flags));
+    CKI(ws_get(ctx, 5, (size_t)k * (sizeof(sd_cand) + 2 * sizeof(double)) + 256, &top));
+    res = (char*)top + (((size_t)k * sizeof(sd_cand) + 255) / 256) * 256;
+    CK(ctx, launch_topk(cand, n_cand, k, top, (unsigned*)flags, st));
+    if (rescore) {
+        RescoreArgs<T> a{};
+        a.p1 = (const vec4<T>*)fixed->pos;
+        a.c1 = (const cplx<T>*)fixed->c;
+        a.m1 = fixed->m;
+        a.p2 = (const vec4<T>*)moving->pos;
+        a.c2 = (const cplx<T>*)moving->c;
+        a.m2 = moving->m;
+        a.top = top;
+        a.k = k;
+        a.quats = quats;
+        a.N = g->N;
+        a.L = g->L;
+        a.sigma_g = ctx->p.sigma_g;
+        a.dim = ctx->p.dim;
+        a.r2max = moving->radius * moving->radius;
+        a.out = (double*)res;
+        CK(ctx, launch_rescore<T>(a, st));
+    }
+    std::vector<sd_cand> hc(k);
+    std::vector<double> hr(2 * (size_t)k, 0.0);
+    CK(ctx, cudaMemcpyAsync(hc.data(), top, k * sizeof(sd_cand), cudaMemcpyDeviceToHost, st));
+    if (rescore) CK(ctx, cudaMemcpyAsync(hr.data(), res, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    const double h = g->L / g->N;
+    for (int i = 0; i < k; ++i) {
+        sd_pose& p = out[i];
+        memset(&p, 0, sizeof p);
+        p.score = hc[i].score;
+        p.rot = hc[i].rot;
+        p.idx = hc[i].idx;
+        int idx = hc[i].idx < 0 ? 0 : hc[i].idx;
+        for (int d = 0; d < ctx->p.dim; ++d) {
+            p.t[d] = (double)(idx % g->N - g->N / 2) * h;
+            idx /= g->N;
+        }
+        p.score_fp64 = hr[2 * i];
+        p.score_fp64_im = hr[2 * i + 1];
+    }
+    return SD_OK;
+}
+
+int sd_top_k_poses(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int rescore_fp64, const sd_shape* fixed,
+                   const sd_shape* moving, const double* quats, const sd_grid* g, sd_pose* out, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    if (!cand || !out || n_cand < 1 || n_cand > ((int64_t)1 << 22) || k < 1 || k > 4096)
+        return fail(ctx, SD_ERR_ARG, "top_k_poses: need 1 <= n_cand <= 2^22, 1 <= k <= 4096 and buffers");
+    if (!g || !grid_ok(g->N)) return fail(ctx, SD_ERR_ARG, "top_k_poses: bad grid");
+    if (rescore_fp64) {
+        CKI(check_pair(ctx, fixed, moving));
+        if (!quats) return fail(ctx, SD_ERR_ARG, "top_k_poses: quats needed for the re-score");
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64)
+        return top_k_t<double>(ctx, cand, n_cand, k, rescore_fp64, fixed, moving, quats, g, out, st);
+    return top_k_t<float>(ctx, cand, n_cand, k, rescore_fp64, fixed, moving, quats, g, out, st);
+}
+
+template <typename T>
+static int score_grad_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g,
+                        const void* quats, const void* trans, int64_t P, void* score, void* dq, void* dt,
+                        cudaStream_t st) {
+    Prep* p = nullptr;
+    CKI(prep_fields<T>(ctx, const_cast<sd_shape*>(fixed), g, &p, st));
+    void* acc;
+    CKI(ws_get(ctx, 4, (size_t)P * 8 * sizeof(double) + 256, &acc));
+    GatherArgs<T> a{};
+    a.p2 = (const vec4<T>*)moving->pos;
+    a.c2 = (const cplx<T>*)moving->c;
+    a.m2 = moving->m;
+    a.quats = (const T*)quats;
+    a.trans = (const T*)trans;
+    a.P = P;
+    a.G = (const cplx<T>*)p->G;
+    a.n = ctx->p.alpha * g->N;
+    a.inv_h = (T)(a.n / g->L);
+    a.beta = (T)ctx->p.beta;
+    a.w = ctx->p.w;
+    a.acc = (double*)acc;
+    CK(ctx, launch_gather<T>(a, ctx->p.dim, st));
+    CK(ctx, launch_grad_finalize<T>((const double*)acc, (const T*)quats, P, ctx->p.dim, (T*)score, (T*)dq, (T*)dt, st));
+    return SD_OK;
+}
+
+int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, const void* quats,
+                  const void* trans, int64_t P, void* score, void* dq, void* dt, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    CKI(check_pair(ctx, fixed, moving));
+    if (P < 0 || P > 65535) return fail(ctx, SD_ERR_ARG, "score_grad: 0 <= P <= 65535");
+    if (P == 0) return SD_OK;
+    if (!quats || !trans || !score || !dq || !dt) return fail(ctx, SD_ERR_ARG, "score_grad: NULL pointer");
+    if (!g || !grid_ok(g->N)) return fail(ctx, SD_ERR_ARG, "score_grad: bad grid");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64)
+        return score_grad_t<double>(ctx, fixed, moving, g, quats, trans, P, score, dq, dt, st);
+    return score_grad_t<float>(ctx, fixed, moving, g, quats, trans, P, score, dq, dt, st);
+}
+
+// Host execution of the line-FFT stage sequence used by every pass kernel, in
+// FP64: lets the index arithmetic be checked without a GPU.  in/out: len x 2.
+int sd_host_line_fft(int len, int inverse, const double* in, double* out) {
+    if (!in || !out || !fft_len_supported(len)) return SD_ERR_ARG;
+    std::vector<double2> a(pad(len) + 2), b(pad(len) + 2), tw(len);
+    for (int j = 0; j < len; ++j) {
+        const double ang = -2.0 * M_PI * (double)j / (double)len;
+        tw[j] = make_double2(cos(ang), sin(ang));
+        a[pad(j)] = make_double2(in[2 * j], in[2 * j + 1]);
+    }
+    double2* r = nullptr;
+#define SD_HOST_CASE(L)                                                                           \
+    case L:                                                                                       \
+        r = inverse ? fft_line_host<double2, L, true>(a.data(), b.data(), tw.data())              \
+                    : fft_line_host<double2, L, false>(a.data(), b.data(), tw.data());            \
+        break;
+    switch (len) { SD_FOR_EACH_LEN(SD_HOST_CASE) }
+#undef SD_HOST_CASE
+    if (!r) return SD_ERR_ARG;
+    for (int j = 0; j < len; ++j) {
+        out[2 * j] = r[pad(j)].x;
+        out[2 * j + 1] = r[pad(j)].y;
+    }
+    return SD_OK;
+}
+
+const char* sd_version(void) { return "sdfdock 0.1 (sm_103a)"; }

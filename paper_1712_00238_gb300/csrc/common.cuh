@@ -1,0 +1,59 @@
+// Shared device helpers: complex arithmetic on float2/double2, real-type traits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sd {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+template <typename T> struct vec4_of;
+template <> struct vec4_of<float> { using type = float4; };
+template <> struct vec4_of<double> { using type = double4_32a; };
+template <typename T> using vec4 = typename vec4_of<T>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { return mk(a.x * s, a.y * s); }
+// a * (-i) for the forward sign, a * (+i) for the inverse sign
+template <bool INV, typename C> __host__ __device__ __forceinline__ C mul_mi(C a) {
+    return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+
+// Complex accumulation into global memory (atomic).
+__device__ __forceinline__ void atomic_cadd(float2* p, float2 v) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    atomicAdd(p, v);  // one vector reduction (sm_90+)
+#else
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+#endif
+}
+__device__ __forceinline__ void atomic_cadd(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+// Rotation matrix of q / |q| (Hamilton, active), row-major 3x3, from doubles.
+template <typename T>
+__device__ __forceinline__ void quat_to_matrix(const double* q4, T R[9]) {
+    double w = q4[0], x = q4[1], y = q4[2], z = q4[3];
+    double n = w * w + x * x + y * y + z * z;
+    double s = (n > 0.0) ? 2.0 / n : 0.0;
+    R[0] = T(1.0 - s * (y * y + z * z)); R[1] = T(s * (x * y - w * z)); R[2] = T(s * (x * z + w * y));
+    R[3] = T(s * (x * y + w * z)); R[4] = T(1.0 - s * (x * x + z * z)); R[5] = T(s * (y * z - w * x));
+    R[6] = T(s * (x * z - w * y)); R[7] = T(s * (y * z + w * x)); R[8] = T(1.0 - s * (x * x + y * y));
+}
+
+}  // namespace sd

@@ -1,0 +1,193 @@
+// Batched line FFTs in shared memory: mixed radix (2, 3, 4, 8, 16) Stockham
+// autosort stages (Van Loan, "Computational Frameworks for the FFT", 1992).
+//
+// Each stage of radix R over a line of LEN points takes, for every butterfly
+// index i in [0, LEN/R), the R inputs x[i + r*LEN/R], multiplies input r by the
+// twiddle exp(-+2 pi i * r*k / (P*R)) with k = i mod P (P = product of the radices
+// of the earlier stages), applies an R-point DFT in registers and stores output r
+// at (i - k)*R + k + r*P.  After the last stage the line is in natural order.
+// Forward transforms use exp(-2 pi i jk/LEN); inverse ones exp(+2 pi i jk/LEN),
+// unnormalised.
+//
+// Lines live in shared memory with a pitch `ld` (complex elements) and an
+// in-line padding of one element per 16 (pad()) so that the strided stores of the
+// early stages do not hit one bank.
+#pragma once
+
+#include "common.cuh"
+
+namespace sd {
+
+// Radix of stage s for a line of `len` points (0 past the last stage).
+__host__ __device__ constexpr int plan_radix(int len, int s) {
+    switch (len) {
+        case 8: return s == 0 ? 8 : 0;
+        case 16: return s == 0 ? 16 : 0;
+        case 24: return s == 0 ? 8 : (s == 1 ? 3 : 0);
+        case 32: return s == 0 ? 8 : (s == 1 ? 4 : 0);
+        case 48: return s == 0 ? 16 : (s == 1 ? 3 : 0);
+        case 64: return s == 0 ? 8 : (s == 1 ? 8 : 0);
+        case 96: return s == 0 ? 8 : (s == 1 ? 4 : (s == 2 ? 3 : 0));
+        case 128: return s == 0 ? 16 : (s == 1 ? 8 : 0);
+        case 192: return s == 0 ? 16 : (s == 1 ? 4 : (s == 2 ? 3 : 0));
+        case 256: return s == 0 ? 16 : (s == 1 ? 16 : 0);
+        case 384: return s == 0 ? 16 : (s == 1 ? 8 : (s == 2 ? 3 : 0));
+        case 512: return s == 0 ? 8 : (s == 1 ? 8 : (s == 2 ? 8 : 0));
+        default: return 0;
+    }
+}
+
+__host__ __device__ constexpr bool fft_len_supported(int len) { return plan_radix(len, 0) != 0; }
+
+// Applies X to every supported line length.
+#define SD_FOR_EACH_LEN(X) X(8) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+__host__ __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+// Padded line storage (elements) and an odd pitch for column-wise tile fills.
+__host__ __device__ constexpr int line_pitch(int len) { return ((len + (len >> 4)) | 1); }
+
+// ---------------------------------------------------------------------------
+// R-point DFTs in registers.  INV selects the +i sign.
+// ---------------------------------------------------------------------------
+
+template <bool INV, typename C>
+__host__ __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+// exp(-+2 pi i m / 16) as constants (cos and sin of multiples of pi/8).
+template <bool INV, typename C>
+__host__ __device__ __forceinline__ C w16(int m) {
+    using T = decltype(C{}.x);
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r = T(0.70710678118654752440);
+    T cr, si;  // exp(-i 2 pi m/16) = cr - i si
+    switch (m) {
+        case 0: cr = 1; si = 0; break;
+        case 1: cr = c1; si = s1; break;
+        case 2: cr = r; si = r; break;
+        case 3: cr = s1; si = c1; break;
+        case 4: cr = 0; si = 1; break;
+        case 6: cr = -r; si = r; break;
+        case 9: cr = -c1; si = -s1; break;
+        default: cr = 1; si = 0; break;  // not used by dft16
+    }
+    return INV ? mk(cr, si) : mk(cr, -si);
+}
+
+template <int R, bool INV, typename C>
+__host__ __device__ __forceinline__ void dft(C* v) {
+    using T = decltype(C{}.x);
+    if constexpr (R == 2) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        const T s3 = T(0.86602540378443864676);
+        C t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
+        C m = csub(v[0], cscale(t, T(0.5)));
+        v[0] = cadd(v[0], t);
+        C d = cscale(mul_mi<INV>(u), s3);
+        v[1] = cadd(m, d);
+        v[2] = csub(m, d);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        const T r = T(0.70710678118654752440);
+        C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+        C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4<INV>(e0, e1, e2, e3);
+        dft4<INV>(o0, o1, o2, o3);
+        // o_k *= exp(-+2 pi i k/8)
+        o1 = cmul(o1, INV ? mk(r, r) : mk(r, -r));
+        o2 = mul_mi<INV>(o2);
+        o3 = cmul(o3, INV ? mk(-r, r) : mk(-r, -r));
+        v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+        v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+        v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+        v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+    } else if constexpr (R == 16) {
+        // n = 4 n1 + n2, k = k1 + 4 k2
+        C b[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            b[n2][0] = v[n2]; b[n2][1] = v[4 + n2]; b[n2][2] = v[8 + n2]; b[n2][3] = v[12 + n2];
+            dft4<INV>(b[n2][0], b[n2][1], b[n2][2], b[n2][3]);
+        }
+#pragma unroll
+        for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) b[n2][k1] = cmul(b[n2][k1], w16<INV, C>(n2 * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C x0 = b[0][k1], x1 = b[1][k1], x2 = b[2][k1], x3 = b[3][k1];
+            dft4<INV>(x0, x1, x2, x3);
+            v[k1] = x0; v[k1 + 4] = x1; v[k1 + 8] = x2; v[k1 + 12] = x3;
+        }
+    }
+}
+
+// One butterfly of a Stockham stage (shared by the device stage loop and the
+// host-side check).  `tw[j]` = exp(-2 pi i j / LEN).
+template <typename C, int LEN, int R, int P, bool INV>
+__host__ __device__ __forceinline__ void stockham_butterfly(const C* __restrict__ src, C* __restrict__ dst,
+                                                            int i, const C* __restrict__ tw) {
+    constexpr int NB = LEN / R;
+    const int k = i % P;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[pad(i + r * NB)];
+    if constexpr (P > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[r * k * (LEN / (P * R))];
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+    }
+    dft<R, INV>(v);
+    const int j = (i - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[pad(j + r * P)] = v[r];
+}
+
+#ifdef __CUDACC__
+// All threads of the block transform `nlines` lines held at src + line*ld.
+// Returns the buffer that holds the result (src or dst).  Contains
+// __syncthreads(); every thread of the block must call it.
+template <typename C, int LEN, bool INV, int S = 0, int P = 1>
+__device__ __forceinline__ C* fft_lines(C* src, C* dst, int nlines, int ld, const C* tw) {
+    constexpr int R = plan_radix(LEN, S);
+    if constexpr (R == 0) {
+        return src;
+    } else {
+        constexpr int NB = LEN / R;
+        const int tot = nlines * NB;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int line = t / NB;
+            const int i = t - line * NB;
+            stockham_butterfly<C, LEN, R, P, INV>(src + line * ld, dst + line * ld, i, tw);
+        }
+        __syncthreads();
+        return fft_lines<C, LEN, INV, S + 1, P * R>(dst, src, nlines, ld, tw);
+    }
+}
+#endif
+
+// Host-side reference of the same stage sequence on one line (used by the
+// library's self-test of the index arithmetic).
+template <typename C, int LEN, bool INV, int S = 0, int P = 1>
+inline C* fft_line_host(C* src, C* dst, const C* tw) {
+    constexpr int R = plan_radix(LEN, S);
+    if constexpr (R == 0) {
+        return src;
+    } else {
+        for (int i = 0; i < LEN / R; ++i) stockham_butterfly<C, LEN, R, P, INV>(src, dst, i, tw);
+        return fft_line_host<C, LEN, INV, S + 1, P * R>(dst, src, tw);
+    }
+}
+
+}  // namespace sd

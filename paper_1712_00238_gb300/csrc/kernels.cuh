@@ -1,0 +1,155 @@
+// Kernel argument blocks and host-side launchers of every device step.
+//
+// Layout conventions (all arrays complex, row-major, x fastest):
+//   sub-box   : the spread target, s^d cells; cell a along an axis stands for the
+//               oversampled-grid index u = a - s_h (mod n).  s = 2 s_h <= n.
+//   modes     : kappa in [-N/2, N/2) stored at kappa mod N along each axis.
+//   score map : t index i in [0, N) per axis, t = (i - N/2) h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sd {
+
+// ---- SDF (Eq. 10A-17t) ------------------------------------------------------
+template <typename T>
+struct SdfArgs {
+    const vec4<T>* bnd;   // n_b boundary positions
+    const vec4<T>* nrm;   // n_b unit outward normals
+    const T* area;        // n_b
+    int64_t n_b;
+    const vec4<T>* qry;   // m query points
+    const T* vol;         // m
+    int64_t m;
+    const int8_t* pmc_override;  // m or null
+    T lam1, lam2, sigma, eps;    // eps < 0 disables truncation
+    // outputs / intermediates
+    T* xi_abs;            // m: nearest distance
+    int8_t* pmc;          // m: +1 / -1
+    cplx<T>* c_out;       // m: rho * vol
+    cplx<T>* rho_out;     // m or null
+    vec4<T>* pos_out;     // m: copy of the query points for the shape
+};
+template <typename T> cudaError_t launch_sdf(const SdfArgs<T>& a, int dim, cudaStream_t st);
+
+// max |p| over m points (result in *out, device double)
+template <typename T> cudaError_t launch_radius(const vec4<T>* p, int64_t m, int dim, double* out,
+                                                cudaStream_t st);
+
+// ---- type-1 spreading -------------------------------------------------------
+template <typename T>
+struct SpreadArgs {
+    const vec4<T>* pos;   // m sample positions
+    const cplx<T>* c;     // m sample weights
+    int64_t m;
+    const double* quats;  // rotation list (w, x, y, z); null = identity
+    int64_t rot0;         // first rotation of this batch
+    T sign;               // spread at sign * R p
+    T inv_h;              // 1 / h' (oversampled spacing)
+    T beta;               // ES kernel shape
+    int w;                // kernel width (cells)
+    int s, s_h;           // sub-box side and half-side
+    cplx<T>* out;         // batch x s^d
+    int64_t out_rot_stride;
+};
+template <typename T> cudaError_t launch_spread(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);
+
+// ---- line passes ------------------------------------------------------------
+enum RowMode { ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3 };
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FUSED = 2, COL_EXPAND = 3 };
+
+template <typename T>
+struct RowArgs {
+    const cplx<T>* in;
+    cplx<T>* out;
+    int64_t in_rot_stride, out_rot_stride;
+    int nrows, in_row_stride, out_row_stride;
+    int len_in;   // ROW_FWD: s (data at u = e - s_h); others: N
+    int s_h;
+    int N;        // modes / outputs per line
+    int n;        // oversampled length (ROW_FWD, ROW_EXPAND)
+    const cplx<T>* tw;        // twiddles of the transform length
+    double* part_score;       // ROW_INV_ARGMAX: batch x gridDim.x
+    int* part_idx;
+};
+template <typename T> cudaError_t launch_rows(int mode, const RowArgs<T>& a, int batch, int* nparts,
+                                              cudaStream_t st);
+
+template <typename T>
+struct ColArgs {
+    const cplx<T>* in;
+    cplx<T>* out;
+    int64_t in_rot_stride, out_rot_stride;
+    int ncols;                          // contiguous columns; element stride along the axis
+    int nouter;
+    int64_t in_outer_stride, out_outer_stride;
+    int len_in;                         // COL_FWD / COL_FUSED: s; others N
+    int s_h;
+    int N, n;
+    const cplx<T>* twF;                 // twiddles of n (forward / expand)
+    const cplx<T>* twI;                 // twiddles of N (inverse)
+    const cplx<T>* W;                   // COL_FUSED: N x ncols table
+};
+template <typename T> cudaError_t launch_cols(int mode, const ColArgs<T>& a, int batch, cudaStream_t st);
+
+// twiddles exp(-2 pi i j / len), computed in FP64
+template <typename T> cudaError_t launch_twiddles(cplx<T>* tw, int len, cudaStream_t st);
+
+// ---- tables (FP64) ------------------------------------------------------------
+// D[kappa'] = (w/2) * psihat(pi * kappa * w / n), kappa' in [0, N), by Gauss-Legendre
+// quadrature of the ES kernel (nodes/weights on [0, pi/2] after z = sin(theta)).
+cudaError_t launch_deconv(double* D, int N, int n, int w, double beta, const double* gl_x,
+                          const double* gl_w, int nq, cudaStream_t st);
+
+// W = (-1)^{sum kappa} exp(-sg^2 |k|^2) B1 / (L^d prod D^2); zero on Nyquist.
+// shift = 0 drops the (-1)^{sum kappa} factor; deriv = -1 (none) or axis a
+// multiplies by i k_a.
+template <typename T>
+cudaError_t launch_wtable(const cplx<T>* B1, const double* D, int N, int dim, double L, double sigma_g,
+                          int shift, int deriv, cplx<T>* W, cudaStream_t st);
+
+// argmax partials -> one candidate per rotation
+cudaError_t launch_reduce_argmax(const double* part_score, const int* part_idx, int nparts, int batch,
+                                 int64_t rot0, void* cand, cudaStream_t st);
+
+// copy field f of 4 into an interleaved [cell][4] array
+template <typename T>
+cudaError_t launch_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f, cudaStream_t st);
+
+// ---- search -----------------------------------------------------------------
+cudaError_t launch_topk(const void* cand, int64_t n, int k, void* out_cand, unsigned* flags,
+                        cudaStream_t st);
+template <typename T>
+struct RescoreArgs {
+    const vec4<T>* p1; const cplx<T>* c1; int64_t m1;
+    const vec4<T>* p2; const cplx<T>* c2; int64_t m2;
+    const void* top;          // k sd_cand
+    int k;
+    const double* quats;
+    int N; double L; double sigma_g; int dim;
+    double r2max;             // squared bounding radius of the moving samples
+    double* out;              // k x 2 (re, im)
+};
+template <typename T> cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st);
+
+// ---- type-2 gather: score and gradient ---------------------------------------
+template <typename T>
+struct GatherArgs {
+    const vec4<T>* p2; const cplx<T>* c2; int64_t m2;
+    const T* quats;           // P x 4
+    const T* trans;           // P x 3
+    int64_t P;
+    const cplx<T>* G;         // n^d x 4 (Phi, dPhi/dx, dPhi/dy, dPhi/dz)
+    int n;
+    T inv_h, beta;
+    int w;
+    double* acc;              // P x 8
+};
+template <typename T> cudaError_t launch_gather(const GatherArgs<T>& a, int dim, cudaStream_t st);
+template <typename T> cudaError_t launch_grad_finalize(const double* acc, const T* quats, int64_t P, int dim,
+                                                       T* score, T* dq, T* dt, cudaStream_t st);
+
+}  // namespace sd

@@ -1,0 +1,516 @@
+// Type-1 nonuniform FFT of rotated samples and the translation-score passes.
+//
+// Per rotation (Section 5: one FFT over the translations per rotation; the
+// scattered samples go through a nonequispaced FFT with oversampling alpha = 2):
+//   spread   c_j at y_j = -R p_j onto the oversampled grid with the
+//            exponential-of-semicircle kernel psi(z) = exp(beta (sqrt(1 - z^2) - 1))
+//            (Barnett, Magland & af Klinteberg 2019), only inside the sub-box that
+//            the rotated shape can reach;
+//   x pass   forward FFT of length n on the sub-box rows, keep the N central modes;
+//   y pass   the same along y (3D);
+//   fused    forward FFT along the last axis, keep N modes, multiply by the fixed
+//            shape's table W(kappa), inverse FFT of length N along that axis;
+//   y pass   inverse along y (3D);
+//   x pass   inverse along x, real part, argmax (or the complex map).
+#pragma once
+
+#include <float.h>
+#include <limits.h>
+
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace sd {
+
+struct CandRec {  // same layout as sd_cand
+    double score;
+    int32_t rot;
+    int32_t idx;
+};
+
+template <typename T, int LEN>
+__host__ __device__ constexpr int lines_per_cta() {
+    return (LEN * (int)sizeof(cplx<T>) > 4096) ? 8 : 16;
+}
+
+// ---------------------------------------------------------------------------
+// spreading
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap_index(int a, int s) {
+    a %= s;
+    return a < 0 ? a + s : a;
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
+    using C = cplx<T>;
+    __shared__ T Rm[9];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) {
+        if (a.quats) {
+            quat_to_matrix<T>(a.quats + 4 * (a.rot0 + b), Rm);
+        } else {
+            for (int i = 0; i < 9; ++i) Rm[i] = (i % 4 == 0) ? T(1) : T(0);
+        }
+    }
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.m) return;
+    const vec4<T> p = a.pos[j];
+    const C c = a.c[j];
+    T y[3];
+    y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
+    y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
+    y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
+    T wt[D][W];
+    int ix[D][W];
+    const T half = T(W) * T(0.5);
+    const T inv_half = T(2) / T(W);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const T g = y[d] * a.inv_h;
+        const int u0 = (int)ceil(g - half);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const T z = (T(u0 + k) - g) * inv_half;
+            const T z2 = z * z;
+            wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+            ix[d][k] = wrap_index(u0 + k + a.s_h, a.s);
+        }
+    }
+    C* out = a.out + (int64_t)b * a.out_rot_stride;
+    const int s = a.s;
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int ky = 0; ky < W; ++ky) {
+            const C cy = cscale(c, wt[1][ky]);
+            C* row = out + (int64_t)ix[1][ky] * s;
+#pragma unroll
+            for (int kx = 0; kx < W; ++kx) atomic_cadd(row + ix[0][kx], cscale(cy, wt[0][kx]));
+        }
+    } else {
+#pragma unroll 1
+        for (int kz = 0; kz < W; ++kz) {
+            const C cz = cscale(c, wt[2][kz]);
+            C* plane = out + (int64_t)ix[2][kz] * s * s;
+#pragma unroll
+            for (int ky = 0; ky < W; ++ky) {
+                const C cy = cscale(cz, wt[1][ky]);
+                C* row = plane + (int64_t)ix[1][ky] * s;
+#pragma unroll
+                for (int kx = 0; kx < W; ++kx) atomic_cadd(row + ix[0][kx], cscale(cy, wt[0][kx]));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row passes (lines contiguous in memory)
+// ---------------------------------------------------------------------------
+
+template <typename T, int LEN, int MODE>
+__global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int LD = line_pitch(LEN);
+    constexpr bool INV = (MODE != ROW_FWD);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufA = reinterpret_cast<C*>(smem_raw);
+    C* bufB = bufA + TR * LD;
+    C* tw = bufB + TR * LD;
+    const int b = blockIdx.y;
+    const int row0 = blockIdx.x * TR;
+    for (int j = threadIdx.x; j < LEN; j += blockDim.x) tw[j] = a.tw[j];
+    const C* in = a.in + (int64_t)b * a.in_rot_stride;
+    const C zero = mk(T(0), T(0));
+    for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+        const int r = idx / LEN;
+        const int pos = idx - r * LEN;
+        const int row = row0 + r;
+        C v = zero;
+        if (row < a.nrows) {
+            const C* src = in + (int64_t)row * a.in_row_stride;
+            if constexpr (MODE == ROW_FWD) {
+                int e = pos + a.s_h;
+                if (e >= LEN) e -= LEN;
+                if (e < a.len_in) v = src[e];
+            } else if constexpr (MODE == ROW_EXPAND) {
+                const int hN = a.N >> 1;
+                const int e = pos < hN ? pos : (pos >= LEN - hN ? pos - LEN + a.N : -1);
+                if (e >= 0) v = src[e];
+            } else {
+                v = src[pos];
+            }
+        }
+        bufA[r * LD + pad(pos)] = v;
+    }
+    __syncthreads();
+    C* res = fft_lines<C, LEN, INV>(bufA, bufB, TR, LD, tw);
+    C* out = a.out + (int64_t)b * a.out_rot_stride;
+    if constexpr (MODE == ROW_FWD) {
+        const int N = a.N, hN = N >> 1;
+        for (int idx = threadIdx.x; idx < TR * N; idx += blockDim.x) {
+            const int r = idx / N;
+            const int kp = idx - r * N;
+            const int row = row0 + r;
+            if (row < a.nrows) {
+                const int pos = kp < hN ? kp : kp - N + LEN;
+                out[(int64_t)row * a.out_row_stride + kp] = res[r * LD + pad(pos)];
+            }
+        }
+    } else if constexpr (MODE == ROW_INV_MAP || MODE == ROW_EXPAND) {
+        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+            const int r = idx / LEN;
+            const int e = idx - r * LEN;
+            const int row = row0 + r;
+            if (row < a.nrows) out[(int64_t)row * a.out_row_stride + e] = res[r * LD + pad(e)];
+        }
+    } else {  // ROW_INV_ARGMAX: best (max Re, lowest index) of this tile
+        T best = -INFINITY;
+        int bidx = INT_MAX;
+        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+            const int r = idx / LEN;
+            const int e = idx - r * LEN;
+            const int row = row0 + r;
+            if (row < a.nrows) {
+                const T v = res[r * LD + pad(e)].x;
+                const int gi = row * LEN + e;
+                if (v > best || (v == best && gi < bidx)) {
+                    best = v;
+                    bidx = gi;
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const T ob = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+            if (ob > best || (ob == best && oi < bidx)) {
+                best = ob;
+                bidx = oi;
+            }
+        }
+        __shared__ T wb[32];
+        __shared__ int wi[32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            wb[warp] = best;
+            wi[warp] = bidx;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = (blockDim.x + 31) >> 5;
+            best = lane < nw ? wb[lane] : T(-INFINITY);
+            bidx = lane < nw ? wi[lane] : INT_MAX;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+                if (ob > best || (ob == best && oi < bidx)) {
+                    best = ob;
+                    bidx = oi;
+                }
+            }
+            if (lane == 0) {
+                const int64_t o = (int64_t)b * gridDim.x + blockIdx.x;
+                a.part_score[o] = (double)best;
+                a.part_idx[o] = bidx;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// column passes (lines strided; a CTA takes TC adjacent columns)
+// ---------------------------------------------------------------------------
+
+template <typename T, int LENF, int LENI, int MODE>
+__global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LENF>();
+    constexpr int LD = line_pitch(LENF);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufA = reinterpret_cast<C*>(smem_raw);
+    C* bufB = bufA + TC * LD;
+    C* twF = bufB + TC * LD;
+    C* twI = twF + LENF;
+    const int b = blockIdx.z;
+    const int outer = blockIdx.y;
+    const int col0 = blockIdx.x * TC;
+    for (int j = threadIdx.x; j < LENF; j += blockDim.x) twF[j] = a.twF[j];
+    if constexpr (MODE == COL_FUSED)
+        for (int j = threadIdx.x; j < LENI; j += blockDim.x) twI[j] = a.twI[j];
+    const int ncols = a.ncols;
+    const C* in = a.in + (int64_t)b * a.in_rot_stride + (int64_t)outer * a.in_outer_stride;
+    C* out = a.out + (int64_t)b * a.out_rot_stride + (int64_t)outer * a.out_outer_stride;
+    const C zero = mk(T(0), T(0));
+    const int hN = a.N >> 1;
+    for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
+        const int col = idx % TC;
+        const int pos = idx / TC;
+        const int gcol = col0 + col;
+        int e;
+        if constexpr (MODE == COL_FWD || MODE == COL_FUSED) {
+            e = pos + a.s_h;
+            if (e >= LENF) e -= LENF;
+            if (e >= a.len_in) e = -1;
+        } else if constexpr (MODE == COL_EXPAND) {
+            e = pos < hN ? pos : (pos >= LENF - hN ? pos - LENF + a.N : -1);
+        } else {
+            e = pos;
+        }
+        C v = zero;
+        if (e >= 0 && gcol < ncols) v = in[(int64_t)e * ncols + gcol];
+        bufA[col * LD + pad(pos)] = v;
+    }
+    __syncthreads();
+    constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
+    C* res = fft_lines<C, LENF, INV1>(bufA, bufB, TC, LD, twF);
+    if constexpr (MODE == COL_FWD) {
+        for (int idx = threadIdx.x; idx < TC * a.N; idx += blockDim.x) {
+            const int col = idx % TC;
+            const int kp = idx / TC;
+            const int gcol = col0 + col;
+            if (gcol < ncols) {
+                const int pos = kp < hN ? kp : kp - a.N + LENF;
+                out[(int64_t)kp * ncols + gcol] = res[col * LD + pad(pos)];
+            }
+        }
+    } else if constexpr (MODE == COL_INV || MODE == COL_EXPAND) {
+        for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
+            const int col = idx % TC;
+            const int e = idx / TC;
+            const int gcol = col0 + col;
+            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = res[col * LD + pad(e)];
+        }
+    } else {  // COL_FUSED: keep N modes, multiply by W, inverse of length N
+        C* other = (res == bufA) ? bufB : bufA;
+        for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
+            const int col = idx % TC;
+            const int kp = idx / TC;
+            const int gcol = col0 + col;
+            C v = zero;
+            if (gcol < ncols) {
+                const int pos = kp < hN ? kp : kp - LENI + LENF;
+                v = cmul(res[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
+            }
+            other[col * LD + pad(kp)] = v;
+        }
+        __syncthreads();
+        C* res2 = fft_lines<C, LENI, true>(other, res, TC, LD, twI);
+        for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
+            const int col = idx % TC;
+            const int e = idx / TC;
+            const int gcol = col0 + col;
+            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = res2[col * LD + pad(e)];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int LEN, int MODE>
+static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    const size_t smem = (size_t)(2 * TR * line_pitch(LEN) + LEN) * sizeof(C);
+    auto kern = k_rows<T, LEN, MODE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const int nb = (a.nrows + TR - 1) / TR;
+    if (nparts) *nparts = nb;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    kern<<<dim3(nb, batch), 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int LENF, int LENI, int MODE>
+static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LENF>();
+    const size_t smem = (size_t)(2 * TC * line_pitch(LENF) + LENF + LENI) * sizeof(C);
+    auto kern = k_cols<T, LENF, LENI, MODE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
+    kern<<<dim3(nb, a.nouter, batch), 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rows_t(int mode, const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    const int len = (mode == ROW_FWD || mode == ROW_EXPAND) ? a.n : a.N;
+#define SD_ROW_CASE(L)                                                          \
+    case L:                                                                     \
+        switch (mode) {                                                         \
+            case ROW_FWD: return rows_impl<T, L, ROW_FWD>(a, batch, nparts, st);   \
+            case ROW_INV_ARGMAX: return rows_impl<T, L, ROW_INV_ARGMAX>(a, batch, nparts, st); \
+            case ROW_INV_MAP: return rows_impl<T, L, ROW_INV_MAP>(a, batch, nparts, st); \
+            case ROW_EXPAND: return rows_impl<T, L, ROW_EXPAND>(a, batch, nparts, st); \
+        }                                                                       \
+        break;
+    switch (len) { SD_FOR_EACH_LEN(SD_ROW_CASE) }
+#undef SD_ROW_CASE
+    return cudaErrorInvalidValue;
+}
+
+// n = 2N pairs for the fused pass
+template <typename T>
+cudaError_t launch_cols_t(int mode, const ColArgs<T>& a, int batch, cudaStream_t st) {
+    if (mode == COL_FUSED) {
+        switch (a.N) {
+#define SD_FUSED_CASE(NN) \
+    case NN: return cols_impl<T, 2 * NN, NN, COL_FUSED>(a, batch, st);
+            SD_FUSED_CASE(8) SD_FUSED_CASE(16) SD_FUSED_CASE(24) SD_FUSED_CASE(32) SD_FUSED_CASE(48)
+            SD_FUSED_CASE(64) SD_FUSED_CASE(96) SD_FUSED_CASE(128) SD_FUSED_CASE(192) SD_FUSED_CASE(256)
+#undef SD_FUSED_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
+    const int len = (mode == COL_INV) ? a.N : a.n;
+#define SD_COL_CASE(L)                                                       \
+    case L:                                                                  \
+        switch (mode) {                                                      \
+            case COL_FWD: return cols_impl<T, L, L, COL_FWD>(a, batch, st);      \
+            case COL_INV: return cols_impl<T, L, L, COL_INV>(a, batch, st);      \
+            case COL_EXPAND: return cols_impl<T, L, L, COL_EXPAND>(a, batch, st); \
+        }                                                                    \
+        break;
+    switch (len) { SD_FOR_EACH_LEN(SD_COL_CASE) }
+#undef SD_COL_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st) {
+    if (a.m == 0 || batch == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((a.m + 255) / 256), batch);
+#define SD_SPREAD_CASE(WW)                                                       \
+    case WW:                                                                     \
+        if (dim == 2) k_spread<T, 2, WW><<<grid, 256, 0, st>>>(a);                \
+        else k_spread<T, 3, WW><<<grid, 256, 0, st>>>(a);                         \
+        return cudaGetLastError();
+    switch (a.w) {
+        SD_SPREAD_CASE(4) SD_SPREAD_CASE(5) SD_SPREAD_CASE(6) SD_SPREAD_CASE(7) SD_SPREAD_CASE(8)
+        SD_SPREAD_CASE(10) SD_SPREAD_CASE(12) SD_SPREAD_CASE(16)
+    }
+#undef SD_SPREAD_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_twiddles(cplx<T>* tw, int len) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)len, &s, &c);
+    tw[j] = mk(T(c), T(s));
+}
+
+template <typename T>
+__global__ void k_wtable(const cplx<T>* B1, const double* D, int N, int dim, double L, double sigma_g,
+                         int shift, int deriv, cplx<T>* W) {
+    const int64_t tot = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tot) return;
+    int kp[3];
+    int64_t r = i;
+    for (int d = 0; d < dim; ++d) {
+        kp[d] = (int)(r % N);
+        r /= N;
+    }
+    const int hN = N >> 1;
+    double k2 = 0.0, prodD = 1.0, kd = 0.0;
+    int ksum = 0;
+    bool nyq = false;
+    for (int d = 0; d < dim; ++d) {
+        const int kap = kp[d] < hN ? kp[d] : kp[d] - N;
+        if (kap == -hN) nyq = true;
+        const double k = 2.0 * M_PI * (double)kap / L;
+        k2 += k * k;
+        prodD *= D[kp[d]];
+        ksum += kap;
+        if (d == deriv) kd = k;
+    }
+    if (nyq) {
+        W[i] = mk(T(0), T(0));
+        return;
+    }
+    double Ld = L * L;
+    if (dim == 3) Ld *= L;
+    double f = exp(-sigma_g * sigma_g * k2) / (Ld * prodD * prodD);
+    if (shift && (ksum & 1)) f = -f;
+    const double br = (double)B1[i].x, bi = (double)B1[i].y;
+    double vr = f * br, vi = f * bi;
+    if (deriv >= 0) {  // times i k
+        const double tr = -vi * kd, ti = vr * kd;
+        vr = tr;
+        vi = ti;
+    }
+    W[i] = mk(T(vr), T(vi));
+}
+
+template <typename T>
+__global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cells) dst[4 * i + f] = src[i];
+}
+
+template <typename T>
+cudaError_t launch_twiddles_t(cplx<T>* tw, int len, cudaStream_t st) {
+    k_twiddles<T><<<(len + 255) / 256, 256, 0, st>>>(tw, len);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_wtable_t(const cplx<T>* B1, const double* D, int N, int dim, double L, double sigma_g,
+                            int shift, int deriv, cplx<T>* W, cudaStream_t st) {
+    const int64_t tot = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    k_wtable<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(B1, D, N, dim, L, sigma_g, shift, deriv, W);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f, cudaStream_t st) {
+    k_interleave<T><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(src, dst, cells, f);
+    return cudaGetLastError();
+}
+
+}  // namespace sd
+
+#define SD_INSTANTIATE_NUFFT(T)                                                                         \
+    namespace sd {                                                                                      \
+    template <> cudaError_t launch_spread<T>(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st) { \
+        return launch_spread_t<T>(a, dim, batch, st);                                                   \
+    }                                                                                                   \
+    template <> cudaError_t launch_rows<T>(int mode, const RowArgs<T>& a, int batch, int* np, cudaStream_t st) { \
+        return launch_rows_t<T>(mode, a, batch, np, st);                                                \
+    }                                                                                                   \
+    template <> cudaError_t launch_cols<T>(int mode, const ColArgs<T>& a, int batch, cudaStream_t st) {   \
+        return launch_cols_t<T>(mode, a, batch, st);                                                    \
+    }                                                                                                   \
+    template <> cudaError_t launch_twiddles<T>(cplx<T>* tw, int len, cudaStream_t st) {                 \
+        return launch_twiddles_t<T>(tw, len, st);                                                       \
+    }                                                                                                   \
+    template <> cudaError_t launch_wtable<T>(const cplx<T>* B1, const double* D, int N, int dim, double L, \
+                                             double sg, int shift, int deriv, cplx<T>* W, cudaStream_t st) { \
+        return launch_wtable_t<T>(B1, D, N, dim, L, sg, shift, deriv, W, st);                           \
+    }                                                                                                   \
+    template <> cudaError_t launch_interleave<T>(const cplx<T>* s, cplx<T>* d, int64_t c, int f, cudaStream_t st) { \
+        return launch_interleave_t<T>(s, d, c, f, st);                                                  \
+    }                                                                                                   \
+    }

@@ -1,0 +1,248 @@
+// Search over the per-rotation maxima (the argmax over T of Section 4) and the
+// FP64 re-score of the best poses.
+//
+// top-k: one CTA selects k candidates in order (score descending, rotation
+// ascending, translation index ascending), k rounds of a block-wide arg-best
+// over the candidates not yet taken (flags in a bitset).
+// re-score: f_c(R, t) = sum_ij c1_i c2_j G_{sigma_g sqrt 2}(R p2_j + t - p1_i) in
+// FP64 (the continuous score of Eq. 8 for Gaussian-represented SDFs).  Pairs
+// are screened in FP32 against a cutoff of 8 sigma_g sqrt 2 (with a margin), and
+// CTA / tile bounding boxes skip whole blocks of far pairs.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace sd {
+
+struct Cand {
+    double score;
+    int32_t rot;
+    int32_t idx;
+};
+
+__device__ __forceinline__ bool cand_better(double s, int r, int i, int64_t p, double s2, int r2, int i2, int64_t p2) {
+    if (s != s2) return s > s2;
+    if (r != r2) return r < r2;
+    if (i != i2) return i < i2;
+    return p < p2;
+}
+
+__global__ void __launch_bounds__(1024) k_topk(const Cand* cand, int64_t n, int k, Cand* out, unsigned* flags) {
+    const int64_t nw = (n + 31) / 32;
+    for (int64_t i = threadIdx.x; i < nw; i += blockDim.x) flags[i] = 0u;
+    __syncthreads();
+    __shared__ double ws[32];
+    __shared__ int wr[32], wi[32];
+    __shared__ long long wp[32];
+    for (int it = 0; it < k; ++it) {
+        double bs = -INFINITY;
+        int br = INT_MAX, bi = INT_MAX;
+        long long bp = LLONG_MAX;
+        for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+            if (flags[p >> 5] & (1u << (p & 31))) continue;
+            const Cand c = cand[p];
+            const double s = (c.score == c.score) ? c.score : -INFINITY;  // NaN ranks last
+            if (bp == LLONG_MAX || cand_better(s, c.rot, c.idx, p, bs, br, bi, bp)) {
+                bs = s; br = c.rot; bi = c.idx; bp = p;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double os = __shfl_down_sync(0xffffffffu, bs, off);
+            const int orr = __shfl_down_sync(0xffffffffu, br, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            const long long op = __shfl_down_sync(0xffffffffu, bp, off);
+            if (op != LLONG_MAX && (bp == LLONG_MAX || cand_better(os, orr, oi, op, bs, br, bi, bp))) {
+                bs = os; br = orr; bi = oi; bp = op;
+            }
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { ws[warp] = bs; wr[warp] = br; wi[warp] = bi; wp[warp] = bp; }
+        __syncthreads();
+        if (warp == 0) {
+            const int nwarp = (blockDim.x + 31) >> 5;
+            bs = lane < nwarp ? ws[lane] : -INFINITY;
+            br = lane < nwarp ? wr[lane] : INT_MAX;
+            bi = lane < nwarp ? wi[lane] : INT_MAX;
+            bp = lane < nwarp ? wp[lane] : LLONG_MAX;
+            for (int off = 16; off > 0; off >>= 1) {
+                const double os = __shfl_down_sync(0xffffffffu, bs, off);
+                const int orr = __shfl_down_sync(0xffffffffu, br, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                const long long op = __shfl_down_sync(0xffffffffu, bp, off);
+                if (op != LLONG_MAX && (bp == LLONG_MAX || cand_better(os, orr, oi, op, bs, br, bi, bp))) {
+                    bs = os; br = orr; bi = oi; bp = op;
+                }
+            }
+            if (lane == 0) {
+                Cand c;
+                if (bp == LLONG_MAX) {
+                    c.score = -INFINITY; c.rot = -1; c.idx = -1;
+                } else {
+                    c = cand[bp];
+                    flags[bp >> 5] |= (1u << (bp & 31));
+                }
+                out[it] = c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_topk(const void* cand, int64_t n, int k, void* out, unsigned* flags, cudaStream_t st) {
+    k_topk<<<1, 1024, 0, st>>>(reinterpret_cast<const Cand*>(cand), n, k, reinterpret_cast<Cand*>(out), flags);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+
+constexpr int RS_TILE = 256;
+constexpr int RS_WARPS = RS_TILE / 32;
+
+// Block-wide bounding box of one point per thread (dead threads pass +inf/-inf).
+__device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float (*wlo)[3], float (*whi)[3],
+                                           float out_lo[3], float out_hi[3]) {
+    for (int d = 0; d < 3; ++d)
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[d] = fminf(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
+            hi[d] = fmaxf(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int d = 0; d < 3; ++d) { wlo[warp][d] = lo[d]; whi[warp][d] = hi[d]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) {
+            float a = FLT_MAX, b = -FLT_MAX;
+            for (int w = 0; w < RS_WARPS; ++w) { a = fminf(a, wlo[w][d]); b = fmaxf(b, whi[w][d]); }
+            out_lo[d] = a;
+            out_hi[d] = b;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
+    __shared__ double yx[RS_TILE], yy[RS_TILE], yz[RS_TILE], cr[RS_TILE], ci[RS_TILE];
+    __shared__ float fx[RS_TILE], fy[RS_TILE], fz[RS_TILE];
+    __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
+    __shared__ float blo[3], bhi[3], tlo[3], thi[3];
+    __shared__ double Rm[9], tv[3];
+    __shared__ int skip;
+    const int pose = blockIdx.y;
+    const Cand cd = reinterpret_cast<const Cand*>(a.top)[pose];
+    if (cd.rot < 0) return;  // uniform over the block
+    const double h = a.L / a.N;
+    if (threadIdx.x == 0) {
+        int idx = cd.idx < 0 ? 0 : cd.idx;
+        for (int d = 0; d < 3; ++d) {
+            if (d < a.dim) {
+                tv[d] = (double)(idx % a.N - a.N / 2) * h;
+                idx /= a.N;
+            } else {
+                tv[d] = 0.0;
+            }
+        }
+        const double* q = a.quats + 4 * (int64_t)cd.rot;
+        const double w = q[0], x = q[1], y = q[2], z = q[3];
+        const double n2 = w * w + x * x + y * y + z * z;
+        const double s = n2 > 0 ? 2.0 / n2 : 0.0;
+        Rm[0] = 1 - s * (y * y + z * z); Rm[1] = s * (x * y - w * z); Rm[2] = s * (x * z + w * y);
+        Rm[3] = s * (x * y + w * z); Rm[4] = 1 - s * (x * x + z * z); Rm[5] = s * (y * z - w * x);
+        Rm[6] = s * (x * z - w * y); Rm[7] = s * (y * z + w * x); Rm[8] = 1 - s * (x * x + y * y);
+    }
+    const double sg2 = 2.0 * a.sigma_g * a.sigma_g;  // (sigma_g sqrt 2)^2
+    const double cut = 8.0 * sqrt(sg2);
+    const float cut2f = (float)(cut * cut) * 1.001f;
+    const double norm = (a.dim == 3) ? pow(2.0 * M_PI * sg2, -1.5) : 1.0 / (2.0 * M_PI * sg2);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < a.m1;
+    double px = 0, py = 0, pz = 0, ar = 0, ai = 0;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (live) {
+        const vec4<T> p = a.p1[i];
+        px = p.x; py = p.y; pz = (a.dim == 3) ? (double)p.z : 0.0;
+        ar = a.c1[i].x; ai = a.c1[i].y;
+        lo[0] = hi[0] = (float)px; lo[1] = hi[1] = (float)py; lo[2] = hi[2] = (float)pz;
+    }
+    block_bbox(lo, hi, wlo, whi, blo, bhi);
+    // the moving shape lies in a ball of radius sqrt(r2max) around t
+    if (threadIdx.x == 0) {
+        double dd = 0.0;
+        for (int d = 0; d < a.dim; ++d) {
+            const double c = tv[d];
+            const double e = c < blo[d] ? blo[d] - c : (c > bhi[d] ? c - bhi[d] : 0.0);
+            dd += e * e;
+        }
+        const double reach = sqrt(a.r2max) * (1.0 + 1e-5) + cut * (1.0 + 1e-4) + 1e-6;
+        skip = dd > reach * reach;
+    }
+    __syncthreads();
+    if (skip) return;
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    double sr = 0.0, si = 0.0;
+    for (int64_t j0 = 0; j0 < a.m2; j0 += RS_TILE) {
+        const int64_t j = j0 + threadIdx.x;
+        float ylo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, yhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        if (j < a.m2) {
+            const vec4<T> p = a.p2[j];
+            const double qx = p.x, qy = p.y, qz = (a.dim == 3) ? (double)p.z : 0.0;
+            const double vx = Rm[0] * qx + Rm[1] * qy + Rm[2] * qz + tv[0];
+            const double vy = Rm[3] * qx + Rm[4] * qy + Rm[5] * qz + tv[1];
+            const double vz = (a.dim == 3) ? Rm[6] * qx + Rm[7] * qy + Rm[8] * qz + tv[2] : 0.0;
+            yx[threadIdx.x] = vx; yy[threadIdx.x] = vy; yz[threadIdx.x] = vz;
+            fx[threadIdx.x] = (float)vx; fy[threadIdx.x] = (float)vy; fz[threadIdx.x] = (float)vz;
+            cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
+            ylo[0] = yhi[0] = (float)vx; ylo[1] = yhi[1] = (float)vy; ylo[2] = yhi[2] = (float)vz;
+        }
+        block_bbox(ylo, yhi, wlo, whi, tlo, thi);
+        if (threadIdx.x == 0) {
+            double dd = 0.0;
+            for (int d = 0; d < a.dim; ++d) {
+                const double g = fmax(0.0, fmax((double)tlo[d] - bhi[d], (double)blo[d] - thi[d]));
+                dd += g * g;
+            }
+            const double c2 = cut * (1.0 + 1e-4) + 1e-5 * (1.0 + fabs(tv[0]) + fabs(tv[1]) + fabs(tv[2]));
+            skip = dd > c2 * c2;
+        }
+        __syncthreads();
+        if (!skip && live) {
+            const int cnt = (int)min((int64_t)RS_TILE, a.m2 - j0);
+            for (int k = 0; k < cnt; ++k) {
+                const float dxf = fx[k] - pxf, dyf = fy[k] - pyf, dzf = fz[k] - pzf;
+                const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                if (d2f > cut2f) continue;
+                const double dx = yx[k] - px, dy = yy[k] - py, dz = yz[k] - pz;
+                const double g = norm * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
+                const double br = cr[k] * g, bi = ci[k] * g;
+                sr += ar * br - ai * bi;
+                si += ar * bi + ai * br;
+            }
+        }
+        __syncthreads();
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, off);
+        si += __shfl_down_sync(0xffffffffu, si, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.out + 2 * pose, sr);
+        atomicAdd(a.out + 2 * pose + 1, si);
+    }
+}
+
+template <typename T>
+cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(a.out, 0, sizeof(double) * 2 * (a.k > 0 ? a.k : 1), st);
+    if (e != cudaSuccess || a.k == 0 || a.m1 == 0 || a.m2 == 0) return e;
+    const dim3 grid((unsigned)((a.m1 + RS_TILE - 1) / RS_TILE), a.k);
+    k_rescore<T><<<grid, RS_TILE, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_rescore<float>(const RescoreArgs<float>&, cudaStream_t);
+template cudaError_t launch_rescore<double>(const RescoreArgs<double>&, cudaStream_t);
+
+}  // namespace sd

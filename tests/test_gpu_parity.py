@@ -1,0 +1,341 @@
+"""CUDA path (through the C ABI) against the CPU FP64 oracle, element by element.
+
+Tolerances (max-norm relative error, max |gpu - oracle| / max |oracle|):
+* FP32 path: 1e-4 for SDF values, score maps, scores and gradients.
+* FP64 path: 1e-9 for SDF values; 2e-5 for maps and gradients, where the
+  exponential-of-semicircle kernel of width 6 bounds the nonuniform FFT at ~2e-6.
+Top-1 poses must be identical wherever the oracle's best and second-best scores
+differ by more than 1e-4 of the map's maximum.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import cplx_to_pairs, oracle_maps, oracle_weights, rel_err, synthetic_weights
+from oracle import score as oscore
+from oracle import sdf as osdf
+from paper_1712_00238_gb300 import sdfdock as sd
+from synth import configs, rotations
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "f64": 2e-5}
+
+
+def make_ctx(w, precision=None, **kw):
+    prm = dict(lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps, sigma_g=w.sigma_g, w=w.w)
+    prm.update(kw)
+    return sd.Context(w.dim, precision or w.precision, 0, **prm)
+
+
+def gpu_shape(ctx, s, return_rho=False):
+    b, q = s.boundary, s.query
+    return ctx.sdf_build(b.pos, b.normal, b.area, q.pos, q.vol, return_rho=return_rho)
+
+
+def quats_dev(q):
+    return torch.as_tensor(np.asarray(q, float), dtype=torch.float64, device="cuda").contiguous()
+
+
+def grid_of(w, N=None):
+    return sd.Grid(N or w.N, w.L)
+
+
+def top1_margin_ok(ref_map):
+    flat = np.sort(np.asarray(ref_map).ravel())[::-1]
+    return flat[0] - flat[1] > 1e-4 * np.abs(flat).max()
+
+
+# ---------------------------------------------------------------------------
+# SDF (Eq. 10A-17t)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,prec,eps", [("tiny_2d", "f64", 1.5), ("tiny_2d", "f32", 1.5),
+                                           ("tiny_3d", "f32", 1.5), ("tiny_3d", "f64", 1.5),
+                                           ("tiny_3d", "f64", math.inf)])
+def test_sdf_values_match_oracle(name, prec, eps):
+    w = getattr(configs, name)()
+    ctx = make_ctx(w, prec, eps=eps)
+    for s in (w.fixed, w.moving):
+        shape, rho = gpu_shape(ctx, s, return_rho=True)
+        got = rho.cpu().numpy()
+        got = got[:, 0] + 1j * got[:, 1]
+        b = s.boundary
+        ref = osdf.sdf_rho(s.query.pos, b.pos, b.normal, b.area, w.lam1, w.lam2, w.sigma_t, eps)
+        tol = 1e-9 if prec == "f64" else 1e-4
+        assert rel_err(got, ref) < tol
+        assert shape.m == s.query.m
+        assert abs(shape.radius - np.linalg.norm(s.query.pos, axis=1).max()) < 1e-5 * shape.radius
+    ctx.close()
+
+
+def test_sdf_full_size_sampled_points():
+    # 3D peg-in-bore shapes at full size (20,000 boundary samples, ~50,000 query
+    # points); the oracle evaluates a seeded sample of the query points.
+    w = configs.peg_in_bore_3d()
+    ctx = make_ctx(w)
+    rng = np.random.default_rng(0)
+    for s in (w.fixed, w.moving):
+        _, rho = gpu_shape(ctx, s, return_rho=True)
+        got = rho.cpu().numpy()
+        sel = rng.choice(s.query.m, 300, replace=False)
+        b = s.boundary
+        ref = osdf.sdf_rho(s.query.pos[sel], b.pos, b.normal, b.area, **w.sdf_params())
+        assert rel_err(got[sel, 0] + 1j * got[sel, 1], ref) < 1e-4
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# score maps and per-rotation argmax
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,prec,N", [("tiny_2d", "f64", 32), ("tiny_2d", "f32", 48), ("tiny_3d", "f32", 16),
+                                         ("tiny_3d", "f32", 24), ("tiny_3d", "f64", 32)])
+def test_maps_match_oracle_all_rotations(name, prec, N):
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], ref[r]) < TOL[prec], r
+    cand = ctx.score_rotations(fx, mv, q, g)
+    s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(cand))
+    assert np.array_equal(rot, np.arange(w.n_rot))
+    for r in range(w.n_rot):
+        # the argmax pass and the map pass run the same transforms
+        assert idx[r] == int(np.argmax(maps[r].real))
+        assert s[r] == maps[r].real.max() if prec == "f64" else abs(s[r] - maps[r].real.max()) <= 1e-6 * abs(s[r])
+        if top1_margin_ok(ref[r].real):
+            assert idx[r] == int(np.argmax(ref[r].real))
+    ctx.close()
+
+
+def test_maps_full_size_peg_in_bore():
+    # 128^3 translations, n = 256 oversampled grid, ~50,000 samples per shape;
+    # weights are seeded synthetic values shared by both sides.
+    w = configs.peg_in_bore_3d()
+    p1, p2 = w.fixed.query.pos, w.moving.query.pos
+    c1 = synthetic_weights(len(p1), 1) * 1e-3
+    c2 = synthetic_weights(len(p2), 2) * 1e-3
+    ctx = make_ctx(w)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    sel = [0, 137, 402]
+    q = quats_dev(w.quats[sel])
+    maps = ctx.score_maps(fx, mv, q, grid_of(w)).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats[sel], w.N, w.L, w.sigma_g)
+    for r in range(len(sel)):
+        assert rel_err(maps[r], ref[r]) < 1e-4
+        if top1_margin_ok(ref[r].real):
+            assert int(np.argmax(maps[r].real)) == int(np.argmax(ref[r].real))
+    ctx.close()
+
+
+def test_end_to_end_peg_in_hole_2d_fp64():
+    # boundary samples -> SDF -> 64 rotations x 128^2 translations, FP64
+    w = configs.peg_in_hole_2d()
+    ctx = make_ctx(w)
+    fx = gpu_shape(ctx, w.fixed)
+    mv = gpu_shape(ctx, w.moving)
+    q = quats_dev(w.quats)
+    g = grid_of(w)
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    p1, c1, p2, c2 = oracle_weights("peg_in_hole_2d")
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, w.N, w.L, w.sigma_g)
+    assert max(rel_err(maps[r], ref[r]) for r in range(w.n_rot)) < TOL["f64"]
+    cand = ctx.score_rotations(fx, mv, q, g)
+    poses = ctx.top_k_poses(cand, 4, fx, mv, q, g, rescore_fp64=True)
+    best_r = [oscore.rotation_best(m.real) for m in ref]
+    ref_top = oscore.global_top_k([b[0] for b in best_r], [b[1] for b in best_r], 4)
+    assert [(p["rot"], p["idx"]) for p in poses] == [(r, i) for r, _, i in ref_top]
+    assert poses[0]["rot"] % 16 == 0 and np.allclose(poses[0]["t"], 0.0)
+    for p, (r, _, i) in zip(poses, ref_top):
+        t = oscore.translation_of_index(i, w.N, w.L, 2)
+        fc = oscore.pair_score_fc(p1, c1, p2, c2, w.quats[r], t, w.sigma_g)
+        assert abs(p["score_fp64"] - fc.real) < 1e-9 * abs(fc)
+    ctx.close()
+
+
+def test_batching_graph_and_plain_paths_agree():
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w)
+    ref = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    base = sd.decode_cands(ctx.score_rotations(fx, mv, q, g))
+    outs = []
+    for opt in ({"batch": 5}, {"plain": 1}, {"batch": 4, "graph": 1}):
+        for k, v in opt.items():
+            ctx.set_option(k, v)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for _ in range(3):   # eager, then captured, then replayed
+                cand = ctx.score_rotations(fx, mv, q, g)
+        st.synchronize()
+        outs.append(sd.decode_cands(cand))
+        for k in opt:
+            ctx.set_option(k, 0)
+    for s, rot, idx in outs:
+        assert torch.equal(rot, base[1])
+        assert (s - base[0]).abs().max().item() <= 1e-5 * np.abs(ref.real).max()
+        for r in range(w.n_rot):
+            if top1_margin_ok(ref[r].real):
+                assert idx[r].item() == base[2][r].item()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# top-k and FP64 re-score
+# ---------------------------------------------------------------------------
+
+def test_top_k_and_fp64_rescore_tiny_3d():
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w)
+    poses = ctx.top_k_poses(ctx.score_rotations(fx, mv, q, g), 3, fx, mv, q, g)
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, w.N, w.L, w.sigma_g)
+    best = [oscore.rotation_best(m.real) for m in ref]
+    ref_top = oscore.global_top_k([b[0] for b in best], [b[1] for b in best], 3)
+    scale = max(abs(b[0]) for b in best)
+    for p, (r, sc, i) in zip(poses, ref_top):
+        assert abs(p["score"] - sc) < 1e-4 * scale
+    gaps = np.diff([-x[1] for x in ref_top])
+    if np.all(gaps > 1e-4 * scale):
+        assert [(p["rot"], p["idx"]) for p in poses] == [(r, i) for r, _, i in ref_top]
+        for p, (r, _, i) in zip(poses, ref_top):
+            t = oscore.translation_of_index(i, w.N, w.L, 3)
+            fc = oscore.pair_score_fc(p1, c1, p2, c2, w.quats[r], t, w.sigma_g)
+            assert abs(p["score_fp64"] - fc.real) < 1e-9 * abs(fc)
+            assert abs(p["score_fp64_im"] - fc.imag) < 1e-9 * abs(fc)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# score and gradient at arbitrary poses (type-2 gather)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,prec,N", [("tiny_3d", "f32", 16), ("tiny_3d", "f64", 24), ("tiny_2d", "f64", 32),
+                                         ("tiny_2d", "f32", 32)])
+def test_score_grad_matches_oracle(name, prec, N):
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    P = 6
+    if w.dim == 3:
+        qs = rotations.random_uniform(P, 11)
+    else:
+        th = np.linspace(0.3, 5.0, P)
+        qs = np.stack([np.cos(th / 2), 0 * th, 0 * th, np.sin(th / 2)], 1)
+    qs = qs * np.linspace(0.7, 1.3, P)[:, None]          # unnormalised on purpose
+    ts = rotations.random_ball(P, 1.0, 12, 3)
+    if w.dim == 2:
+        ts[:, 2] = 0
+    real = torch.float64 if prec == "f64" else torch.float32
+    s, dq, dt = ctx.score_grad(fx, mv, grid_of(w, N), torch.tensor(qs, dtype=real, device="cuda"),
+                               torch.tensor(ts, dtype=real, device="cuda"))
+    s, dq, dt = s.cpu().numpy(), dq.cpu().numpy(), dt.cpu().numpy()
+    ref = [oscore.pair_grad_fN(p1, c1, p2, c2, qs[i], ts[i, : w.dim], N, w.L, w.sigma_g) for i in range(P)]
+    fs = np.array([r[0] for r in ref])
+    rdt = np.array([r[1] for r in ref])
+    rdq = np.array([r[2] for r in ref])
+    tol = TOL[prec]
+    assert rel_err(s, fs) < tol
+    assert rel_err(dt, rdt) < tol
+    assert rel_err(dq, rdq) < tol
+    assert np.abs((dq * qs).sum(1)).max() < 1e-4 * np.abs(dq).max()
+    ctx.close()
+
+
+def test_score_grad_equals_map_on_grid_points():
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w, "f64")
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    g = grid_of(w, 16)
+    q = quats_dev(w.quats[:2])
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    idx = np.array([0, 77, 1000, 4095])
+    qs = np.repeat(w.quats[:2], len(idx), 0)
+    ts = np.array([oscore.translation_of_index(int(i), 16, w.L, 3) for i in idx] * 2)
+    s, _, _ = ctx.score_grad(fx, mv, g, torch.tensor(qs, device="cuda"), torch.tensor(ts, device="cuda"))
+    want = np.concatenate([maps[0].real[idx], maps[1].real[idx]])
+    assert np.abs(s.cpu().numpy() - want).max() < 2e-5 * np.abs(maps.real).max()
+    ctx.close()
+
+
+def test_autograd_function_and_refinement():
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w, "f64")
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    g = grid_of(w, 16)
+    q = torch.tensor(rotations.random_uniform(3, 5), device="cuda", requires_grad=True)
+    t = torch.tensor(rotations.random_ball(3, 1.0, 6, 3), device="cuda", requires_grad=True)
+    s = sd.sdf_score(ctx, fx, mv, g, q, t)
+    gq, gt = torch.autograd.grad(s.sum(), (q, t))
+    h = 1e-5
+    for a in range(3):
+        e = torch.zeros_like(t)
+        e[:, a] = h
+        fd = (ctx.score_grad(fx, mv, g, q.detach(), t.detach() + e)[0]
+              - ctx.score_grad(fx, mv, g, q.detach(), t.detach() - e)[0]) / (2 * h)
+        assert torch.allclose(fd, gt[:, a], rtol=1e-4, atol=1e-6 * gt.abs().max().item())
+    for a in range(4):
+        e = torch.zeros_like(q)
+        e[:, a] = h
+        fd = (ctx.score_grad(fx, mv, g, q.detach() + e, t.detach())[0]
+              - ctx.score_grad(fx, mv, g, q.detach() - e, t.detach())[0]) / (2 * h)
+        assert torch.allclose(fd, gq[:, a], rtol=1e-4, atol=1e-6 * gq.abs().max().item())
+    q1, t1, hist = sd.refine_poses(ctx, fx, mv, g, q.detach(), t.detach(), steps=20, lr_t=0.02, lr_q=0.01)
+    assert (hist[-1] >= hist[0]).all()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+
+def test_argument_errors_are_reported():
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    with pytest.raises(sd.SdError) as e:
+        ctx.score_rotations(fx, mv, q, sd.Grid(100, w.L))
+    assert e.value.code == sd.SD_ERR_ARG
+    with pytest.raises(sd.SdError) as e:
+        ctx.score_rotations(fx, mv, q, grid_of(w), k_r=2)
+    assert e.value.code == sd.SD_ERR_UNIMPLEMENTED
+    with pytest.raises(sd.SdError):
+        ctx.score_rotations(fx, mv, q, sd.Grid(32, -1.0))
+    other = make_ctx(w)
+    ofx = other.shape_from_samples(p1, cplx_to_pairs(c1))
+    with pytest.raises(sd.SdError) as e:
+        ctx.score_rotations(ofx, mv, q, grid_of(w))
+    assert "another context" in str(e.value)
+    # the context stays usable after errors
+    cand = ctx.score_rotations(fx, mv, q, grid_of(w))
+    assert torch.isfinite(sd.decode_cands(cand)[0]).all()
+    other.close()
+    ctx.close()
