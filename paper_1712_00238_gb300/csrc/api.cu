@@ -106,9 +106,18 @@ struct DeviceGuard {
 
 static size_t real_size(const sd_ctx* ctx) { return ctx->p.precision == SD_F64 ? 8 : 4; }
 
+// Captured graphs hold raw workspace and table pointers: drop them before any
+// of those buffers is freed.
+static void drop_graphs(sd_ctx* ctx) {
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graphs.clear();
+    ctx->seen.clear();
+}
+
 static int ws_get(sd_ctx* ctx, int slot, size_t bytes, void** out) {
     DevBuf& b = ctx->ws[slot];
     if (b.bytes < bytes) {
+        drop_graphs(ctx);
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
         b.bytes = 0;
@@ -688,7 +697,7 @@ int sd_destroy(sd_ctx* ctx) {
         if (b.p) cudaFree(b.p);
     for (auto& kv : ctx->twiddles) cudaFree(kv.second);
     for (auto& kv : ctx->deconv) cudaFree(kv.second);
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    drop_graphs(ctx);
     if (ctx->gl_x) cudaFree(ctx->gl_x);
     if (ctx->gl_w) cudaFree(ctx->gl_w);
     delete ctx;
@@ -839,6 +848,7 @@ int sd_shape_info(const sd_shape* s, int64_t* m, double* radius) {
 int sd_shape_free(sd_shape* s) {
     if (!s) return SD_OK;
     DeviceGuard dg(s->ctx ? s->ctx->device : 0);
+    if (s->ctx) drop_graphs(s->ctx);
     if (s->pos) cudaFree(s->pos);
     if (s->c) cudaFree(s->c);
     for (auto& p : s->preps) {
