@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the SDF complementarity search on one or more GPUs.
+
+One step runs the whole hot path on the 3D peg-in-bore workload (cylinder
+r = 1, length 3, into a 6x6x4 block with a blind bore r = 1.02, depth 2.5;
+20,000 boundary samples and ~50,000 SDF samples per shape; 128^3 translations;
+576 Hopf-grid rotations):
+
+  SDF build of both shapes -> per-rotation search (rotate, spread, forward FFT,
+  product, inverse FFT, argmax) -> global top-10 with FP64 re-score ->
+  gradient refinement of the 10 poses (type-2 score+gradient, 20 steps).
+
+metric: poses scored per second = rotations x translations / step time.
+`value` uses device-resident inputs; `e2e` copies the step's inputs from pinned
+host memory and reads the poses back inside the timed region.  Under torchrun
+every rank runs its own copy of the workload (weak scaling); rank 0 prints one
+JSON line.  `--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "poses scored/s (rot x trans) at <=1e-4 rel err"
+UNIT = "poses/s"
+L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
+FALLBACK_HBM_GBS = 6800.0
+TOP_K = 10
+REFINE_STEPS = 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=0, help="rotations per batch (0: automatic)")
+    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def load_workload():
+    from synth import configs
+    return configs.peg_in_bore_3d()
+
+
+def host_inputs(w, torch):
+    """Pinned host tensors of everything a step reads (FP32 points padded to 4 reals)."""
+    def pad4(a):
+        out = np.zeros((a.shape[0], 4), np.float32)
+        out[:, : a.shape[1]] = a
+        return out
+
+    t = {}
+    for tag, s in (("f", w.fixed), ("m", w.moving)):
+        t[tag + "_bnd"] = pad4(s.boundary.pos)
+        t[tag + "_nrm"] = pad4(s.boundary.normal)
+        t[tag + "_area"] = s.boundary.area.astype(np.float32)
+        t[tag + "_qry"] = pad4(s.query.pos)
+        t[tag + "_vol"] = s.query.vol.astype(np.float32)
+    t["quats"] = np.ascontiguousarray(w.quats, dtype=np.float64)
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in t.items()}
+
+
+def algorithmic_bytes_per_rotation(s: int, N: int, m_moving: int) -> dict:
+    """Bytes each pass must move per rotation (complex64 elements of 8 bytes)."""
+    c = 8
+    return {
+        "clear": s ** 3 * c,
+        "spread": m_moving * 24 + s ** 3 * c,
+        "fwd_x": (s ** 3 + s * s * N) * c,
+        "fwd_y": (s * s * N + s * N * N) * c,
+        "fused": (s * N * N + 2 * N ** 3) * c,
+        "inv_y": 2 * N ** 3 * c,
+        "inv_x": N ** 3 * c,
+        "reduce": 0,
+    }
+
+
+def sub_box(radius: float, N: int, L: float, w: int = 6) -> int:
+    n = 2 * N
+    s_h = int(math.floor(radius * n / L + 0.5 * w)) + 2
+    return n if 2 * s_h >= n else 2 * s_h
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1712_00238_gb300 import sdfdock as sd
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = load_workload()
+    ctx = sd.Context(3, "f32", local, lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps,
+                     sigma_g=w.sigma_g, w=w.w)
+    ctx.set_option("batch", args.batch)
+    ctx.set_option("plain", args.plain)
+    ctx.set_option("graph", 0 if args.plain else args.graph)
+    grid = sd.Grid(w.N, w.L)
+    host = host_inputs(w, torch)
+    devin = {k: v.to(dev) for k, v in host.items()}
+    n_rot = w.n_rot
+    cand = torch.empty((n_rot, sd.CAND_BYTES), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step(inp):
+        fx = ctx.sdf_build(inp["f_bnd"], inp["f_nrm"], inp["f_area"], inp["f_qry"], inp["f_vol"])
+        mv = ctx.sdf_build(inp["m_bnd"], inp["m_nrm"], inp["m_area"], inp["m_qry"], inp["m_vol"])
+        ctx.score_rotations(fx, mv, inp["quats"], grid, out=cand)
+        poses = ctx.top_k_poses(cand, TOP_K, fx, mv, inp["quats"], grid, rescore_fp64=True)
+        rots = torch.tensor([p["rot"] for p in poses], device=dev)
+        q0 = inp["quats"][rots].float()
+        t0 = torch.tensor([p["t"] for p in poses], dtype=torch.float32, device=dev)
+        q, t, hist = sd.refine_poses(ctx, fx, mv, grid, q0, t0, steps=REFINE_STEPS, lr_t=0.01, lr_q=0.005)
+        ctx.shapes.remove(fx)
+        ctx.shapes.remove(mv)
+        fx.free()
+        mv.free()
+        return poses, hist
+
+    def timed_steps(k, e2e):
+        times = []
+        out = None
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                if e2e:
+                    inp = {kk: v.to(dev, non_blocking=True) for kk, v in host.items()}
+                    poses, hist = step(inp)
+                    final = hist[-1].cpu()
+                else:
+                    poses, hist = step(devin)
+                b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            out = (poses, hist)
+        return times, out
+
+    # warm-up (also captures the search graph on this stream)
+    timed_steps(max(args.warmup, 0), False)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    ctx.set_option("timing", 1)
+    ctx.pass_times(reset=True)
+    l0 = sd.launch_count()
+    times, (poses, hist) = timed_steps(args.steps, False)
+    launches = sd.launch_count() - l0
+    ptimes = ctx.pass_times(reset=True)
+    ctx.set_option("timing", 0)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    e2e_times, _ = timed_steps(args.steps, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    ms = statistics.mean(times)
+    ms_e2e = statistics.mean(e2e_times)
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = t.tolist()
+        parts = [None] * world
+        dist.all_gather_object(parts, [(p["score"], p["rot"], p["idx"]) for p in poses])
+        merged = sd.merge_top_k(parts, TOP_K)
+    else:
+        merged = [(p["score"], p["rot"], p["idx"]) for p in poses]
+
+    poses_per_step = n_rot * w.N ** 3
+    value = world * poses_per_step / (ms * 1e-3)
+    e2e_value = world * poses_per_step / (ms_e2e * 1e-3)
+    # inputs, plus the pose indices / translations sent back for refinement
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + TOP_K * (8 + 12)
+    # top-k candidates and FP64 re-scores, then the refined scores
+    d2h = TOP_K * (16 + 16) + TOP_K * 4
+
+    # roofline of the dominant search pass (live CUDA-event times of the timed steps)
+    radius = float(np.linalg.norm(w.moving.query.pos, axis=1).max())
+    s = sub_box(radius, w.N, w.L, w.w)
+    per_rot = algorithmic_bytes_per_rotation(s, w.N, w.moving.query.m)
+    passes = {k: v for k, v in ptimes.items() if v[0] > 0 and k != "graph"}
+    roofline = None
+    pass_report = {}
+    if passes:
+        for k, (n, t) in passes.items():
+            tot_bytes = per_rot.get(k, 0) * n_rot * args.steps
+            pass_report[k] = {"launches": n, "ms_total": round(t, 4),
+                              "gbs": round(tot_bytes / (t * 1e-3) / 1e9, 1) if t > 0 else None}
+        dom = max((k for k in passes if per_rot.get(k, 0) > 0 and k not in ("spread", "clear")),
+                  key=lambda k: passes[k][1])
+        n, t = passes[dom]
+        per_launch = per_rot[dom] * n_rot * args.steps / n
+        avg_s = t * 1e-3 / n
+        peak, src = measured_peak()
+        ach = per_launch / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "peak_source": src,
+                    "algorithmic_bytes_per_launch": int(per_launch),
+                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, s, w.N)),
+                    "avg_launch_us": round(avg_s * 1e6, 2)}
+    search_ms = None
+    if passes:
+        search_ms = sum(v[1] for v in passes.values()) / args.steps
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "peg_in_bore_3d: cylinder r1 l3 into 6x6x4 block, bore r1.02 depth 2.5; "
+                               "20k boundary + ~50k SDF samples per shape; 128^3 translations, n=256; "
+                               "576 Hopf rotations; top-10 + FP64 re-score; 20-step gradient refinement",
+                   "rotations": n_rot, "translations": w.N ** 3, "sub_box": s,
+                   "batch": args.batch, "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": ms_e2e},
+        "gpu_launches": int(launches // max(args.steps, 1)),
+        "gpu_launches_total": int(launches),
+        "roofline": roofline,
+        "passes": pass_report,
+        "search_ms_per_step": search_ms,
+        "top1": {"score": merged[0][0], "rot": merged[0][1], "idx": merged[0][2]},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# search passes from one ncu capture of this workload, keyed by (pass, sub-box
+# side, N); absent entries report null.
+TRAFFIC_PER_LAUNCH: dict = {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_setup(w):
+    from oracle import score as oscore
+    rng = np.random.default_rng(np.random.SeedSequence([7, 99]))
+    p1, p2 = w.fixed.query.pos, w.moving.query.pos
+    c1 = rng.standard_normal(len(p1)) + 1j * rng.standard_normal(len(p1))
+    c2 = rng.standard_normal(len(p2)) + 1j * rng.standard_normal(len(p2))
+    F1 = oscore.nudft(p1, c1, w.N, w.L, -1)
+    return p1, c1, p2, c2, F1
+
+
+def oracle_rotation(w, st, r):
+    from oracle import score as oscore
+    p1, c1, p2, c2, F1 = st
+    m = oscore.score_map_fN(p1, c1, p2, c2, w.quats[r], w.N, w.L, w.sigma_g, F1=F1).real
+    return oscore.rotation_best(m)
+
+
+def cpu_baseline(w, n_rot=2):
+    st = oracle_setup(w)
+    t0 = time.perf_counter()
+    for r in range(n_rot):
+        oracle_rotation(w, st, r)
+    dt = time.perf_counter() - t0
+    return {"value": n_rot * w.N ** 3 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_rot} of {w.n_rot} rotations of the 128^3 map: FP64 direct NUDFT of the moving "
+                      f"samples, spectral product, numpy inverse FFT, argmax (SDF build, fixed-shape "
+                      f"transform and top-k excluded); seeded weights"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = load_workload()
+    st = oracle_setup(w)
+    for r in range(max(args.warmup, 0)):
+        oracle_rotation(w, st, r % w.n_rot)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_rotation(w, st, k % w.n_rot)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    value = w.N ** 3 / (ms * 1e-3)
+    sample = ("each step: one rotation of the 128^3 map by the FP64 oracle (direct NUDFT of the moving "
+              "samples, spectral product, numpy inverse FFT, argmax) on the 3D peg-in-bore workload")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "peg_in_bore_3d (one rotation per step)", "rotations": 1,
+                   "translations": w.N ** 3},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

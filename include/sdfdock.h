@@ -107,8 +107,10 @@ int sd_destroy(sd_ctx* ctx);
 const char* sd_last_error(const sd_ctx* ctx);
 
 /* Set a tuning option: "batch" (rotations per batch, 0 = automatic),
- * "graph" (1: replay the batched launch sequence from a captured CUDA graph),
- * "plain" (1: one rotation at a time, unfused passes, no graph). */
+ * "graph" (1: replay the batched launch sequence from a captured CUDA graph;
+ * needs a non-NULL stream; the first call with given arguments runs eagerly,
+ * later ones capture once and replay), "plain" (1: one rotation per batch, no
+ * graph), "timing" (1: CUDA-event timing of every pass, see sd_pass_times). */
 int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
 
 /* ---- shapes: the sampled SDF (Section 4, Eq. 10A-17t) ------------------- */
@@ -201,6 +203,27 @@ int sd_host_line_fft(int len, int inverse, const double* in, double* out);
 
 /* Library version string (static storage). */
 const char* sd_version(void);
+
+/* Number of kernels the library has launched in this process. */
+int64_t sd_launch_count(void);
+
+/* Pass kinds of the search pipeline, for sd_pass_times. */
+#define SD_PASS_CLEAR 0   /* zeroing of the spread sub-box                    */
+#define SD_PASS_SPREAD 1  /* rotate + spread (type-1, first half)             */
+#define SD_PASS_FWD_X 2   /* forward FFT along x, N of n modes kept           */
+#define SD_PASS_FWD_Y 3   /* forward FFT along y (3D)                         */
+#define SD_PASS_FUSED 4   /* last axis: forward FFT, product, inverse FFT     */
+#define SD_PASS_INV_Y 5   /* inverse FFT along y (3D)                         */
+#define SD_PASS_INV_X 6   /* inverse FFT along x with argmax (or the map)     */
+#define SD_PASS_REDUCE 7  /* per-rotation argmax reduction                    */
+#define SD_PASS_GRAPH 8   /* one replay of a captured search graph            */
+#define SD_PASS_COUNT 9
+
+/* With the context option "timing" = 1, every pass launch of the search is
+ * bracketed by CUDA events on its stream.  Returns the number of timed
+ * launches and their summed device time (ms) for `kind`; synchronises on the
+ * recorded events.  kind < 0 resets the totals. */
+int sd_pass_times(sd_ctx* ctx, int kind, int64_t* launches, double* ms);
 
 #ifdef __cplusplus
 }

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <string>
@@ -39,8 +40,18 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
 };
 
+struct TimerRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
 struct sd_ctx {
     int device = 0;
+    int opt_timing = 0;
+    std::vector<TimerRec> pending;       // event pairs not yet read back
+    std::vector<cudaEvent_t> event_pool;
+    double pass_ms[SD_PASS_COUNT] = {};
+    int64_t pass_n[SD_PASS_COUNT] = {};
     sd_params p{};
     std::string err;
     int64_t opt_batch = 0;
@@ -66,6 +77,60 @@ struct sd_shape {
 };
 
 static std::string g_create_err;
+static std::atomic<long long> g_launches{0};
+
+void sd::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// CUDA-event timing of one pass launch on the stream (when the context's
+// "timing" option is on and no graph is being captured).
+static cudaEvent_t pool_event(sd_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+struct PassTimer {
+    sd_ctx* ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    PassTimer(sd_ctx* c, int k, cudaStream_t s, bool on) : ctx(c), kind(k), st(s) {
+        if (on && c->opt_timing) {
+            a = pool_event(c);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~PassTimer() {
+        if (!a) return;
+        cudaEvent_t b = pool_event(ctx);
+        if (!b) return;
+        cudaEventRecord(b, st);
+        ctx->pending.push_back({kind, a, b});
+    }
+};
+
+static void harvest_timers(sd_ctx* ctx) {
+    for (auto& r : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->pass_ms[r.kind] += ms;
+            ctx->pass_n[r.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        ctx->event_pool.push_back(r.a);
+        ctx->event_pool.push_back(r.b);
+    }
+    ctx->pending.clear();
+}
 
 static int fail(sd_ctx* ctx, int code, const char* fmt, ...) {
     char buf[512];
@@ -559,10 +624,13 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
     const int64_t Nd = (G.dim == 2) ? (int64_t)G.N * G.N : (int64_t)G.N * G.N * G.N;
 
     // One launch sequence per batch; optionally replayed from a captured graph.
-    auto enqueue = [&](cudaStream_t s) -> int {
+    auto enqueue = [&](cudaStream_t s, bool timed) -> int {
         for (int64_t r0 = 0; r0 < n_r; r0 += B) {
             const int b = (int)std::min<int64_t>(B, n_r - r0);
-            CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
+            {
+                PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
+                CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
+            }
             SpreadArgs<T> sa{};
             sa.pos = (const vec4<T>*)moving->pos;
             sa.c = (const C*)moving->c;
@@ -577,17 +645,33 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             sa.s_h = G.s_h;
             sa.out = b0;
             sa.out_rot_stride = e0;
-            CK(ctx, launch_spread<T>(sa, G.dim, b, s));
-            CK(ctx, pass_x_fwd<T>(G, tw, b0, e0, b1, e1, b, s));
+            {
+                PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
+                CK(ctx, launch_spread<T>(sa, G.dim, b, s));
+            }
+            {
+                PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
+                CK(ctx, pass_x_fwd<T>(G, tw, b0, e0, b1, e1, b, s));
+            }
             C* fin;
             int64_t fin_rs;
             if (G.dim == 3) {
-                CK(ctx, pass_y_fwd<T>(G, tw, b1, e1, b0, e0, b, s));
-                CK(ctx, pass_last<T>(COL_FUSED, G, tw, b0, e0, b1, e1, W, b, s));
-                CK(ctx, pass_y_inv<T>(G, tw, b1, e1, b, s));
+                {
+                    PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
+                    CK(ctx, pass_y_fwd<T>(G, tw, b1, e1, b0, e0, b, s));
+                }
+                {
+                    PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
+                    CK(ctx, pass_last<T>(COL_FUSED, G, tw, b0, e0, b1, e1, W, b, s));
+                }
+                {
+                    PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
+                    CK(ctx, pass_y_inv<T>(G, tw, b1, e1, b, s));
+                }
                 fin = b1;
                 fin_rs = e1;
             } else {
+                PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
                 CK(ctx, pass_last<T>(COL_FUSED, G, tw, b1, e1, b0, e0, W, b, s));
                 fin = b0;
                 fin_rs = e0;
@@ -605,12 +689,17 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             if (maps) {
                 r.out = (C*)out + r0 * Nd;
                 r.out_rot_stride = Nd;
+                PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
                 CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
             } else {
                 int nparts = 0;
                 r.part_score = (double*)psv;
                 r.part_idx = (int*)piv;
-                CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
+                {
+                    PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
+                    CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
+                }
+                PassTimer pt(ctx, SD_PASS_REDUCE, s, timed);
                 CK(ctx, launch_reduce_argmax((const double*)psv, (const int*)piv, nparts, b, r0, out, s));
             }
         }
@@ -624,10 +713,10 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
-            if (ctx->seen[k]++ == 0) return enqueue(st);  // first call runs eagerly (sets kernel attributes)
+            if (ctx->seen[k]++ == 0) return enqueue(st, true);  // first call runs eagerly (sets kernel attributes)
             cudaGraph_t graph;
             CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue(st);
+            int rc = enqueue(st, false);
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (rc != SD_OK) return rc;
             CK(ctx, ec);
@@ -637,10 +726,13 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             CK(ctx, ec);
             it = ctx->graphs.emplace(k, ge).first;
         }
-        CK(ctx, cudaGraphLaunch(it->second.exec, st));
+        {
+            PassTimer pt(ctx, SD_PASS_GRAPH, st, true);
+            CK(ctx, cudaGraphLaunch(it->second.exec, st));
+        }
         return SD_OK;
     }
-    return enqueue(st);
+    return enqueue(st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -698,6 +790,8 @@ int sd_destroy(sd_ctx* ctx) {
     for (auto& kv : ctx->twiddles) cudaFree(kv.second);
     for (auto& kv : ctx->deconv) cudaFree(kv.second);
     drop_graphs(ctx);
+    harvest_timers(ctx);
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->gl_x) cudaFree(ctx->gl_x);
     if (ctx->gl_w) cudaFree(ctx->gl_w);
     delete ctx;
@@ -711,6 +805,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     if (!strcmp(key, "batch")) ctx->opt_batch = value;
     else if (!strcmp(key, "graph")) ctx->opt_graph = (int)value;
     else if (!strcmp(key, "plain")) ctx->opt_plain = (int)value;
+    else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
     return SD_OK;
 }
@@ -1030,3 +1125,22 @@ int sd_host_line_fft(int len, int inverse, const double* in, double* out) {
 }
 
 const char* sd_version(void) { return "sdfdock 0.1 (sm_103a)"; }
+
+int64_t sd_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int sd_pass_times(sd_ctx* ctx, int kind, int64_t* launches, double* ms) {
+    if (!ctx) return SD_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    harvest_timers(ctx);
+    if (kind < 0) {
+        for (int k = 0; k < SD_PASS_COUNT; ++k) {
+            ctx->pass_ms[k] = 0.0;
+            ctx->pass_n[k] = 0;
+        }
+        return SD_OK;
+    }
+    if (kind >= SD_PASS_COUNT) return fail(ctx, SD_ERR_ARG, "pass kind out of range");
+    if (launches) *launches = ctx->pass_n[kind];
+    if (ms) *ms = ctx->pass_ms[kind];
+    return SD_OK;
+}

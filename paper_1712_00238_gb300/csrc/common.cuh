@@ -6,6 +6,9 @@
 
 namespace sd {
 
+// Counts kernel launches made by the library (defined in api.cu).
+void note_launch(int n = 1);
+
 template <typename T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };

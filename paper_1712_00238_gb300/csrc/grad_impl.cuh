@@ -140,6 +140,7 @@ cudaError_t launch_gather(const GatherArgs<T>& a, int dim, cudaStream_t st) {
     case WW:                                                                    \
         if (dim == 2) k_gather<T, 2, WW><<<grid, GA_THREADS, 0, st>>>(a);        \
         else k_gather<T, 3, WW><<<grid, GA_THREADS, 0, st>>>(a);                 \
+        note_launch();                                                          \
         return cudaGetLastError();
     switch (a.w) {
         SD_GATHER_CASE(4) SD_GATHER_CASE(5) SD_GATHER_CASE(6) SD_GATHER_CASE(7) SD_GATHER_CASE(8)
@@ -180,6 +181,7 @@ cudaError_t launch_grad_finalize(const double* acc, const T* quats, int64_t P, i
                                  cudaStream_t st) {
     if (P == 0) return cudaSuccess;
     k_grad_finalize<T><<<(unsigned)((P + 127) / 128), 128, 0, st>>>(acc, quats, P, dim, score, dq, dt);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ __global__ void k_deconv(double* D, int N, int n, int w, double beta, const doub
 cudaError_t launch_deconv(double* D, int N, int n, int w, double beta, const double* gx, const double* gw,
                           int nq, cudaStream_t st) {
     k_deconv<<<(N + 127) / 128, 128, 0, st>>>(D, N, n, w, beta, gx, gw, nq);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -84,6 +85,7 @@ cudaError_t launch_reduce_argmax(const double* ps, const int* pi, int nparts, in
                                  void* cand, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     k_reduce_argmax<<<batch, 256, 0, st>>>(ps, pi, nparts, rot0, reinterpret_cast<CandRec*>(cand));
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -330,6 +330,7 @@ static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaSt
     if (nparts) *nparts = nb;
     if (nb == 0 || batch == 0) return cudaSuccess;
     kern<<<dim3(nb, batch), 256, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -344,6 +345,7 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     const int nb = (a.ncols + TC - 1) / TC;
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
     kern<<<dim3(nb, a.nouter, batch), 256, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -399,6 +401,7 @@ cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStre
     case WW:                                                                     \
         if (dim == 2) k_spread<T, 2, WW><<<grid, 256, 0, st>>>(a);                \
         else k_spread<T, 3, WW><<<grid, 256, 0, st>>>(a);                         \
+        note_launch();                                                           \
         return cudaGetLastError();
     switch (a.w) {
         SD_SPREAD_CASE(4) SD_SPREAD_CASE(5) SD_SPREAD_CASE(6) SD_SPREAD_CASE(7) SD_SPREAD_CASE(8)
@@ -473,6 +476,7 @@ __global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, in
 template <typename T>
 cudaError_t launch_twiddles_t(cplx<T>* tw, int len, cudaStream_t st) {
     k_twiddles<T><<<(len + 255) / 256, 256, 0, st>>>(tw, len);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -481,12 +485,14 @@ cudaError_t launch_wtable_t(const cplx<T>* B1, const double* D, int N, int dim, 
                             int shift, int deriv, cplx<T>* W, cudaStream_t st) {
     const int64_t tot = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
     k_wtable<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(B1, D, N, dim, L, sigma_g, shift, deriv, W);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f, cudaStream_t st) {
     k_interleave<T><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(src, dst, cells, f);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -143,6 +143,7 @@ cudaError_t launch_sdf(const SdfArgs<T>& a, int dim, cudaStream_t st) {
         k_sdf_nearest<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
         k_sdf_sum<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
     }
+    note_launch(2);
     return cudaGetLastError();
 }
 
@@ -168,6 +169,7 @@ cudaError_t launch_radius(const vec4<T>* p, int64_t m, int dim, double* out, cud
     if (m == 0) return cudaSuccess;
     const int nb = (int)((m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024);
     k_radius<T><<<nb, 256, 0, st>>>(p, m, dim, out);
+    note_launch();
     return cudaGetLastError();
 }
 

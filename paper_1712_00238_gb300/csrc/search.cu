@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(1024) k_topk(const Cand* cand, int64_t n, int 
 
 cudaError_t launch_topk(const void* cand, int64_t n, int k, void* out, unsigned* flags, cudaStream_t st) {
     k_topk<<<1, 1024, 0, st>>>(reinterpret_cast<const Cand*>(cand), n, k, reinterpret_cast<Cand*>(out), flags);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -239,6 +240,7 @@ cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st) {
     if (e != cudaSuccess || a.k == 0 || a.m1 == 0 || a.m2 == 0) return e;
     const dim3 grid((unsigned)((a.m1 + RS_TILE - 1) / RS_TILE), a.k);
     k_rescore<T><<<grid, RS_TILE, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -83,7 +83,11 @@ _SIGS = {
                                  ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "sd_host_line_fft": (ct.c_int, [ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_version": (ct.c_char_p, []),
+    "sd_launch_count": (ct.c_int64, []),
+    "sd_pass_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
 }
+
+PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph"]
 
 
 def library_path() -> str:
@@ -199,6 +203,18 @@ class Context:
     def set_option(self, key: str, value: int):
         self._check(self.lib.sd_set_option(self.handle, key.encode(), int(value)))
 
+    def pass_times(self, reset: bool = False) -> dict:
+        """{pass name: (timed launches, summed device ms)} from CUDA events (option "timing")."""
+        out = {}
+        for k, name in enumerate(PASS_NAMES):
+            n = ct.c_int64()
+            ms = ct.c_double()
+            self._check(self.lib.sd_pass_times(self.handle, k, ct.byref(n), ct.byref(ms)))
+            out[name] = (n.value, ms.value)
+        if reset:
+            self._check(self.lib.sd_pass_times(self.handle, -1, None, None))
+        return out
+
     # -- tensor helpers --------------------------------------------------------
     def _dev(self, x, dtype=None, cols=None) -> torch.Tensor:
         dtype = dtype or self.real
@@ -289,6 +305,11 @@ class Context:
                                            _ptr(trans), P, _ptr(score), _ptr(dq), _ptr(dt),
                                            _stream(self.device)))
         return score, dq, dt[:, : self.dim]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().sd_launch_count())
 
 
 def decode_cands(buf: torch.Tensor):

@@ -109,10 +109,15 @@ def test_maps_match_oracle_all_rotations(name, prec, N):
     cand = ctx.score_rotations(fx, mv, q, g)
     s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(cand))
     assert np.array_equal(rot, np.arange(w.n_rot))
+    # the argmax pass runs the same transforms as the map pass; spreading
+    # accumulates with float atomics, so two runs agree to rounding only
+    run_tol = 1e-12 if prec == "f64" else 1e-6
     for r in range(w.n_rot):
-        # the argmax pass and the map pass run the same transforms
-        assert idx[r] == int(np.argmax(maps[r].real))
-        assert s[r] == maps[r].real.max() if prec == "f64" else abs(s[r] - maps[r].real.max()) <= 1e-6 * abs(s[r])
+        mr = maps[r].real
+        assert abs(s[r] - mr.max()) <= run_tol * np.abs(mr).max()
+        top2 = np.sort(mr)[-2:]
+        if top2[1] - top2[0] > 10 * run_tol * np.abs(mr).max():
+            assert idx[r] == int(np.argmax(mr))
         if top1_margin_ok(ref[r].real):
             assert idx[r] == int(np.argmax(ref[r].real))
     ctx.close()
@@ -220,8 +225,9 @@ def test_top_k_and_fp64_rescore_tiny_3d():
         for p, (r, _, i) in zip(poses, ref_top):
             t = oscore.translation_of_index(i, w.N, w.L, 3)
             fc = oscore.pair_score_fc(p1, c1, p2, c2, w.quats[r], t, w.sigma_g)
-            assert abs(p["score_fp64"] - fc.real) < 1e-9 * abs(fc)
-            assert abs(p["score_fp64_im"] - fc.imag) < 1e-9 * abs(fc)
+            # FP64 sums of the shape's FP32-stored positions and weights
+            assert abs(p["score_fp64"] - fc.real) < 1e-6 * abs(fc)
+            assert abs(p["score_fp64_im"] - fc.imag) < 1e-6 * abs(fc)
     ctx.close()
 
 
@@ -282,6 +288,9 @@ def test_score_grad_equals_map_on_grid_points():
 
 
 def test_autograd_function_and_refinement():
+    # backward returns the analytic gradient (checked against the oracle above);
+    # central differences of the interpolated score agree up to the derivative
+    # of the interpolation error (about 1e-3 of the largest gradient at h = 1e-3)
     w = configs.tiny_3d()
     p1, c1, p2, c2 = oracle_weights("tiny_3d")
     ctx = make_ctx(w, "f64")
@@ -292,19 +301,21 @@ def test_autograd_function_and_refinement():
     t = torch.tensor(rotations.random_ball(3, 1.0, 6, 3), device="cuda", requires_grad=True)
     s = sd.sdf_score(ctx, fx, mv, g, q, t)
     gq, gt = torch.autograd.grad(s.sum(), (q, t))
-    h = 1e-5
+    s2, dq2, dt2 = ctx.score_grad(fx, mv, g, q.detach(), t.detach())
+    assert torch.equal(s, s2) and torch.equal(gq, dq2) and torch.equal(gt, dt2)
+    h = 1e-3
     for a in range(3):
         e = torch.zeros_like(t)
         e[:, a] = h
         fd = (ctx.score_grad(fx, mv, g, q.detach(), t.detach() + e)[0]
               - ctx.score_grad(fx, mv, g, q.detach(), t.detach() - e)[0]) / (2 * h)
-        assert torch.allclose(fd, gt[:, a], rtol=1e-4, atol=1e-6 * gt.abs().max().item())
+        assert (fd - gt[:, a]).abs().max().item() < 2e-3 * gt.abs().max().item()
     for a in range(4):
         e = torch.zeros_like(q)
         e[:, a] = h
         fd = (ctx.score_grad(fx, mv, g, q.detach() + e, t.detach())[0]
               - ctx.score_grad(fx, mv, g, q.detach() - e, t.detach())[0]) / (2 * h)
-        assert torch.allclose(fd, gq[:, a], rtol=1e-4, atol=1e-6 * gq.abs().max().item())
+        assert (fd - gq[:, a]).abs().max().item() < 2e-3 * gq.abs().max().item()
     q1, t1, hist = sd.refine_poses(ctx, fx, mv, g, q.detach(), t.detach(), steps=20, lr_t=0.02, lr_q=0.01)
     assert (hist[-1] >= hist[0]).all()
     ctx.close()
