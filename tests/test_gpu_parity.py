@@ -302,7 +302,9 @@ def test_autograd_function_and_refinement():
     s = sd.sdf_score(ctx, fx, mv, g, q, t)
     gq, gt = torch.autograd.grad(s.sum(), (q, t))
     s2, dq2, dt2 = ctx.score_grad(fx, mv, g, q.detach(), t.detach())
-    assert torch.equal(s, s2) and torch.equal(gq, dq2) and torch.equal(gt, dt2)
+    # per-pose sums accumulate across blocks with FP64 atomics: equal to rounding
+    for a, b in ((s, s2), (gq, dq2), (gt, dt2)):
+        assert (a.detach() - b).abs().max().item() <= 1e-12 * b.abs().max().item()
     h = 1e-3
     for a in range(3):
         e = torch.zeros_like(t)
