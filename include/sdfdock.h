@@ -192,6 +192,29 @@ int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
                   const void* quats, const void* trans, int64_t P, void* score, void* dq,
                   void* dt, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------------- */
+
+/* Largest candidate count accepted by sd_top_k_static. */
+#define SD_TOP_K_STATIC_MAX (1 << 20)
+
+/* Top-k selection over per-rotation candidates, ordered like sd_top_k_poses
+ * (score descending, rotation ascending, index ascending; no FP64 re-score),
+ * that allocates no device memory.  The paper has no counterpart of this entry:
+ * it exists for callers that cannot allocate while they run (real-time loops
+ * that must not stall on cudaMalloc's implicit synchronisation, engines bound
+ * to a fixed shared memory pool, device memory owned by a foreign allocator).
+ *   cand   device, n_cand sd_cand, 1 <= n_cand <= SD_TOP_K_STATIC_MAX
+ *   out    device, k sd_cand (1 <= k <= 4096), best first; entries past the
+ *          number of candidates have rot = idx = -1
+ * Scratch: a 128 KiB bitset in a fixed device array that every GPU which loads
+ * the library keeps until the process exits; each call clears the bits it uses.
+ * The first call on a device looks up the array's device address (set-up):
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls whose kernels can overlap on the GPU (other streams, other
+ * host threads) race; serialise them.  Larger inputs return SD_ERR_ARG.
+ * Asynchronous on `stream`. */
+int sd_top_k_static(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, sd_cand* out, void* stream);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 
 /* Runs, on the host in FP64, the same sequence of mixed-radix Stockham stages

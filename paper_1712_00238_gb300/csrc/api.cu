@@ -1128,6 +1128,18 @@ const char* sd_version(void) { return "sdfdock 0.1 (sm_103a)"; }
 
 int64_t sd_launch_count(void) { return (int64_t)g_launches.load(); }
 
+// Helpers for entry points defined in other translation units.
+int sd_internal_fail(sd_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return fail(ctx, code, "%s", buf);
+}
+
+int sd_internal_device(const sd_ctx* ctx) { return ctx ? ctx->device : -1; }
+
 int sd_pass_times(sd_ctx* ctx, int kind, int64_t* launches, double* ms) {
     if (!ctx) return SD_ERR_ARG;
     DeviceGuard dg(ctx->device);

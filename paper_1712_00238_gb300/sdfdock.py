@@ -28,6 +28,7 @@ SD_ERR_TIMEOUT = -4
 SD_ERR_UNIMPLEMENTED = -5
 SD_ERR_NONFINITE = -6
 SD_F32, SD_F64 = 0, 1
+SD_TOP_K_STATIC_MAX = 1 << 20
 
 _ERRNAMES = {SD_ERR_ARG: "SD_ERR_ARG", SD_ERR_OOM: "SD_ERR_OOM", SD_ERR_CUDA: "SD_ERR_CUDA",
              SD_ERR_TIMEOUT: "SD_ERR_TIMEOUT", SD_ERR_UNIMPLEMENTED: "SD_ERR_UNIMPLEMENTED",
@@ -84,6 +85,7 @@ _SIGS = {
     "sd_host_line_fft": (ct.c_int, [ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_version": (ct.c_char_p, []),
     "sd_launch_count": (ct.c_int64, []),
+    "sd_top_k_static": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_pass_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
 }
 
