@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0, help="rotations per batch (0: automatic)")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
+    ap.add_argument("--spread-direct", type=int, default=0, help="one global atomic per spreading tap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -193,6 +194,7 @@ def run_ours(args):
     ctx.set_option("batch", args.batch)
     ctx.set_option("plain", args.plain)
     ctx.set_option("graph", 0 if args.plain else args.graph)
+    ctx.set_option("spread_direct", args.spread_direct)
     grid = sd.Grid(w.N, w.L)
     host = host_inputs(w, torch)
     devin = {k: v.to(dev) for k, v in host.items()}
@@ -316,6 +318,7 @@ def run_ours(args):
                                "576 Hopf rotations; top-10 + FP64 re-score; 20-step gradient refinement",
                    "rotations": n_rot, "translations": w.N ** 3, "sub_box": s,
                    "batch": args.batch, "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
+                   "spread": "direct atomics" if args.spread_direct else "shared-memory tiles",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -57,6 +57,7 @@ struct sd_ctx {
     int64_t opt_batch = 0;
     int opt_graph = 0;
     int opt_plain = 0;
+    int opt_spread_direct = 0;
     DevBuf ws[6];
     std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
     std::map<std::tuple<int, int, int, double>, double*> deconv;
@@ -465,6 +466,7 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     sa.s_h = G.s_h;
     sa.out = b0;
     sa.out_rot_stride = 0;
+    sa.direct = ctx->opt_spread_direct;
     CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
     CK(ctx, pass_x_fwd<T>(G, tw, b0, 0, b1, 0, 1, st));
     if (G.dim == 3) {
@@ -645,6 +647,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             sa.s_h = G.s_h;
             sa.out = b0;
             sa.out_rot_stride = e0;
+            sa.direct = ctx->opt_spread_direct;
             {
                 PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
                 CK(ctx, launch_spread<T>(sa, G.dim, b, s));
@@ -806,6 +809,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "graph")) ctx->opt_graph = (int)value;
     else if (!strcmp(key, "plain")) ctx->opt_plain = (int)value;
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
+    else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
     return SD_OK;
 }
@@ -870,6 +874,7 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     }
     if (!isfinite(r2)) return fail(ctx, SD_ERR_NONFINITE, "sdf_build: non-finite query point");
     s->radius = sqrt(r2);
+    CK(ctx, sort_by_morton<T>((vec4<T>*)s->pos, (cplx<T>*)s->c, m, s->radius, ctx->p.dim, st));
     *out = guard.release();
     return SD_OK;
 }
@@ -929,6 +934,10 @@ int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m
     }
     if (!isfinite(r2)) return fail(ctx, SD_ERR_NONFINITE, "shape_from_samples: non-finite position");
     s->radius = sqrt(r2);
+    e = (ctx->p.precision == SD_F64)
+            ? sort_by_morton<double>((double4_32a*)s->pos, (double2*)s->c, m, s->radius, ctx->p.dim, st)
+            : sort_by_morton<float>((float4*)s->pos, (float2*)s->c, m, s->radius, ctx->p.dim, st);
+    if (e != cudaSuccess) return fail(ctx, SD_ERR_CUDA, "shape_from_samples: ordering failed: %s", cudaGetErrorString(e));
     *out = guard.release();
     return SD_OK;
 }
@@ -995,8 +1004,13 @@ static int top_k_t(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int 
                    const sd_shape* moving, const double* quats, const sd_grid* g, sd_pose* out, cudaStream_t st) {
     void *flags, *top, *res;
     CKI(ws_get(ctx, 4, (size_t)((n_cand + 31) / 32) * 4 + 256, &flags));
-    CKI(ws_get(ctx, 5, (size_t)k * (sizeof(sd_cand) + 2 * sizeof(double)) + 256, &top));
+    const size_t moved_bytes = rescore ? (size_t)k * moving->m * 4 * sizeof(double) : 0;
+    const size_t box_bytes = rescore ? (size_t)k * rescore_tiles(moving->m) * 6 * sizeof(float) : 0;
+    const size_t head = (((size_t)k * (sizeof(sd_cand) + 2 * sizeof(double)) + 255) / 256) * 256;
+    CKI(ws_get(ctx, 5, head + moved_bytes + box_bytes + 512, &top));
     res = (char*)top + (((size_t)k * sizeof(sd_cand) + 255) / 256) * 256;
+    void* moved = (char*)top + head;
+    float* tile_box = (float*)((char*)moved + ((moved_bytes + 255) / 256) * 256);
     CK(ctx, launch_topk(cand, n_cand, k, top, (unsigned*)flags, st));
     if (rescore) {
         RescoreArgs<T> a{};
@@ -1015,6 +1029,8 @@ static int top_k_t(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int 
         a.dim = ctx->p.dim;
         a.r2max = moving->radius * moving->radius;
         a.out = (double*)res;
+        a.moved = moved;
+        a.tile_box = tile_box;
         CK(ctx, launch_rescore<T>(a, st));
     }
     std::vector<sd_cand> hc(k);

@@ -54,6 +54,7 @@ struct SpreadArgs {
     int s, s_h;           // sub-box side and half-side
     cplx<T>* out;         // batch x s^d
     int64_t out_rot_stride;
+    int direct;           // 1: one global atomic per tap (no shared-memory tile)
 };
 template <typename T> cudaError_t launch_spread(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);
 
@@ -132,8 +133,15 @@ struct RescoreArgs {
     int N; double L; double sigma_g; int dim;
     double r2max;             // squared bounding radius of the moving samples
     double* out;              // k x 2 (re, im)
+    void* moved;              // scratch: k x m2 double4 (moved samples)
+    float* tile_box;          // scratch: k x rescore_tiles(m2) x 6 (lo, hi)
 };
 template <typename T> cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st);
+int rescore_tiles(int64_t m2);
+
+// Reorder a shape's samples by the Morton code of their position (in place).
+template <typename T>
+cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, int dim, cudaStream_t st);
 
 // ---- type-2 gather: score and gradient ---------------------------------------
 template <typename T>

@@ -101,7 +101,8 @@ cudaError_t launch_topk(const void* cand, int64_t n, int k, void* out, unsigned*
 constexpr int RS_TILE = 256;
 constexpr int RS_WARPS = RS_TILE / 32;
 
-// Block-wide bounding box of one point per thread (dead threads pass +inf/-inf).
+// Block-wide bounding box of one point per thread (dead threads pass +inf/-inf);
+// the result is valid in out_lo/out_hi (shared) after the call.
 __device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float (*wlo)[3], float (*whi)[3],
                                            float out_lo[3], float out_hi[3]) {
     for (int d = 0; d < 3; ++d)
@@ -124,35 +125,76 @@ __device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float (*wlo
     __syncthreads();
 }
 
+// Pose (R, t) of a candidate: rotation matrix (FP64) and translation of its grid index.
+__device__ void pose_of(const Cand& cd, const double* quats, int N, double L, int dim, double Rm[9], double tv[3]) {
+    const double h = L / N;
+    int idx = cd.idx < 0 ? 0 : cd.idx;
+    for (int d = 0; d < 3; ++d) {
+        if (d < dim) {
+            tv[d] = (double)(idx % N - N / 2) * h;
+            idx /= N;
+        } else {
+            tv[d] = 0.0;
+        }
+    }
+    const double* q = quats + 4 * (int64_t)cd.rot;
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double n2 = w * w + x * x + y * y + z * z;
+    const double s = n2 > 0 ? 2.0 / n2 : 0.0;
+    Rm[0] = 1 - s * (y * y + z * z); Rm[1] = s * (x * y - w * z); Rm[2] = s * (x * z + w * y);
+    Rm[3] = s * (x * y + w * z); Rm[4] = 1 - s * (x * x + z * z); Rm[5] = s * (y * z - w * x);
+    Rm[6] = s * (x * z - w * y); Rm[7] = s * (y * z + w * x); Rm[8] = 1 - s * (x * x + y * y);
+}
+
+// Per pose: the moved samples y_j = R p2_j + t in FP64 and the float bounding box
+// of every tile of RS_TILE consecutive samples.
+template <typename T>
+__global__ void __launch_bounds__(RS_TILE) k_rescore_move(RescoreArgs<T> a) {
+    __shared__ double Rm[9], tv[3];
+    __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
+    __shared__ float blo[3], bhi[3];
+    const int pose = blockIdx.y;
+    const Cand cd = reinterpret_cast<const Cand*>(a.top)[pose];
+    const int ntiles = gridDim.x;
+    float* tb = a.tile_box + ((int64_t)pose * ntiles + blockIdx.x) * 6;
+    if (cd.rot < 0) {
+        if (threadIdx.x < 3) { tb[threadIdx.x] = FLT_MAX; tb[3 + threadIdx.x] = -FLT_MAX; }
+        return;
+    }
+    if (threadIdx.x == 0) pose_of(cd, a.quats, a.N, a.L, a.dim, Rm, tv);
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * RS_TILE + threadIdx.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (j < a.m2) {
+        const vec4<T> p = a.p2[j];
+        const double qx = p.x, qy = p.y, qz = (a.dim == 3) ? (double)p.z : 0.0;
+        double4 y;
+        y.x = Rm[0] * qx + Rm[1] * qy + Rm[2] * qz + tv[0];
+        y.y = Rm[3] * qx + Rm[4] * qy + Rm[5] * qz + tv[1];
+        y.z = (a.dim == 3) ? Rm[6] * qx + Rm[7] * qy + Rm[8] * qz + tv[2] : 0.0;
+        y.w = 0.0;
+        reinterpret_cast<double4*>(a.moved)[(int64_t)pose * a.m2 + j] = y;
+        lo[0] = hi[0] = (float)y.x; lo[1] = hi[1] = (float)y.y; lo[2] = hi[2] = (float)y.z;
+    }
+    block_bbox(lo, hi, wlo, whi, blo, bhi);
+    if (threadIdx.x < 3) { tb[threadIdx.x] = blo[threadIdx.x]; tb[3 + threadIdx.x] = bhi[threadIdx.x]; }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     __shared__ double yx[RS_TILE], yy[RS_TILE], yz[RS_TILE], cr[RS_TILE], ci[RS_TILE];
     __shared__ float fx[RS_TILE], fy[RS_TILE], fz[RS_TILE];
     __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
-    __shared__ float blo[3], bhi[3], tlo[3], thi[3];
-    __shared__ double Rm[9], tv[3];
+    __shared__ float blo[3], bhi[3];
+    __shared__ double tv[3];
     __shared__ int skip;
     const int pose = blockIdx.y;
     const Cand cd = reinterpret_cast<const Cand*>(a.top)[pose];
     if (cd.rot < 0) return;  // uniform over the block
-    const double h = a.L / a.N;
     if (threadIdx.x == 0) {
-        int idx = cd.idx < 0 ? 0 : cd.idx;
-        for (int d = 0; d < 3; ++d) {
-            if (d < a.dim) {
-                tv[d] = (double)(idx % a.N - a.N / 2) * h;
-                idx /= a.N;
-            } else {
-                tv[d] = 0.0;
-            }
-        }
-        const double* q = a.quats + 4 * (int64_t)cd.rot;
-        const double w = q[0], x = q[1], y = q[2], z = q[3];
-        const double n2 = w * w + x * x + y * y + z * z;
-        const double s = n2 > 0 ? 2.0 / n2 : 0.0;
-        Rm[0] = 1 - s * (y * y + z * z); Rm[1] = s * (x * y - w * z); Rm[2] = s * (x * z + w * y);
-        Rm[3] = s * (x * y + w * z); Rm[4] = 1 - s * (x * x + z * z); Rm[5] = s * (y * z - w * x);
-        Rm[6] = s * (x * z - w * y); Rm[7] = s * (y * z + w * x); Rm[8] = 1 - s * (x * x + y * y);
+        double Rm[9], t3[3];
+        pose_of(cd, a.quats, a.N, a.L, a.dim, Rm, t3);
+        tv[0] = t3[0]; tv[1] = t3[1]; tv[2] = t3[2];
     }
     const double sg2 = 2.0 * a.sigma_g * a.sigma_g;  // (sigma_g sqrt 2)^2
     const double cut = 8.0 * sqrt(sg2);
@@ -169,7 +211,7 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
         lo[0] = hi[0] = (float)px; lo[1] = hi[1] = (float)py; lo[2] = hi[2] = (float)pz;
     }
     block_bbox(lo, hi, wlo, whi, blo, bhi);
-    // the moving shape lies in a ball of radius sqrt(r2max) around t
+    // the moved samples lie in a ball of radius sqrt(r2max) around t
     if (threadIdx.x == 0) {
         double dd = 0.0;
         for (int d = 0; d < a.dim; ++d) {
@@ -182,35 +224,36 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     }
     __syncthreads();
     if (skip) return;
+    // tile test margin: float rounding of both boxes
+    const double mag = fabs(tv[0]) + fabs(tv[1]) + fabs(tv[2]) + sqrt(a.r2max) + 1.0;
+    const double cmarg = cut * (1.0 + 1e-4) + 1e-6 * mag;
+    const float blo0 = blo[0], blo1 = blo[1], blo2 = blo[2], bhi0 = bhi[0], bhi1 = bhi[1], bhi2 = bhi[2];
     const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    const int ntiles = (int)((a.m2 + RS_TILE - 1) / RS_TILE);
+    const float* tbase = a.tile_box + (int64_t)pose * ntiles * 6;
+    const double4* moved = reinterpret_cast<const double4*>(a.moved) + (int64_t)pose * a.m2;
     double sr = 0.0, si = 0.0;
-    for (int64_t j0 = 0; j0 < a.m2; j0 += RS_TILE) {
-        const int64_t j = j0 + threadIdx.x;
-        float ylo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, yhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-        if (j < a.m2) {
-            const vec4<T> p = a.p2[j];
-            const double qx = p.x, qy = p.y, qz = (a.dim == 3) ? (double)p.z : 0.0;
-            const double vx = Rm[0] * qx + Rm[1] * qy + Rm[2] * qz + tv[0];
-            const double vy = Rm[3] * qx + Rm[4] * qy + Rm[5] * qz + tv[1];
-            const double vz = (a.dim == 3) ? Rm[6] * qx + Rm[7] * qy + Rm[8] * qz + tv[2] : 0.0;
-            yx[threadIdx.x] = vx; yy[threadIdx.x] = vy; yz[threadIdx.x] = vz;
-            fx[threadIdx.x] = (float)vx; fy[threadIdx.x] = (float)vy; fz[threadIdx.x] = (float)vz;
-            cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
-            ylo[0] = yhi[0] = (float)vx; ylo[1] = yhi[1] = (float)vy; ylo[2] = yhi[2] = (float)vz;
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const float* tb = tbase + tile * 6;
+        double dd = 0.0;
+        {
+            const double g0 = fmax(0.0, fmax((double)tb[0] - bhi0, (double)blo0 - tb[3]));
+            const double g1 = fmax(0.0, fmax((double)tb[1] - bhi1, (double)blo1 - tb[4]));
+            const double g2 = fmax(0.0, fmax((double)tb[2] - bhi2, (double)blo2 - tb[5]));
+            dd = g0 * g0 + g1 * g1 + (a.dim == 3 ? g2 * g2 : 0.0);
         }
-        block_bbox(ylo, yhi, wlo, whi, tlo, thi);
-        if (threadIdx.x == 0) {
-            double dd = 0.0;
-            for (int d = 0; d < a.dim; ++d) {
-                const double g = fmax(0.0, fmax((double)tlo[d] - bhi[d], (double)blo[d] - thi[d]));
-                dd += g * g;
-            }
-            const double c2 = cut * (1.0 + 1e-4) + 1e-5 * (1.0 + fabs(tv[0]) + fabs(tv[1]) + fabs(tv[2]));
-            skip = dd > c2 * c2;
+        if (dd > cmarg * cmarg) continue;  // same decision in every thread
+        const int64_t j = (int64_t)tile * RS_TILE + threadIdx.x;
+        __syncthreads();
+        if (j < a.m2) {
+            const double4 y = moved[j];
+            yx[threadIdx.x] = y.x; yy[threadIdx.x] = y.y; yz[threadIdx.x] = y.z;
+            fx[threadIdx.x] = (float)y.x; fy[threadIdx.x] = (float)y.y; fz[threadIdx.x] = (float)y.z;
+            cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
         }
         __syncthreads();
-        if (!skip && live) {
-            const int cnt = (int)min((int64_t)RS_TILE, a.m2 - j0);
+        if (live) {
+            const int cnt = (int)min((int64_t)RS_TILE, a.m2 - (int64_t)tile * RS_TILE);
             for (int k = 0; k < cnt; ++k) {
                 const float dxf = fx[k] - pxf, dyf = fy[k] - pyf, dzf = fz[k] - pzf;
                 const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
@@ -222,7 +265,6 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
                 si += ar * bi + ai * br;
             }
         }
-        __syncthreads();
     }
     for (int off = 16; off > 0; off >>= 1) {
         sr += __shfl_down_sync(0xffffffffu, sr, off);
@@ -238,6 +280,9 @@ template <typename T>
 cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(a.out, 0, sizeof(double) * 2 * (a.k > 0 ? a.k : 1), st);
     if (e != cudaSuccess || a.k == 0 || a.m1 == 0 || a.m2 == 0) return e;
+    const unsigned ntiles = (unsigned)((a.m2 + RS_TILE - 1) / RS_TILE);
+    k_rescore_move<T><<<dim3(ntiles, a.k), RS_TILE, 0, st>>>(a);
+    note_launch();
     const dim3 grid((unsigned)((a.m1 + RS_TILE - 1) / RS_TILE), a.k);
     k_rescore<T><<<grid, RS_TILE, 0, st>>>(a);
     note_launch();
@@ -246,5 +291,7 @@ cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st) {
 
 template cudaError_t launch_rescore<float>(const RescoreArgs<float>&, cudaStream_t);
 template cudaError_t launch_rescore<double>(const RescoreArgs<double>&, cudaStream_t);
+
+int rescore_tiles(int64_t m2) { return (int)((m2 + RS_TILE - 1) / RS_TILE); }
 
 }  // namespace sd
