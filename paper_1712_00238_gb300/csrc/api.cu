@@ -1006,9 +1006,12 @@ static int top_k_t(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, int 
     CKI(ws_get(ctx, 4, (size_t)((n_cand + 31) / 32) * 4 + 256, &flags));
     const size_t moved_bytes = rescore ? (size_t)k * moving->m * 4 * sizeof(double) : 0;
     const size_t box_bytes = rescore ? (size_t)k * rescore_tiles(moving->m) * 6 * sizeof(float) : 0;
-    const size_t head = (((size_t)k * (sizeof(sd_cand) + 2 * sizeof(double)) + 255) / 256) * 256;
-    CKI(ws_get(ctx, 5, head + moved_bytes + box_bytes + 512, &top));
-    res = (char*)top + (((size_t)k * sizeof(sd_cand) + 255) / 256) * 256;
+    // layout: [top k sd_cand][re-scores 2k doubles][moved samples][tile boxes], 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t res_off = up((size_t)k * sizeof(sd_cand));
+    const size_t head = up(res_off + (size_t)k * 2 * sizeof(double));
+    CKI(ws_get(ctx, 5, head + up(moved_bytes) + box_bytes + 256, &top));
+    res = (char*)top + res_off;
     void* moved = (char*)top + head;
     float* tile_box = (float*)((char*)moved + ((moved_bytes + 255) / 256) * 256);
     CK(ctx, launch_topk(cand, n_cand, k, top, (unsigned*)flags, st));
