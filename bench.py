@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
     ap.add_argument("--spread-direct", type=int, default=0, help="one global atomic per spreading tap")
+    ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -128,9 +129,15 @@ class ClockSampler:
 # workload
 # ---------------------------------------------------------------------------
 
-def load_workload():
+def load_workload(n_rot: int = 0):
+    import copy
+
     from synth import configs
-    return configs.peg_in_bore_3d()
+    w = configs.peg_in_bore_3d()
+    if n_rot and n_rot < w.n_rot:
+        w = copy.copy(w)
+        w.quats = w.quats[:n_rot]
+    return w
 
 
 def host_inputs(w, torch):
@@ -188,7 +195,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = load_workload()
+    w = load_workload(args.rotations)
     ctx = sd.Context(3, "f32", local, lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps,
                      sigma_g=w.sigma_g, w=w.w)
     ctx.set_option("batch", args.batch)
