@@ -1121,24 +1121,22 @@ int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
 // FP64: lets the index arithmetic be checked without a GPU.  in/out: len x 2.
 int sd_host_line_fft(int len, int inverse, const double* in, double* out) {
     if (!in || !out || !fft_len_supported(len)) return SD_ERR_ARG;
-    std::vector<double2> a(pad(len) + 2), b(pad(len) + 2), tw(len);
-    for (int j = 0; j < len; ++j) {
-        const double ang = -2.0 * M_PI * (double)j / (double)len;
+    std::vector<double2> a(pad(len) + 2), tw(std::max(tw_count(len), 1));
+    tw_for_each(len, [&](int j, int r, int k, int P, int R) {
+        const double ang = -2.0 * M_PI * (double)(r * k) / (double)(P * R);
         tw[j] = make_double2(cos(ang), sin(ang));
-        a[pad(j)] = make_double2(in[2 * j], in[2 * j + 1]);
-    }
-    double2* r = nullptr;
-#define SD_HOST_CASE(L)                                                                           \
-    case L:                                                                                       \
-        r = inverse ? fft_line_host<double2, L, true>(a.data(), b.data(), tw.data())              \
-                    : fft_line_host<double2, L, false>(a.data(), b.data(), tw.data());            \
+    });
+    for (int j = 0; j < len; ++j) a[pad(j)] = make_double2(in[2 * j], in[2 * j + 1]);
+#define SD_HOST_CASE(L)                                                 \
+    case L:                                                             \
+        if (inverse) fft_line_host<double2, L, true>(a.data(), tw.data()); \
+        else fft_line_host<double2, L, false>(a.data(), tw.data());        \
         break;
     switch (len) { SD_FOR_EACH_LEN(SD_HOST_CASE) }
 #undef SD_HOST_CASE
-    if (!r) return SD_ERR_ARG;
     for (int j = 0; j < len; ++j) {
-        out[2 * j] = r[pad(j)].x;
-        out[2 * j + 1] = r[pad(j)].y;
+        out[2 * j] = a[pad(j)].x;
+        out[2 * j + 1] = a[pad(j)].y;
     }
     return SD_OK;
 }

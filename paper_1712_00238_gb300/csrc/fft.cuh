@@ -130,63 +130,118 @@ __host__ __device__ __forceinline__ void dft(C* v) {
     }
 }
 
-// One butterfly of a Stockham stage (shared by the device stage loop and the
-// host-side check).  `tw[j]` = exp(-2 pi i j / LEN).
+// Twiddles are stored stage by stage: for a stage of radix R after stages of
+// product P > 1, the block of P*(R-1) entries tw[off + k*(R-1) + (r-1)] =
+// exp(-2 pi i r k / (P R)), k in [0, P), r in [1, R).  Consecutive butterflies
+// (consecutive k) read entries R-1 apart (an odd stride): no bank conflicts.
+__host__ __device__ constexpr int tw_offset(int len, int s) {
+    int off = 0, p = 1;
+    for (int q = 0; q < s; ++q) {
+        const int r = plan_radix(len, q);
+        if (p > 1) off += p * (r - 1);
+        p *= r;
+    }
+    return off;
+}
+__host__ __device__ constexpr int tw_count(int len) {
+    int s = 0;
+    while (plan_radix(len, s) != 0) ++s;
+    return tw_offset(len, s);
+}
+
+// Fills the stage-ordered table of one length (host or device, any precision);
+// `f(j, r, k, P, R)` stores exp(-2 pi i r k / (P R)) at entry j.
+template <typename F>
+__host__ __device__ inline void tw_for_each(int len, F f) {
+    int off = 0, p = 1;
+    for (int s = 0; plan_radix(len, s) != 0; ++s) {
+        const int R = plan_radix(len, s);
+        if (p > 1)
+            for (int k = 0; k < p; ++k)
+                for (int r = 1; r < R; ++r) f(off + k * (R - 1) + (r - 1), r, k, p, R);
+        if (p > 1) off += p * (R - 1);
+        p *= R;
+    }
+}
+
+// Load, twiddle and transform one butterfly of a Stockham stage into v[].
 template <typename C, int LEN, int R, int P, bool INV>
-__host__ __device__ __forceinline__ void stockham_butterfly(const C* __restrict__ src, C* __restrict__ dst,
-                                                            int i, const C* __restrict__ tw) {
+__host__ __device__ __forceinline__ void stockham_load(const C* __restrict__ line, int i, const C* __restrict__ tw,
+                                                       C v[R]) {
     constexpr int NB = LEN / R;
     const int k = i % P;
-    C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[pad(i + r * NB)];
+    for (int r = 0; r < R; ++r) v[r] = line[pad(i + r * NB)];
     if constexpr (P > 1) {
+        const C* t = tw + k * (R - 1);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            C w = tw[r * k * (LEN / (P * R))];
+            C w = t[r - 1];
             if (INV) w.y = -w.y;
             v[r] = cmul(v[r], w);
         }
     }
     dft<R, INV>(v);
+}
+
+template <typename C, int LEN, int R, int P>
+__host__ __device__ __forceinline__ void stockham_store(C* __restrict__ line, int i, const C v[R]) {
+    const int k = i % P;
     const int j = (i - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[pad(j + r * P)] = v[r];
+    for (int r = 0; r < R; ++r) line[pad(j + r * P)] = v[r];
 }
 
 #ifdef __CUDACC__
-// All threads of the block transform `nlines` lines held at src + line*ld.
-// Returns the buffer that holds the result (src or dst).  Contains
+// In-place transform of NL lines held at buf + line*ld by a block of exactly
+// 256 threads: each stage loads its butterflies into registers, synchronises,
+// and stores them back.  `tw` is the stage-ordered table of LEN.  Contains
 // __syncthreads(); every thread of the block must call it.
-template <typename C, int LEN, bool INV, int S = 0, int P = 1>
-__device__ __forceinline__ C* fft_lines(C* src, C* dst, int nlines, int ld, const C* tw) {
+constexpr int FFT_THREADS = 256;
+
+template <typename C, int LEN, bool INV, int NL, int S = 0, int P = 1>
+__device__ __forceinline__ void fft_inplace(C* buf, int ld, const C* tw) {
     constexpr int R = plan_radix(LEN, S);
-    if constexpr (R == 0) {
-        return src;
-    } else {
+    if constexpr (R != 0) {
         constexpr int NB = LEN / R;
-        const int tot = nlines * NB;
-        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-            const int line = t / NB;
-            const int i = t - line * NB;
-            stockham_butterfly<C, LEN, R, P, INV>(src + line * ld, dst + line * ld, i, tw);
+        constexpr int TOT = NL * NB;
+        constexpr int PER = (TOT + FFT_THREADS - 1) / FFT_THREADS;
+        const C* tws = tw + tw_offset(LEN, S);
+        C v[PER][R];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int t = threadIdx.x + q * FFT_THREADS;
+            if (TOT % FFT_THREADS == 0 || t < TOT) {
+                const int line = t / NB;
+                stockham_load<C, LEN, R, P, INV>(buf + line * ld, t - line * NB, tws, v[q]);
+            }
         }
         __syncthreads();
-        return fft_lines<C, LEN, INV, S + 1, P * R>(dst, src, nlines, ld, tw);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int t = threadIdx.x + q * FFT_THREADS;
+            if (TOT % FFT_THREADS == 0 || t < TOT) {
+                const int line = t / NB;
+                stockham_store<C, LEN, R, P>(buf + line * ld, t - line * NB, v[q]);
+            }
+        }
+        __syncthreads();
+        fft_inplace<C, LEN, INV, NL, S + 1, P * R>(buf, ld, tw);
     }
 }
 #endif
 
-// Host-side reference of the same stage sequence on one line (used by the
+// Host execution of the same stage sequence on one line, in place (used by the
 // library's self-test of the index arithmetic).
 template <typename C, int LEN, bool INV, int S = 0, int P = 1>
-inline C* fft_line_host(C* src, C* dst, const C* tw) {
+inline void fft_line_host(C* line, const C* tw) {
     constexpr int R = plan_radix(LEN, S);
-    if constexpr (R == 0) {
-        return src;
-    } else {
-        for (int i = 0; i < LEN / R; ++i) stockham_butterfly<C, LEN, R, P, INV>(src, dst, i, tw);
-        return fft_line_host<C, LEN, INV, S + 1, P * R>(dst, src, tw);
+    if constexpr (R != 0) {
+        constexpr int NB = LEN / R;
+        C v[NB][R];
+        for (int i = 0; i < NB; ++i) stockham_load<C, LEN, R, P, INV>(line, i, tw + tw_offset(LEN, S), v[i]);
+        for (int i = 0; i < NB; ++i) stockham_store<C, LEN, R, P>(line, i, v[i]);
+        fft_line_host<C, LEN, INV, S + 1, P * R>(line, tw);
     }
 }
 

@@ -210,14 +210,14 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
     using C = cplx<T>;
     constexpr int TR = lines_per_cta<T, LEN>();
     constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
     constexpr bool INV = (MODE != ROW_FWD);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* bufA = reinterpret_cast<C*>(smem_raw);
-    C* bufB = bufA + TR * LD;
-    C* tw = bufB + TR * LD;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TR * LD;
     const int b = blockIdx.y;
     const int row0 = blockIdx.x * TR;
-    for (int j = threadIdx.x; j < LEN; j += blockDim.x) tw[j] = a.tw[j];
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
     const C* in = a.in + (int64_t)b * a.in_rot_stride;
     const C zero = mk(T(0), T(0));
     for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
@@ -239,10 +239,11 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
                 v = src[pos];
             }
         }
-        bufA[r * LD + pad(pos)] = v;
+        buf[r * LD + pad(pos)] = v;
     }
     __syncthreads();
-    C* res = fft_lines<C, LEN, INV>(bufA, bufB, TR, LD, tw);
+    fft_inplace<C, LEN, INV, TR>(buf, LD, tw);
+    const C* res = buf;
     C* out = a.out + (int64_t)b * a.out_rot_stride;
     if constexpr (MODE == ROW_FWD) {
         const int N = a.N, hN = N >> 1;
@@ -326,17 +327,18 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     using C = cplx<T>;
     constexpr int TC = lines_per_cta<T, LENF>();
     constexpr int LD = line_pitch(LENF);
+    constexpr int NTWF = tw_count(LENF);
+    constexpr int NTWI = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* bufA = reinterpret_cast<C*>(smem_raw);
-    C* bufB = bufA + TC * LD;
-    C* twF = bufB + TC * LD;
-    C* twI = twF + LENF;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* twF = buf + TC * LD;
+    C* twI = twF + NTWF;
     const int b = blockIdx.z;
     const int outer = blockIdx.y;
     const int col0 = blockIdx.x * TC;
-    for (int j = threadIdx.x; j < LENF; j += blockDim.x) twF[j] = a.twF[j];
+    for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
     if constexpr (MODE == COL_FUSED)
-        for (int j = threadIdx.x; j < LENI; j += blockDim.x) twI[j] = a.twI[j];
+        for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
     const int ncols = a.ncols;
     const C* in = a.in + (int64_t)b * a.in_rot_stride + (int64_t)outer * a.in_outer_stride;
     C* out = a.out + (int64_t)b * a.out_rot_stride + (int64_t)outer * a.out_outer_stride;
@@ -358,11 +360,12 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
         }
         C v = zero;
         if (e >= 0 && gcol < ncols) v = in[(int64_t)e * ncols + gcol];
-        bufA[col * LD + pad(pos)] = v;
+        buf[col * LD + pad(pos)] = v;
     }
     __syncthreads();
     constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
-    C* res = fft_lines<C, LENF, INV1>(bufA, bufB, TC, LD, twF);
+    fft_inplace<C, LENF, INV1, TC>(buf, LD, twF);
+    C* res = buf;
     if constexpr (MODE == COL_FWD) {
         for (int idx = threadIdx.x; idx < TC * a.N; idx += blockDim.x) {
             const int col = idx % TC;
@@ -380,26 +383,36 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             const int gcol = col0 + col;
             if (gcol < ncols) out[(int64_t)e * ncols + gcol] = res[col * LD + pad(e)];
         }
-    } else {  // COL_FUSED: keep N modes, multiply by W, inverse of length N
-        C* other = (res == bufA) ? bufB : bufA;
-        for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
-            const int col = idx % TC;
-            const int kp = idx / TC;
-            const int gcol = col0 + col;
-            C v = zero;
-            if (gcol < ncols) {
-                const int pos = kp < hN ? kp : kp - LENI + LENF;
-                v = cmul(res[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
+    } else {  // COL_FUSED: keep N modes, multiply by W, inverse of length N (in place)
+        constexpr int PERX = (TC * LENI + FFT_THREADS - 1) / FFT_THREADS;
+        C v[PERX];
+#pragma unroll
+        for (int q = 0; q < PERX; ++q) {
+            const int idx = threadIdx.x + q * FFT_THREADS;
+            v[q] = zero;
+            if (idx < TC * LENI) {
+                const int col = idx % TC;
+                const int kp = idx / TC;
+                const int gcol = col0 + col;
+                if (gcol < ncols) {
+                    const int pos = kp < hN ? kp : kp - LENI + LENF;
+                    v[q] = cmul(res[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
+                }
             }
-            other[col * LD + pad(kp)] = v;
         }
         __syncthreads();
-        C* res2 = fft_lines<C, LENI, true>(other, res, TC, LD, twI);
+#pragma unroll
+        for (int q = 0; q < PERX; ++q) {
+            const int idx = threadIdx.x + q * FFT_THREADS;
+            if (idx < TC * LENI) buf[(idx % TC) * LD + pad(idx / TC)] = v[q];
+        }
+        __syncthreads();
+        fft_inplace<C, LENI, true, TC>(buf, LD, twI);
         for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
             const int col = idx % TC;
             const int e = idx / TC;
             const int gcol = col0 + col;
-            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = res2[col * LD + pad(e)];
+            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
         }
     }
 }
@@ -428,7 +441,7 @@ template <typename T, int LEN, int MODE>
 static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
     using C = cplx<T>;
     constexpr int TR = lines_per_cta<T, LEN>();
-    const size_t smem = (size_t)(2 * TR * line_pitch(LEN) + LEN) * sizeof(C);
+    const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
     auto kern = k_rows<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -444,7 +457,7 @@ template <typename T, int LENF, int LENI, int MODE>
 static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     using C = cplx<T>;
     constexpr int TC = lines_per_cta<T, LENF>();
-    const size_t smem = (size_t)(2 * TC * line_pitch(LENF) + LENF + LENI) * sizeof(C);
+    const size_t smem = (size_t)(TC * line_pitch(LENF) + tw_count(LENF) + tw_count(LENI)) * sizeof(C);
     auto kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -529,13 +542,16 @@ cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStre
 // small kernels
 // ---------------------------------------------------------------------------
 
+// Stage-ordered twiddle table of one line length, in FP64 (one thread: at most
+// a few hundred entries, built once).
 template <typename T>
 __global__ void k_twiddles(cplx<T>* tw, int len) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= len) return;
-    double s, c;
-    sincospi(-2.0 * (double)j / (double)len, &s, &c);
-    tw[j] = mk(T(c), T(s));
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    tw_for_each(len, [&](int j, int r, int k, int P, int R) {
+        double s, c;
+        sincospi(-2.0 * (double)(r * k) / (double)(P * R), &s, &c);
+        tw[j] = mk(T(c), T(s));
+    });
 }
 
 template <typename T>
@@ -589,7 +605,7 @@ __global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, in
 
 template <typename T>
 cudaError_t launch_twiddles_t(cplx<T>* tw, int len, cudaStream_t st) {
-    k_twiddles<T><<<(len + 255) / 256, 256, 0, st>>>(tw, len);
+    k_twiddles<T><<<1, 32, 0, st>>>(tw, len);
     note_launch();
     return cudaGetLastError();
 }
