@@ -210,15 +210,30 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(dev)
 
+    phase_ms = {"sdf_build": 0.0, "search": 0.0, "top_k_rescore": 0.0, "refine": 0.0}
+
+    def mark():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(torch.cuda.current_stream(dev))
+        return e
+
     def step(inp):
+        e0 = mark()
         fx = ctx.sdf_build(inp["f_bnd"], inp["f_nrm"], inp["f_area"], inp["f_qry"], inp["f_vol"])
         mv = ctx.sdf_build(inp["m_bnd"], inp["m_nrm"], inp["m_area"], inp["m_qry"], inp["m_vol"])
+        e1 = mark()
         ctx.score_rotations(fx, mv, inp["quats"], grid, out=cand)
+        e2 = mark()
         poses = ctx.top_k_poses(cand, TOP_K, fx, mv, inp["quats"], grid, rescore_fp64=True)
+        e3 = mark()
         rots = torch.tensor([p["rot"] for p in poses], device=dev)
         q0 = inp["quats"][rots].float()
         t0 = torch.tensor([p["t"] for p in poses], dtype=torch.float32, device=dev)
         q, t, hist = sd.refine_poses(ctx, fx, mv, grid, q0, t0, steps=REFINE_STEPS, lr_t=0.01, lr_q=0.005)
+        e4 = mark()
+        e4.synchronize()
+        for k, (a_, b_) in zip(phase_ms, ((e0, e1), (e1, e2), (e2, e3), (e3, e4))):
+            phase_ms[k] += a_.elapsed_time(b_)
         ctx.shapes.remove(fx)
         ctx.shapes.remove(mv)
         fx.free()
@@ -256,9 +271,12 @@ def run_ours(args):
     clocks = ClockSampler(local)
     ctx.set_option("timing", 1)
     ctx.pass_times(reset=True)
+    for k in phase_ms:
+        phase_ms[k] = 0.0
     l0 = sd.launch_count()
     times, (poses, hist) = timed_steps(args.steps, False)
     launches = sd.launch_count() - l0
+    phases = {k: round(v / max(args.steps, 1), 3) for k, v in phase_ms.items()}
     ptimes = ctx.pass_times(reset=True)
     ctx.set_option("timing", 0)
     torch.cuda.synchronize(dev)
@@ -335,6 +353,7 @@ def run_ours(args):
         "roofline": roofline,
         "passes": pass_report,
         "search_ms_per_step": search_ms,
+        "phase_ms_per_step": phases,
         "top1": {"score": merged[0][0], "rot": merged[0][1], "idx": merged[0][2]},
         "clocks": clk,
     }
