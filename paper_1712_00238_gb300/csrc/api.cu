@@ -58,7 +58,7 @@ struct sd_ctx {
     int opt_graph = 0;
     int opt_plain = 0;
     int opt_spread_direct = 0;
-    DevBuf ws[6];
+    DevBuf ws[8];
     std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
     std::map<std::tuple<int, int, int, double>, double*> deconv;
     double* gl_x = nullptr;
@@ -423,6 +423,30 @@ static cudaError_t pass_y_inv(const Geo& G, const Tw<T>& tw, cplx<T>* buf, int64
     return launch_cols<T>(COL_INV, c, batch, st);
 }
 
+// Bin workspace of one spread batch (slot 6).
+static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* bn) {
+    const int nb = (s + 7) / 8;
+    const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
+    const size_t ints = (size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m;
+    void* p = nullptr;
+    CKI(ws_get(ctx, 6, ints * sizeof(int) + 1024, &p));
+    int* q = (int*)p;
+    bn->nb = nb;
+    bn->nbins = nbins;
+    bn->count = q;
+    q += (size_t)batch * nbins;
+    bn->offset = q;
+    q += (size_t)batch * (nbins + 1);
+    bn->bin_of = q;
+    q += (size_t)batch * m;
+    bn->rank = q;
+    q += (size_t)batch * m;
+    bn->sorted = q;
+    return SD_OK;
+}
+
+static bool bins_supported(int w) { return w >= 4 && w <= 8; }
+
 // ---------------------------------------------------------------------------
 // fixed-shape preparation for a grid
 // ---------------------------------------------------------------------------
@@ -451,7 +475,6 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     if (sz2) CK(ctx, cudaMalloc(&b2, sz2 * sizeof(C)));
     CK(ctx, cudaMalloc(&B1, Nd * sizeof(C)));
     CK(ctx, cudaMalloc(&W, Nd * sizeof(C)));
-    CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
     SpreadArgs<T> sa{};
     sa.pos = (const vec4<T>*)fx->pos;
     sa.c = (const C*)fx->c;
@@ -467,7 +490,15 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     sa.out = b0;
     sa.out_rot_stride = 0;
     sa.direct = ctx->opt_spread_direct;
-    CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
+    sa.n_full = G.n;
+    if (ctx->opt_spread_direct || !bins_supported(ctx->p.w)) {
+        CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
+        CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
+    } else {
+        BinArgs bn;
+        CKI(bins_for(ctx, G.s, G.dim, fx->m, 1, &bn));
+        CK(ctx, launch_spread_bins<T>(sa, bn, G.dim, 1, st));
+    }
     CK(ctx, pass_x_fwd<T>(G, tw, b0, 0, b1, 0, 1, st));
     if (G.dim == 3) {
         CK(ctx, pass_y_fwd<T>(G, tw, b1, 0, b2, 0, 1, st));
@@ -623,13 +654,16 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
     C* b0 = (C*)b0v;
     C* b1 = (C*)b1v;
     const C* W = (const C*)prep->W;
+    const bool use_bins = !ctx->opt_spread_direct && bins_supported(ctx->p.w);
+    BinArgs bn{};
+    if (use_bins) CKI(bins_for(ctx, G.s, G.dim, moving->m, B, &bn));
     const int64_t Nd = (G.dim == 2) ? (int64_t)G.N * G.N : (int64_t)G.N * G.N * G.N;
 
     // One launch sequence per batch; optionally replayed from a captured graph.
     auto enqueue = [&](cudaStream_t s, bool timed) -> int {
         for (int64_t r0 = 0; r0 < n_r; r0 += B) {
             const int b = (int)std::min<int64_t>(B, n_r - r0);
-            {
+            if (!use_bins) {
                 PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
                 CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
             }
@@ -648,9 +682,11 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             sa.out = b0;
             sa.out_rot_stride = e0;
             sa.direct = ctx->opt_spread_direct;
+            sa.n_full = G.n;
             {
                 PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
-                CK(ctx, launch_spread<T>(sa, G.dim, b, s));
+                if (use_bins) CK(ctx, launch_spread_bins<T>(sa, bn, G.dim, b, s));
+                else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
             }
             {
                 PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);

@@ -55,8 +55,24 @@ struct SpreadArgs {
     cplx<T>* out;         // batch x s^d
     int64_t out_rot_stride;
     int direct;           // 1: one global atomic per tap (no shared-memory tile)
+    int n_full;           // oversampled grid length n (s == n means periodic wrap)
 };
 template <typename T> cudaError_t launch_spread(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);
+
+// Bins of the spread sub-box (8^d cells each) and the per-rotation sample order.
+struct BinArgs {
+    int nb;               // bins per axis = ceil(s / 8)
+    int nbins;            // nb^d
+    int* count;           // batch x nbins
+    int* offset;          // batch x (nbins + 1)
+    int* bin_of;          // batch x m
+    int* rank;            // batch x m
+    int32_t* sorted;      // batch x m: sample indices in bin order
+};
+// Spread by bins: writes every cell of the batch's sub-boxes (no clearing needed).
+// Supports w = 4..8 (the tap box must fit in two bins per axis).
+template <typename T>
+cudaError_t launch_spread_bins(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st);
 
 // ---- line passes ------------------------------------------------------------
 enum RowMode { ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3 };

@@ -202,6 +202,202 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a, int cap_cells) 
 }
 
 // ---------------------------------------------------------------------------
+// spreading by bins (no global atomics, no clearing pass)
+// ---------------------------------------------------------------------------
+//
+// The sub-box is cut into bins of SPREAD_BIN^d cells.  A sample belongs to the
+// bin that holds the first cell of its tap box.  Since W - 1 < SPREAD_BIN, the
+// taps of a sample only reach its own bin and the next one along each axis, so
+// the tile of bin t receives taps only from samples of bins t - {0,1}^d.  One CTA
+// per tile gathers those samples, accumulates the taps that fall in its tile in
+// shared memory and stores the whole tile (zeros included) once.
+
+constexpr int SPREAD_BIN = 8;
+
+// Tap-box origin (sub-box coordinates, wrapped when the sub-box is the whole
+// periodic grid) and kernel weights of sample j under rotation Rm.
+template <typename T, int D, int W>
+__device__ __forceinline__ void sample_taps(const SpreadArgs<T>& a, const T* Rm, int64_t j, int org[D], T wt[D][W],
+                                            cplx<T>& c) {
+    const vec4<T> p = a.pos[j];
+    c = a.c[j];
+    T y[3];
+    y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
+    y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
+    y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
+    const T half = T(W) * T(0.5);
+    const T inv_half = T(2) / T(W);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const T g = y[d] * a.inv_h;
+        const int u0 = (int)ceil(g - half);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const T z = (T(u0 + k) - g) * inv_half;
+            const T z2 = z * z;
+            wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+        }
+        org[d] = wrap_index(u0 + a.s_h, a.s);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_rotation(const SpreadArgs<T>& a, int b, T* Rm) {
+    if (a.quats) {
+        quat_to_matrix<T>(a.quats + 4 * (a.rot0 + b), Rm);
+    } else {
+        for (int i = 0; i < 9; ++i) Rm[i] = (i % 4 == 0) ? T(1) : T(0);
+    }
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) {
+    __shared__ T Rm[9];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) load_rotation(a, b, Rm);
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.m) return;
+    int org[D];
+    T wt[D][W];
+    cplx<T> c;
+    sample_taps<T, D, W>(a, Rm, j, org, wt, c);
+    int bin = 0;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / SPREAD_BIN;
+    const int64_t o = (int64_t)b * a.m + j;
+    bn.bin_of[o] = bin;
+    bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
+}
+
+// Exclusive scan of the bin counts of one rotation (one CTA of 1024 threads).
+static __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs bn) {
+    __shared__ int wsum[32];
+    const int b = blockIdx.x;
+    const int* cnt = bn.count + (int64_t)b * bn.nbins;
+    int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
+    const int per = (bn.nbins + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per;
+    const int hi = min(bn.nbins, lo + per);
+    int local = 0;
+    for (int i = lo; i < hi; ++i) local += cnt[i];
+    // block exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = lo; i < hi; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) off[bn.nbins] = run;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
+    const int b = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t o = (int64_t)b * m + j;
+    const int pos = bn.offset[(int64_t)b * (bn.nbins + 1) + bn.bin_of[o]] + bn.rank[o];
+    bn.sorted[(int64_t)b * m + pos] = (int32_t)j;
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<T> a, BinArgs bn) {
+    using C = cplx<T>;
+    constexpr int CELLS = (D == 3) ? SPREAD_BIN * SPREAD_BIN * SPREAD_BIN : SPREAD_BIN * SPREAD_BIN;
+    __shared__ T tile[2 * CELLS];
+    __shared__ T Rm[9];
+    __shared__ int nbr_lo[1 << D], nbr_hi[1 << D];
+    __shared__ int shift[1 << D][3];
+    const int b = blockIdx.y;
+    const int t = blockIdx.x;
+    const int nb = bn.nb, s = a.s;
+    int tb[3] = {t % nb, (t / nb) % nb, (D == 3) ? t / (nb * nb) : 0};
+    const bool periodic = (s == a.n_full);
+    for (int i = threadIdx.x; i < 2 * CELLS; i += blockDim.x) tile[i] = T(0);
+    if (threadIdx.x == 0) load_rotation(a, b, Rm);
+    if (threadIdx.x < (1 << D)) {
+        // neighbour bin t - delta; shift[] moves its samples' origins into this tile's frame
+        int nbin = 0;
+        bool ok = true;
+        for (int d = D - 1; d >= 0; --d) {
+            const int delta = (threadIdx.x >> d) & 1;
+            int q = tb[d] - delta;
+            int sh = 0;
+            if (q < 0) {
+                if (!periodic) ok = false;
+                q += nb;
+                sh = -s;
+            }
+            shift[threadIdx.x][d] = sh;
+            nbin = nbin * nb + q;
+        }
+        const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
+        nbr_lo[threadIdx.x] = ok ? off[nbin] : 0;
+        nbr_hi[threadIdx.x] = ok ? off[nbin + 1] : 0;
+    }
+    __syncthreads();
+    int ext[3], org0[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        org0[d] = tb[d] * SPREAD_BIN;
+        ext[d] = (d < D) ? min(SPREAD_BIN, s - org0[d]) : 1;
+    }
+    const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
+    for (int q = 0; q < (1 << D); ++q) {
+        for (int p = nbr_lo[q] + threadIdx.x; p < nbr_hi[q]; p += blockDim.x) {
+            int org[D];
+            T wt[D][W];
+            C c;
+            sample_taps<T, D, W>(a, Rm, sorted[p], org, wt, c);
+            int l[3] = {0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < D; ++d) l[d] = org[d] + shift[q][d] - org0[d];
+            const int kz0 = (D == 3) ? max(0, -l[2]) : 0, kz1 = (D == 3) ? min(W, ext[2] - l[2]) : 1;
+            const int ky0 = max(0, -l[1]), ky1 = min(W, ext[1] - l[1]);
+            const int kx0 = max(0, -l[0]), kx1 = min(W, ext[0] - l[0]);
+            for (int kz = kz0; kz < kz1; ++kz) {
+                const C cz = (D == 3) ? cscale(c, wt[D == 3 ? 2 : 0][kz]) : c;
+                for (int ky = ky0; ky < ky1; ++ky) {
+                    const C cy = cscale(cz, wt[1][ky]);
+                    T* row = tile + 2 * (((l[2] + kz) * SPREAD_BIN + (l[1] + ky)) * SPREAD_BIN + l[0]);
+                    for (int kx = kx0; kx < kx1; ++kx) {
+                        atomicAdd(row + 2 * kx, cy.x * wt[0][kx]);
+                        atomicAdd(row + 2 * kx + 1, cy.y * wt[0][kx]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    C* out = a.out + (int64_t)b * a.out_rot_stride;
+    for (int li = threadIdx.x; li < CELLS; li += blockDim.x) {
+        const int x = li % SPREAD_BIN, y = (li / SPREAD_BIN) % SPREAD_BIN, z = li / (SPREAD_BIN * SPREAD_BIN);
+        if (x < ext[0] && y < ext[1] && z < ext[2]) {
+            int64_t o = (int64_t)(org0[1] + y) * s + (org0[0] + x);
+            if (D == 3) o += (int64_t)(org0[2] + z) * s * s;
+            out[o] = mk(tile[2 * li], tile[2 * li + 1]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // row passes (lines contiguous in memory)
 // ---------------------------------------------------------------------------
 
@@ -538,6 +734,36 @@ cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStre
     return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
+    if (e != cudaSuccess) return e;
+    const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
+    const dim3 gtiles((unsigned)bn.nbins, batch);
+#define SD_BIN_CASE(WW)                                                           \
+    case WW:                                                                      \
+        if (a.m > 0) {                                                            \
+            if (dim == 2) k_bin_count<T, 2, WW><<<gpts, 256, 0, st>>>(a, bn);      \
+            else k_bin_count<T, 3, WW><<<gpts, 256, 0, st>>>(a, bn);               \
+            k_bin_scan<<<batch, 1024, 0, st>>>(bn);                                \
+            k_bin_scatter<T><<<gpts, 256, 0, st>>>(a.m, bn);                        \
+            note_launch(3);                                                       \
+        } else {                                                                  \
+            k_bin_scan<<<batch, 1024, 0, st>>>(bn);                                \
+            note_launch();                                                        \
+        }                                                                         \
+        if (dim == 2) k_spread_tiles<T, 2, WW><<<gtiles, 256, 0, st>>>(a, bn);     \
+        else k_spread_tiles<T, 3, WW><<<gtiles, 256, 0, st>>>(a, bn);              \
+        note_launch();                                                            \
+        return cudaGetLastError();
+    switch (a.w) {
+        SD_BIN_CASE(4) SD_BIN_CASE(5) SD_BIN_CASE(6) SD_BIN_CASE(7) SD_BIN_CASE(8)
+    }
+#undef SD_BIN_CASE
+    return cudaErrorInvalidValue;
+}
+
 // ---------------------------------------------------------------------------
 // small kernels
 // ---------------------------------------------------------------------------
@@ -638,6 +864,10 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int64_t cells,
     }                                                                                                   \
     template <> cudaError_t launch_cols<T>(int mode, const ColArgs<T>& a, int batch, cudaStream_t st) {   \
         return launch_cols_t<T>(mode, a, batch, st);                                                    \
+    }                                                                                                   \
+    template <> cudaError_t launch_spread_bins<T>(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, \
+                                                  cudaStream_t st) {                                    \
+        return launch_spread_bins_t<T>(a, bn, dim, batch, st);                                          \
     }                                                                                                   \
     template <> cudaError_t launch_twiddles<T>(cplx<T>* tw, int len, cudaStream_t st) {                 \
         return launch_twiddles_t<T>(tw, len, st);                                                       \

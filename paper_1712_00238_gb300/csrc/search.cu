@@ -180,10 +180,17 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore_move(RescoreArgs<T> a) {
     if (threadIdx.x < 3) { tb[threadIdx.x] = blo[threadIdx.x]; tb[3 + threadIdx.x] = bhi[threadIdx.x]; }
 }
 
+// Pairs that pass the FP32 screen are queued per warp and evaluated 32 at a
+// time in FP64 with every lane busy: only the pose's total is needed, so any
+// lane may take any pair.
+constexpr int RS_QUEUE = 256;  // pair slots per warp
+
 template <typename T>
 __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     __shared__ double yx[RS_TILE], yy[RS_TILE], yz[RS_TILE], cr[RS_TILE], ci[RS_TILE];
+    __shared__ double qx1[RS_TILE], qy1[RS_TILE], qz1[RS_TILE], ar1[RS_TILE], ai1[RS_TILE];
     __shared__ float fx[RS_TILE], fy[RS_TILE], fz[RS_TILE];
+    __shared__ unsigned short qpair[RS_WARPS][RS_QUEUE][2];  // (fixed slot, moving slot)
     __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
     __shared__ float blo[3], bhi[3];
     __shared__ double tv[3];
@@ -197,18 +204,25 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
         tv[0] = t3[0]; tv[1] = t3[1]; tv[2] = t3[2];
     }
     const double sg2 = 2.0 * a.sigma_g * a.sigma_g;  // (sigma_g sqrt 2)^2
+    const double inv_2sg2 = 1.0 / (2.0 * sg2);
     const double cut = 8.0 * sqrt(sg2);
     const float cut2f = (float)(cut * cut) * 1.001f;
     const double norm = (a.dim == 3) ? pow(2.0 * M_PI * sg2, -1.5) : 1.0 / (2.0 * M_PI * sg2);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.m1;
-    double px = 0, py = 0, pz = 0, ar = 0, ai = 0;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    if (live) {
-        const vec4<T> p = a.p1[i];
-        px = p.x; py = p.y; pz = (a.dim == 3) ? (double)p.z : 0.0;
-        ar = a.c1[i].x; ai = a.c1[i].y;
-        lo[0] = hi[0] = (float)px; lo[1] = hi[1] = (float)py; lo[2] = hi[2] = (float)pz;
+    float pxf = 0.f, pyf = 0.f, pzf = 0.f;
+    {
+        double px = 0, py = 0, pz = 0, ar = 0, ai = 0;
+        if (live) {
+            const vec4<T> p = a.p1[i];
+            px = p.x; py = p.y; pz = (a.dim == 3) ? (double)p.z : 0.0;
+            ar = a.c1[i].x; ai = a.c1[i].y;
+            pxf = (float)px; pyf = (float)py; pzf = (float)pz;
+            lo[0] = hi[0] = pxf; lo[1] = hi[1] = pyf; lo[2] = hi[2] = pzf;
+        }
+        qx1[threadIdx.x] = px; qy1[threadIdx.x] = py; qz1[threadIdx.x] = pz;
+        ar1[threadIdx.x] = ar; ai1[threadIdx.x] = ai;
     }
     block_bbox(lo, hi, wlo, whi, blo, bhi);
     // the moved samples lie in a ball of radius sqrt(r2max) around t
@@ -226,23 +240,35 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     if (skip) return;
     // tile test margin: float rounding of both boxes
     const double mag = fabs(tv[0]) + fabs(tv[1]) + fabs(tv[2]) + sqrt(a.r2max) + 1.0;
-    const double cmarg = cut * (1.0 + 1e-4) + 1e-6 * mag;
+    const float cmarg = (float)(cut * (1.0 + 1e-4) + 1e-6 * mag);
+    const float cm2 = cmarg * cmarg;
     const float blo0 = blo[0], blo1 = blo[1], blo2 = blo[2], bhi0 = bhi[0], bhi1 = bhi[1], bhi2 = bhi[2];
-    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
     const int ntiles = (int)((a.m2 + RS_TILE - 1) / RS_TILE);
     const float* tbase = a.tile_box + (int64_t)pose * ntiles * 6;
     const double4* moved = reinterpret_cast<const double4*>(a.moved) + (int64_t)pose * a.m2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned short(*queue)[2] = qpair[warp];
+    int qn = 0;  // entries in this warp's queue (same value in every lane)
     double sr = 0.0, si = 0.0;
+    auto drain = [&](int upto) {  // evaluate queue entries [0, upto) in FP64
+        for (int q0 = 0; q0 < upto; q0 += 32) {
+            const int q = q0 + lane;
+            if (q < upto) {
+                const int fi = queue[q][0], mj = queue[q][1];
+                const double dx = yx[mj] - qx1[fi], dy = yy[mj] - qy1[fi], dz = yz[mj] - qz1[fi];
+                const double g = norm * exp(-(dx * dx + dy * dy + dz * dz) * inv_2sg2);
+                const double br = cr[mj] * g, bi = ci[mj] * g;
+                sr += ar1[fi] * br - ai1[fi] * bi;
+                si += ar1[fi] * bi + ai1[fi] * br;
+            }
+        }
+    };
     for (int tile = 0; tile < ntiles; ++tile) {
         const float* tb = tbase + tile * 6;
-        double dd = 0.0;
-        {
-            const double g0 = fmax(0.0, fmax((double)tb[0] - bhi0, (double)blo0 - tb[3]));
-            const double g1 = fmax(0.0, fmax((double)tb[1] - bhi1, (double)blo1 - tb[4]));
-            const double g2 = fmax(0.0, fmax((double)tb[2] - bhi2, (double)blo2 - tb[5]));
-            dd = g0 * g0 + g1 * g1 + (a.dim == 3 ? g2 * g2 : 0.0);
-        }
-        if (dd > cmarg * cmarg) continue;  // same decision in every thread
+        const float g0 = fmaxf(0.f, fmaxf(tb[0] - bhi0, blo0 - tb[3]));
+        const float g1 = fmaxf(0.f, fmaxf(tb[1] - bhi1, blo1 - tb[4]));
+        const float g2 = (a.dim == 3) ? fmaxf(0.f, fmaxf(tb[2] - bhi2, blo2 - tb[5])) : 0.f;
+        if (g0 * g0 + g1 * g1 + g2 * g2 > cm2) continue;  // same decision in every thread
         const int64_t j = (int64_t)tile * RS_TILE + threadIdx.x;
         __syncthreads();
         if (j < a.m2) {
@@ -252,25 +278,39 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
             cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
         }
         __syncthreads();
-        if (live) {
-            const int cnt = (int)min((int64_t)RS_TILE, a.m2 - (int64_t)tile * RS_TILE);
-            for (int k = 0; k < cnt; ++k) {
+        const int cnt = (int)min((int64_t)RS_TILE, a.m2 - (int64_t)tile * RS_TILE);
+        for (int k = 0; k < cnt; ++k) {
+            bool pass = false;
+            if (live) {
                 const float dxf = fx[k] - pxf, dyf = fy[k] - pyf, dzf = fz[k] - pzf;
-                const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-                if (d2f > cut2f) continue;
-                const double dx = yx[k] - px, dy = yy[k] - py, dz = yz[k] - pz;
-                const double g = norm * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
-                const double br = cr[k] * g, bi = ci[k] * g;
-                sr += ar * br - ai * bi;
-                si += ar * bi + ai * br;
+                pass = dxf * dxf + dyf * dyf + dzf * dzf <= cut2f;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (m) {
+                if (pass) {
+                    const int slot = qn + __popc(m & ((1u << lane) - 1u));
+                    queue[slot][0] = (unsigned short)threadIdx.x;
+                    queue[slot][1] = (unsigned short)k;
+                }
+                qn += __popc(m);
+                if (qn > RS_QUEUE - 32) {
+                    __syncwarp();
+                    drain(qn);
+                    __syncwarp();
+                    qn = 0;
+                }
             }
         }
+        __syncwarp();
+        drain(qn);  // the tile's smem is overwritten by the next tile
+        __syncwarp();
+        qn = 0;
     }
     for (int off = 16; off > 0; off >>= 1) {
         sr += __shfl_down_sync(0xffffffffu, sr, off);
         si += __shfl_down_sync(0xffffffffu, si, off);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         atomicAdd(a.out + 2 * pose, sr);
         atomicAdd(a.out + 2 * pose + 1, si);
     }
