@@ -445,7 +445,7 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* 
     return SD_OK;
 }
 
-static bool bins_supported(int w) { return w >= 4 && w <= 8; }
+static bool bins_supported(int w) { return w >= 4 && w <= 7; }
 
 // ---------------------------------------------------------------------------
 // fixed-shape preparation for a grid
@@ -491,8 +491,8 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     sa.out_rot_stride = 0;
     sa.direct = ctx->opt_spread_direct;
     sa.n_full = G.n;
+    CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
     if (ctx->opt_spread_direct || !bins_supported(ctx->p.w)) {
-        CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
         CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
     } else {
         BinArgs bn;
@@ -663,7 +663,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
     auto enqueue = [&](cudaStream_t s, bool timed) -> int {
         for (int64_t r0 = 0; r0 < n_r; r0 += B) {
             const int b = (int)std::min<int64_t>(B, n_r - r0);
-            if (!use_bins) {
+            {
                 PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
                 CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
             }

@@ -69,8 +69,8 @@ struct BinArgs {
     int* rank;            // batch x m
     int32_t* sorted;      // batch x m: sample indices in bin order
 };
-// Spread by bins: writes every cell of the batch's sub-boxes (no clearing needed).
-// Supports w = 4..8 (the tap box must fit in two bins per axis).
+// Spread by bins; accumulates into the batch's sub-boxes, which must be cleared first.
+// Supports w = 4..7 (shared tile of (8 + w - 1)^d cells).
 template <typename T>
 cudaError_t launch_spread_bins(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st);
 

@@ -317,70 +317,45 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
     bn.sorted[(int64_t)b * m + pos] = (int32_t)j;
 }
 
+// One CTA per bin: its samples' taps all fall in the bin grown by W - 1 cells,
+// accumulated in shared memory (every sample once, taps unrolled), then added to
+// the sub-box with one vector atomic per non-zero cell.
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<T> a, BinArgs bn) {
     using C = cplx<T>;
-    constexpr int CELLS = (D == 3) ? SPREAD_BIN * SPREAD_BIN * SPREAD_BIN : SPREAD_BIN * SPREAD_BIN;
+    constexpr int PS = SPREAD_BIN + W - 1;
+    constexpr int CELLS = (D == 3) ? PS * PS * PS : PS * PS;
     __shared__ T tile[2 * CELLS];
     __shared__ T Rm[9];
-    __shared__ int nbr_lo[1 << D], nbr_hi[1 << D];
-    __shared__ int shift[1 << D][3];
     const int b = blockIdx.y;
     const int t = blockIdx.x;
-    const int nb = bn.nb, s = a.s;
-    int tb[3] = {t % nb, (t / nb) % nb, (D == 3) ? t / (nb * nb) : 0};
-    const bool periodic = (s == a.n_full);
+    const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
+    const int lo = off[t], hi = off[t + 1];
+    if (lo == hi) return;  // empty bin (uniform over the block)
     for (int i = threadIdx.x; i < 2 * CELLS; i += blockDim.x) tile[i] = T(0);
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
-    if (threadIdx.x < (1 << D)) {
-        // neighbour bin t - delta; shift[] moves its samples' origins into this tile's frame
-        int nbin = 0;
-        bool ok = true;
-        for (int d = D - 1; d >= 0; --d) {
-            const int delta = (threadIdx.x >> d) & 1;
-            int q = tb[d] - delta;
-            int sh = 0;
-            if (q < 0) {
-                if (!periodic) ok = false;
-                q += nb;
-                sh = -s;
-            }
-            shift[threadIdx.x][d] = sh;
-            nbin = nbin * nb + q;
-        }
-        const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
-        nbr_lo[threadIdx.x] = ok ? off[nbin] : 0;
-        nbr_hi[threadIdx.x] = ok ? off[nbin + 1] : 0;
-    }
     __syncthreads();
-    int ext[3], org0[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        org0[d] = tb[d] * SPREAD_BIN;
-        ext[d] = (d < D) ? min(SPREAD_BIN, s - org0[d]) : 1;
-    }
+    const int nb = bn.nb, s = a.s;
+    const int org0[3] = {(t % nb) * SPREAD_BIN, ((t / nb) % nb) * SPREAD_BIN,
+                         (D == 3) ? (t / (nb * nb)) * SPREAD_BIN : 0};
     const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
-    for (int q = 0; q < (1 << D); ++q) {
-        for (int p = nbr_lo[q] + threadIdx.x; p < nbr_hi[q]; p += blockDim.x) {
-            int org[D];
-            T wt[D][W];
-            C c;
-            sample_taps<T, D, W>(a, Rm, sorted[p], org, wt, c);
-            int l[3] = {0, 0, 0};
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+        int org[D];
+        T wt[D][W];
+        C c;
+        sample_taps<T, D, W>(a, Rm, sorted[p], org, wt, c);
+        const int lx = org[0] - org0[0], ly = org[1] - org0[1], lz = (D == 3) ? org[2] - org0[2] : 0;
+#pragma unroll 1
+        for (int kz = 0; kz < (D == 3 ? W : 1); ++kz) {
+            const C cz = (D == 3) ? cscale(c, wt[D == 3 ? 2 : 0][kz]) : c;
 #pragma unroll
-            for (int d = 0; d < D; ++d) l[d] = org[d] + shift[q][d] - org0[d];
-            const int kz0 = (D == 3) ? max(0, -l[2]) : 0, kz1 = (D == 3) ? min(W, ext[2] - l[2]) : 1;
-            const int ky0 = max(0, -l[1]), ky1 = min(W, ext[1] - l[1]);
-            const int kx0 = max(0, -l[0]), kx1 = min(W, ext[0] - l[0]);
-            for (int kz = kz0; kz < kz1; ++kz) {
-                const C cz = (D == 3) ? cscale(c, wt[D == 3 ? 2 : 0][kz]) : c;
-                for (int ky = ky0; ky < ky1; ++ky) {
-                    const C cy = cscale(cz, wt[1][ky]);
-                    T* row = tile + 2 * (((l[2] + kz) * SPREAD_BIN + (l[1] + ky)) * SPREAD_BIN + l[0]);
-                    for (int kx = kx0; kx < kx1; ++kx) {
-                        atomicAdd(row + 2 * kx, cy.x * wt[0][kx]);
-                        atomicAdd(row + 2 * kx + 1, cy.y * wt[0][kx]);
-                    }
+            for (int ky = 0; ky < W; ++ky) {
+                const C cy = cscale(cz, wt[1][ky]);
+                T* row = tile + 2 * (((lz + kz) * PS + (ly + ky)) * PS + lx);
+#pragma unroll
+                for (int kx = 0; kx < W; ++kx) {
+                    atomicAdd(row + 2 * kx, cy.x * wt[0][kx]);
+                    atomicAdd(row + 2 * kx + 1, cy.y * wt[0][kx]);
                 }
             }
         }
@@ -388,12 +363,12 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<T> a, BinArgs b
     __syncthreads();
     C* out = a.out + (int64_t)b * a.out_rot_stride;
     for (int li = threadIdx.x; li < CELLS; li += blockDim.x) {
-        const int x = li % SPREAD_BIN, y = (li / SPREAD_BIN) % SPREAD_BIN, z = li / (SPREAD_BIN * SPREAD_BIN);
-        if (x < ext[0] && y < ext[1] && z < ext[2]) {
-            int64_t o = (int64_t)(org0[1] + y) * s + (org0[0] + x);
-            if (D == 3) o += (int64_t)(org0[2] + z) * s * s;
-            out[o] = mk(tile[2 * li], tile[2 * li + 1]);
-        }
+        const C v = mk(tile[2 * li], tile[2 * li + 1]);
+        if (v.x == T(0) && v.y == T(0)) continue;
+        const int x = li % PS, y = (li / PS) % PS, z = li / (PS * PS);
+        int64_t o = (int64_t)wrap_index(org0[1] + y, s) * s + wrap_index(org0[0] + x, s);
+        if (D == 3) o += (int64_t)wrap_index(org0[2] + z, s) * s * s;
+        atomic_cadd(out + o, v);
     }
 }
 
@@ -758,7 +733,7 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
         note_launch();                                                            \
         return cudaGetLastError();
     switch (a.w) {
-        SD_BIN_CASE(4) SD_BIN_CASE(5) SD_BIN_CASE(6) SD_BIN_CASE(7) SD_BIN_CASE(8)
+        SD_BIN_CASE(4) SD_BIN_CASE(5) SD_BIN_CASE(6) SD_BIN_CASE(7)
     }
 #undef SD_BIN_CASE
     return cudaErrorInvalidValue;
