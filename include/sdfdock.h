@@ -111,8 +111,9 @@ const char* sd_last_error(const sd_ctx* ctx);
  * needs a non-NULL stream; the first call with given arguments runs eagerly,
  * later ones capture once and replay), "plain" (1: one rotation per batch, no
  * graph), "timing" (1: CUDA-event timing of every pass, see sd_pass_times),
- * "spread_direct" (1: spread with one global atomic per kernel tap instead of
- * shared-memory tiles). */
+ * "spread_direct" (1, the default: spread with global vector atomics per kernel
+ * row; 0: sort the samples into 8^d-cell bins and accumulate each bin's taps in
+ * shared memory first). */
 int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
 
 /* ---- shapes: the sampled SDF (Section 4, Eq. 10A-17t) ------------------- */

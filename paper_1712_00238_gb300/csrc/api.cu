@@ -57,7 +57,7 @@ struct sd_ctx {
     int64_t opt_batch = 0;
     int opt_graph = 0;
     int opt_plain = 0;
-    int opt_spread_direct = 0;
+    int opt_spread_direct = 1;  // 0: spread by bins
     DevBuf ws[8];
     std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
     std::map<std::tuple<int, int, int, double>, double*> deconv;

@@ -46,6 +46,71 @@ __device__ __forceinline__ int wrap_index(int a, int s) {
     return a < 0 ? a + s : a;
 }
 
+// Adds the taps of one sample to the sub-box with global atomics.  Along x the
+// six (or W) cells of a row are added two at a time with one 16-byte vector
+// atomic on an even-aligned cell pair (the out-of-row half of an edge pair adds
+// zero), which cuts the L2 atomic operations of a row from W to about W/2 + 1.
+// Rows that wrap around a periodic sub-box use one atomic per cell.
+__device__ __forceinline__ void add_pair(float2* cell_even, float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    atomicAdd(reinterpret_cast<float4*>(cell_even), make_float4(a.x, a.y, b.x, b.y));
+#else
+    atomic_cadd(cell_even, a);
+    atomic_cadd(cell_even + 1, b);
+#endif
+}
+__device__ __forceinline__ void add_pair(double2* cell_even, double2 a, double2 b) {
+    atomic_cadd(cell_even, a);
+    atomic_cadd(cell_even + 1, b);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void spread_row(cplx<T>* row, int s, int ax0, bool wraps, cplx<T> cy, const T* wx) {
+    using C = cplx<T>;
+    if (wraps || sizeof(T) == 8) {
+#pragma unroll
+        for (int kx = 0; kx < W; ++kx) atomic_cadd(row + wrap_index(ax0 + kx, s), cscale(cy, wx[kx]));
+        return;
+    }
+    const C zero = mk(T(0), T(0));
+    if ((ax0 & 1) == 0) {
+#pragma unroll
+        for (int kx = 0; kx < W; kx += 2)
+            add_pair(row + ax0 + kx, cscale(cy, wx[kx]), kx + 1 < W ? cscale(cy, wx[kx + 1]) : zero);
+    } else {
+        add_pair(row + ax0 - 1, zero, cscale(cy, wx[0]));
+#pragma unroll
+        for (int kx = 1; kx < W; kx += 2)
+            add_pair(row + ax0 + kx, cscale(cy, wx[kx]), kx + 1 < W ? cscale(cy, wx[kx + 1]) : zero);
+    }
+}
+
+template <typename T, int D, int W>
+__device__ __forceinline__ void spread_direct(cplx<T>* out, int s, int s_h, const int* u0, const T (*wt)[W],
+                                              cplx<T> c) {
+    using C = cplx<T>;
+    int ax0 = u0[0] + s_h;
+    const bool wraps = (ax0 < 0) || (ax0 + W > s);
+    ax0 = wrap_index(ax0, s);
+    int iy[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) iy[k] = wrap_index(u0[1] + k + s_h, s);
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int ky = 0; ky < W; ++ky)
+            spread_row<T, W>(out + (int64_t)iy[ky] * s, s, ax0, wraps, cscale(c, wt[1][ky]), wt[0]);
+    } else {
+#pragma unroll 1
+        for (int kz = 0; kz < W; ++kz) {
+            const C cz = cscale(c, wt[2][kz]);
+            C* plane = out + (int64_t)wrap_index(u0[2] + kz + s_h, s) * s * s;
+#pragma unroll
+            for (int ky = 0; ky < W; ++ky)
+                spread_row<T, W>(plane + (int64_t)iy[ky] * s, s, ax0, wraps, cscale(cz, wt[1][ky]), wt[0]);
+        }
+    }
+}
+
 // One CTA spreads 256 consecutive samples.  Because the samples are stored in
 // Morton order, their taps after rotation usually fit a small box: the CTA
 // accumulates them there in shared memory (shared atomics) and then adds the
@@ -172,33 +237,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a, int cap_cells) 
         return;
     }
     if (!live) return;
-    int ix[D][W];
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-#pragma unroll
-        for (int k = 0; k < W; ++k) ix[d][k] = wrap_index(u0[d] + k + a.s_h, s);
-    if constexpr (D == 2) {
-#pragma unroll
-        for (int ky = 0; ky < W; ++ky) {
-            const C cy = cscale(c, wt[1][ky]);
-            C* row = out + (int64_t)ix[1][ky] * s;
-#pragma unroll
-            for (int kx = 0; kx < W; ++kx) atomic_cadd(row + ix[0][kx], cscale(cy, wt[0][kx]));
-        }
-    } else {
-#pragma unroll 1
-        for (int kz = 0; kz < W; ++kz) {
-            const C cz = cscale(c, wt[2][kz]);
-            C* plane = out + (int64_t)ix[2][kz] * s * s;
-#pragma unroll
-            for (int ky = 0; ky < W; ++ky) {
-                const C cy = cscale(cz, wt[1][ky]);
-                C* row = plane + (int64_t)ix[1][ky] * s;
-#pragma unroll
-                for (int kx = 0; kx < W; ++kx) atomic_cadd(row + ix[0][kx], cscale(cy, wt[0][kx]));
-            }
-        }
-    }
+    spread_direct<T, D, W>(a.out + (int64_t)b * a.out_rot_stride, s, a.s_h, u0, wt, c);
 }
 
 // ---------------------------------------------------------------------------
