@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0, help="rotations per batch (0: automatic)")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
-    ap.add_argument("--spread-direct", type=int, default=0, help="one global atomic per spreading tap")
+    ap.add_argument("--spread-direct", type=int, default=1, help="1: global vector atomics; 0: spread by bins")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -343,7 +343,7 @@ def run_ours(args):
                                "576 Hopf rotations; top-10 + FP64 re-score; 20-step gradient refinement",
                    "rotations": n_rot, "translations": w.N ** 3, "sub_box": s,
                    "batch": args.batch, "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": "direct atomics" if args.spread_direct else "shared-memory tiles",
+                   "spread": "global vector atomics" if args.spread_direct else "binned shared-memory tiles",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
