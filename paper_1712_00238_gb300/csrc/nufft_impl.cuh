@@ -17,6 +17,7 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -628,6 +629,289 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// pipelined passes: persistent CTAs that double-buffer their input tiles with
+// asynchronous 16-byte copies (cp.async), so the next tile streams in while the
+// current one is transformed
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Row passes.  Tile = TR consecutive rows of one rotation; rows are contiguous
+// (in_row_stride == len_in), so a tile is one contiguous run of TR*len_in
+// elements.  Stage layout: [row][e], dense.
+template <typename T, int LEN, int MODE>
+__global__ void __launch_bounds__(256) k_rows_p(RowArgs<T> a, int tiles_per_rot, int total_tiles) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr bool INV = (MODE != ROW_FWD);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TR * LD;
+    C* stage = tw + ((NTW + 1) & ~1);  // 16-byte aligned
+    const int stage_elems = TR * a.len_in;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
+    constexpr int EPC = 16 / (int)sizeof(C);  // elements per 16-byte chunk
+
+    auto issue = [&](int t, int slot) {
+        const int b = t / tiles_per_rot;
+        const int row0 = (t - b * tiles_per_rot) * TR;
+        const int rows = min(TR, a.nrows - row0);
+        const C* src = a.in + (int64_t)b * a.in_rot_stride + (int64_t)row0 * a.len_in;
+        C* dst = stage + slot * stage_elems;
+        const int chunks = rows * a.len_in / EPC;
+        for (int q = threadIdx.x; q < chunks; q += blockDim.x) cp_async16(dst + q * EPC, src + q * EPC);
+    };
+
+    int t = blockIdx.x;
+    if (t < total_tiles) issue(t, 0);
+    cp_async_commit();
+    for (int it = 0; t < total_tiles; ++it) {
+        const int tn = t + gridDim.x;
+        if (tn < total_tiles) issue(tn, (it + 1) & 1);
+        cp_async_commit();
+        cp_async_wait_1();
+        __syncthreads();
+        const int b = t / tiles_per_rot;
+        const int tl = t - b * tiles_per_rot;
+        const int row0 = tl * TR;
+        const C* st = stage + (it & 1) * stage_elems;
+        const C zero = mk(T(0), T(0));
+        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+            const int r = idx / LEN;
+            const int pos = idx - r * LEN;
+            C v = zero;
+            if (row0 + r < a.nrows) {
+                const C* src = st + r * a.len_in;
+                if constexpr (MODE == ROW_FWD) {
+                    int e = pos + a.s_h;
+                    if (e >= LEN) e -= LEN;
+                    if (e < a.len_in) v = src[e];
+                } else if constexpr (MODE == ROW_EXPAND) {
+                    const int hN = a.N >> 1;
+                    const int e = pos < hN ? pos : (pos >= LEN - hN ? pos - LEN + a.N : -1);
+                    if (e >= 0) v = src[e];
+                } else {
+                    v = src[pos];
+                }
+            }
+            buf[r * LD + pad(pos)] = v;
+        }
+        __syncthreads();
+        fft_inplace<C, LEN, INV, TR>(buf, LD, tw);
+        C* out = a.out + (int64_t)b * a.out_rot_stride;
+        if constexpr (MODE == ROW_FWD) {
+            const int N = a.N, hN = N >> 1;
+            for (int idx = threadIdx.x; idx < TR * N; idx += blockDim.x) {
+                const int r = idx / N;
+                const int kp = idx - r * N;
+                const int row = row0 + r;
+                if (row < a.nrows) {
+                    const int pos = kp < hN ? kp : kp - N + LEN;
+                    out[(int64_t)row * a.out_row_stride + kp] = buf[r * LD + pad(pos)];
+                }
+            }
+        } else if constexpr (MODE == ROW_INV_MAP || MODE == ROW_EXPAND) {
+            for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+                const int r = idx / LEN;
+                const int e = idx - r * LEN;
+                const int row = row0 + r;
+                if (row < a.nrows) out[(int64_t)row * a.out_row_stride + e] = buf[r * LD + pad(e)];
+            }
+        } else {  // ROW_INV_ARGMAX
+            T best = -INFINITY;
+            int bidx = INT_MAX;
+            for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
+                const int r = idx / LEN;
+                const int e = idx - r * LEN;
+                const int row = row0 + r;
+                if (row < a.nrows) {
+                    const T v = buf[r * LD + pad(e)].x;
+                    const int gi = row * LEN + e;
+                    if (v > best || (v == best && gi < bidx)) {
+                        best = v;
+                        bidx = gi;
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+                if (ob > best || (ob == best && oi < bidx)) {
+                    best = ob;
+                    bidx = oi;
+                }
+            }
+            __shared__ T wb[32];
+            __shared__ int wi[32];
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) {
+                wb[warp] = best;
+                wi[warp] = bidx;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int nw = (blockDim.x + 31) >> 5;
+                best = lane < nw ? wb[lane] : T(-INFINITY);
+                bidx = lane < nw ? wi[lane] : INT_MAX;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const T ob = __shfl_down_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+                    if (ob > best || (ob == best && oi < bidx)) {
+                        best = ob;
+                        bidx = oi;
+                    }
+                }
+                if (lane == 0) {
+                    const int64_t o = (int64_t)b * tiles_per_rot + tl;
+                    a.part_score[o] = (double)best;
+                    a.part_idx[o] = bidx;
+                }
+            }
+        }
+        __syncthreads();  // buf and this stage slot are reused by the next tile
+        t = tn;
+    }
+}
+
+// Column passes.  Tile = TC adjacent columns of one (rotation, outer) slab; each
+// line element row of the tile is TC contiguous elements.  Stage layout: [e][col].
+template <typename T, int LENF, int LENI, int MODE>
+__global__ void __launch_bounds__(256) k_cols_p(ColArgs<T> a, int col_tiles, int total_tiles) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LENF>();
+    constexpr int LD = line_pitch(LENF);
+    constexpr int NTWF = tw_count(LENF);
+    constexpr int NTWI = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
+    constexpr int EPC = 16 / (int)sizeof(C);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* twF = buf + TC * LD;
+    C* twI = twF + NTWF;
+    C* stage = twI + ((NTWI + NTWF + 1) & ~1) - NTWF;  // 16-byte aligned past both tables
+    const int L = a.len_in;  // line elements loaded per column
+    const int stage_elems = L * TC;
+    for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
+    if constexpr (MODE == COL_FUSED)
+        for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
+    const int ncols = a.ncols;
+    const int per_rot = col_tiles * a.nouter;
+
+    auto issue = [&](int t, int slot) {
+        const int b = t / per_rot;
+        const int rem = t - b * per_rot;
+        const int outer = rem / col_tiles;
+        const int col0 = (rem - outer * col_tiles) * TC;
+        const int cols = min(TC, ncols - col0);
+        const int cpr = cols / EPC;  // 16-byte chunks per line element
+        const C* src = a.in + (int64_t)b * a.in_rot_stride + (int64_t)outer * a.in_outer_stride + col0;
+        C* dst = stage + slot * stage_elems;
+        const int chunks = L * cpr;
+        for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+            const int e = q / cpr;
+            const int c = (q - e * cpr) * EPC;
+            cp_async16(dst + e * TC + c, src + (int64_t)e * ncols + c);
+        }
+    };
+
+    int t = blockIdx.x;
+    if (t < total_tiles) issue(t, 0);
+    cp_async_commit();
+    const int hN = a.N >> 1;
+    const C zero = mk(T(0), T(0));
+    for (int it = 0; t < total_tiles; ++it) {
+        const int tn = t + gridDim.x;
+        if (tn < total_tiles) issue(tn, (it + 1) & 1);
+        cp_async_commit();
+        cp_async_wait_1();
+        __syncthreads();
+        const int b = t / per_rot;
+        const int rem = t - b * per_rot;
+        const int outer = rem / col_tiles;
+        const int col0 = (rem - outer * col_tiles) * TC;
+        const C* st = stage + (it & 1) * stage_elems;
+        for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
+            const int col = idx % TC;
+            const int pos = idx / TC;
+            int e;
+            if constexpr (MODE == COL_FWD || MODE == COL_FUSED) {
+                e = pos + a.s_h;
+                if (e >= LENF) e -= LENF;
+                if (e >= L) e = -1;
+            } else if constexpr (MODE == COL_EXPAND) {
+                e = pos < hN ? pos : (pos >= LENF - hN ? pos - LENF + a.N : -1);
+            } else {
+                e = pos;
+            }
+            buf[col * LD + pad(pos)] = (e >= 0 && col0 + col < ncols) ? st[e * TC + col] : zero;
+        }
+        __syncthreads();
+        constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
+        fft_inplace<C, LENF, INV1, TC>(buf, LD, twF);
+        C* out = a.out + (int64_t)b * a.out_rot_stride + (int64_t)outer * a.out_outer_stride;
+        if constexpr (MODE == COL_FWD) {
+            for (int idx = threadIdx.x; idx < TC * a.N; idx += blockDim.x) {
+                const int col = idx % TC;
+                const int kp = idx / TC;
+                const int gcol = col0 + col;
+                if (gcol < ncols) {
+                    const int pos = kp < hN ? kp : kp - a.N + LENF;
+                    out[(int64_t)kp * ncols + gcol] = buf[col * LD + pad(pos)];
+                }
+            }
+        } else if constexpr (MODE == COL_INV || MODE == COL_EXPAND) {
+            for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
+                const int col = idx % TC;
+                const int e = idx / TC;
+                const int gcol = col0 + col;
+                if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
+            }
+        } else {  // COL_FUSED
+            constexpr int PERX = (TC * LENI + FFT_THREADS - 1) / FFT_THREADS;
+            C v[PERX];
+#pragma unroll
+            for (int q = 0; q < PERX; ++q) {
+                const int idx = threadIdx.x + q * FFT_THREADS;
+                v[q] = zero;
+                if (idx < TC * LENI) {
+                    const int col = idx % TC;
+                    const int kp = idx / TC;
+                    const int gcol = col0 + col;
+                    if (gcol < ncols) {
+                        const int pos = kp < hN ? kp : kp - LENI + LENF;
+                        v[q] = cmul(buf[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < PERX; ++q) {
+                const int idx = threadIdx.x + q * FFT_THREADS;
+                if (idx < TC * LENI) buf[(idx % TC) * LD + pad(idx / TC)] = v[q];
+            }
+            __syncthreads();
+            fft_inplace<C, LENI, true, TC>(buf, LD, twI);
+            for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
+                const int col = idx % TC;
+                const int e = idx / TC;
+                const int gcol = col0 + col;
+                if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
+            }
+        }
+        __syncthreads();
+        t = tn;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 
@@ -647,17 +931,48 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return e;
 }
 
+// Persistent grid: as many CTAs as fit on the device at once, capped by the tiles.
+template <typename K>
+static int persistent_grid(K kernel, size_t smem, int tiles) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm <= 0)
+        per_sm = 1;
+    return std::max(1, std::min(tiles, sms * per_sm));
+}
+
 template <typename T, int LEN, int MODE>
 static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
     using C = cplx<T>;
     constexpr int TR = lines_per_cta<T, LEN>();
+    const int nb = (a.nrows + TR - 1) / TR;
+    if (nparts) *nparts = nb;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    const bool aligned = (a.in_row_stride == a.len_in) && ((a.len_in * (int)sizeof(C)) % 16 == 0) &&
+                         ((a.in_rot_stride * (int64_t)sizeof(C)) % 16 == 0) &&
+                         ((reinterpret_cast<uintptr_t>(a.in) & 15) == 0);
+    if (aligned) {
+        const int ntw = tw_count(LEN);
+        const size_t smem =
+            (size_t)(TR * line_pitch(LEN) + ((ntw + 1) & ~1) + 2 * TR * a.len_in) * sizeof(C);
+        auto kern = k_rows_p<T, LEN, MODE>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        const int total = nb * batch;
+        kern<<<persistent_grid(kern, smem, total), 256, smem, st>>>(a, nb, total);
+        note_launch();
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
     auto kern = k_rows<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const int nb = (a.nrows + TR - 1) / TR;
-    if (nparts) *nparts = nb;
-    if (nb == 0 || batch == 0) return cudaSuccess;
     kern<<<dim3(nb, batch), 256, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
@@ -667,12 +982,29 @@ template <typename T, int LENF, int LENI, int MODE>
 static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     using C = cplx<T>;
     constexpr int TC = lines_per_cta<T, LENF>();
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
+    const int epc = 16 / (int)sizeof(C);
+    const bool aligned = (a.ncols % TC == 0 || (a.ncols % TC) % epc == 0) && (a.ncols % epc == 0) &&
+                         ((a.in_rot_stride * (int64_t)sizeof(C)) % 16 == 0) &&
+                         ((a.in_outer_stride * (int64_t)sizeof(C)) % 16 == 0) &&
+                         ((reinterpret_cast<uintptr_t>(a.in) & 15) == 0) && a.len_in <= LENF;
+    const int ntwf = tw_count(LENF), ntwi = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
+    if (aligned) {
+        const size_t smem =
+            (size_t)(TC * line_pitch(LENF) + ((ntwf + ntwi + 1) & ~1) + 2 * (size_t)a.len_in * TC) * sizeof(C);
+        auto kern = k_cols_p<T, LENF, LENI, MODE>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        const int total = nb * a.nouter * batch;
+        kern<<<persistent_grid(kern, smem, total), 256, smem, st>>>(a, nb, total);
+        note_launch();
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)(TC * line_pitch(LENF) + tw_count(LENF) + tw_count(LENI)) * sizeof(C);
     auto kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const int nb = (a.ncols + TC - 1) / TC;
-    if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
     kern<<<dim3(nb, a.nouter, batch), 256, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
