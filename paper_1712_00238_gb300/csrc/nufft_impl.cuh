@@ -932,24 +932,26 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // Persistent grid: as many CTAs as fit on the device at once, capped by the tiles.
+// A failed query is cleared and falls back to one CTA per SM.
 template <typename K>
 static int persistent_grid(K kernel, size_t smem, int tiles) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 1;
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm <= 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
         per_sm = 1;
+    }
     return std::max(1, std::min(tiles, sms * per_sm));
 }
 
 template <typename T, int LEN, int MODE>
 static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
     using C = cplx<T>;
+    if (cudaPeekAtLastError() != cudaSuccess) return cudaErrorUnknown;  // an earlier call left an error
     constexpr int TR = lines_per_cta<T, LEN>();
     const int nb = (a.nrows + TR - 1) / TR;
     if (nparts) *nparts = nb;
@@ -981,6 +983,7 @@ static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaSt
 template <typename T, int LENF, int LENI, int MODE>
 static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     using C = cplx<T>;
+    if (cudaPeekAtLastError() != cudaSuccess) return cudaErrorUnknown;  // an earlier call left an error
     constexpr int TC = lines_per_cta<T, LENF>();
     const int nb = (a.ncols + TC - 1) / TC;
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
