@@ -18,6 +18,7 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -915,19 +916,22 @@ __global__ void __launch_bounds__(256) k_cols_p(ColArgs<T> a, int col_tiles, int
 // launch helpers
 // ---------------------------------------------------------------------------
 
-// Opt a kernel into more than 48 KiB of dynamic shared memory, once per device.
+// Opt a kernel into more than 48 KiB of dynamic shared memory.  The attribute
+// is one value per kernel and device, so it only ever grows: a launch with less
+// shared memory than the current cap needs no change.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     static std::mutex mu;
-    static std::set<std::tuple<int, const void*, size_t>> done;
+    static std::map<std::pair<int, const void*>, size_t> cap;
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, (const void*)kernel, bytes);
+    const auto key = std::make_pair(dev, (const void*)kernel);
     std::lock_guard<std::mutex> lock(mu);
-    if (done.count(key)) return cudaSuccess;
+    auto it = cap.find(key);
+    if (it != cap.end() && it->second >= bytes) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done.insert(key);
+    if (e == cudaSuccess) cap[key] = bytes;
     return e;
 }
 
