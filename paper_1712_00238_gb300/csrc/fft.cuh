@@ -231,6 +231,77 @@ __device__ __forceinline__ void fft_inplace(C* buf, int ld, const C* tw) {
 }
 #endif
 
+#ifdef __CUDACC__
+// Line transforms whose first stage reads its inputs through a loader (global
+// memory, registers in flight) and whose last stage hands its outputs to an
+// emitter (global memory or the next step), so only the stages in between go
+// through shared memory: one round trip for two-stage lengths.
+//
+// LAY_ROW: lines are contiguous (a warp's lanes take consecutive butterflies of
+// one line); LAY_COL: lines are columns (lanes take consecutive lines).  NL lines
+// per block of FFT_THREADS threads.  load(line, pos) returns input `pos`;
+// emit(line, o, v) receives output `o` (natural order).  SRC_SMEM: the inputs
+// are already in `buf` (pitch ld, padded) and are read from there.
+enum { LAY_ROW = 0, LAY_COL = 1 };
+
+template <int LAY, int NL, int NB>
+__device__ __forceinline__ void butterfly_of(int t, int& line, int& i) {
+    if constexpr (LAY == LAY_ROW) {
+        line = t / NB;
+        i = t - line * NB;
+    } else {
+        i = t / NL;
+        line = t - i * NL;
+    }
+}
+
+template <typename C, int LEN, bool INV, int NL, int LAY, bool SRC_SMEM, int S = 0, int P = 1, typename Load,
+          typename Emit>
+__device__ __forceinline__ void fft_lines_io(C* buf, int ld, const C* tw, Load& load, Emit& emit) {
+    constexpr int R = plan_radix(LEN, S);
+    constexpr bool first = (S == 0);
+    constexpr bool last = (plan_radix(LEN, S + 1) == 0);
+    constexpr int NB = LEN / R;
+    constexpr int TOT = NL * NB;
+    constexpr int PER = (TOT + FFT_THREADS - 1) / FFT_THREADS;
+    C v[PER][R];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int t = threadIdx.x + q * FFT_THREADS;
+        if (TOT % FFT_THREADS == 0 || t < TOT) {
+            int line, i;
+            butterfly_of<LAY, NL, NB>(t, line, i);
+            if constexpr (first && !SRC_SMEM) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q][r] = load(line, i + r * NB);
+                dft<R, INV>(v[q]);
+            } else {
+                stockham_load<C, LEN, R, P, INV>(buf + line * ld, i, tw + tw_offset(LEN, S), v[q]);
+            }
+        }
+    }
+    if constexpr (!first || SRC_SMEM) __syncthreads();  // every read of buf before any write
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int t = threadIdx.x + q * FFT_THREADS;
+        if (TOT % FFT_THREADS == 0 || t < TOT) {
+            int line, i;
+            butterfly_of<LAY, NL, NB>(t, line, i);
+            if constexpr (last) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) emit(line, i + r * P, v[q][r]);  // P = NB here
+            } else {
+                stockham_store<C, LEN, R, P>(buf + line * ld, i, v[q]);
+            }
+        }
+    }
+    if constexpr (!last) {
+        __syncthreads();
+        fft_lines_io<C, LEN, INV, NL, LAY, SRC_SMEM, S + 1, P * R>(buf, ld, tw, load, emit);
+    }
+}
+#endif
+
 // Host execution of the same stage sequence on one line, in place (used by the
 // library's self-test of the index arithmetic).
 template <typename C, int LEN, bool INV, int S = 0, int P = 1>

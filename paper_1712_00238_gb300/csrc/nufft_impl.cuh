@@ -414,9 +414,50 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<T> a, BinArgs b
 }
 
 // ---------------------------------------------------------------------------
-// row passes (lines contiguous in memory)
+// line passes: the first FFT stage reads global memory into registers and the
+// last stage writes global memory from registers; stages in between (and the
+// product step of the fused pass) go through shared memory
 // ---------------------------------------------------------------------------
 
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& best, int& bidx, T v, int i) {
+    if (v > best || (v == best && i < bidx)) {
+        best = v;
+        bidx = i;
+    }
+}
+
+// Block-wide (max value, lowest index); the result is valid in thread 0.
+template <typename T>
+__device__ __forceinline__ void block_argmax(T& best, int& bidx) {
+    __shared__ T wb[32];
+    __shared__ int wi[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        argmax_merge(best, bidx, ob, oi);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        wb[warp] = best;
+        wi[warp] = bidx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        best = lane < nw ? wb[lane] : T(-INFINITY);
+        bidx = lane < nw ? wi[lane] : INT_MAX;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const T ob = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+            argmax_merge(best, bidx, ob, oi);
+        }
+    }
+}
+
+// Row passes: TR consecutive rows of one rotation per CTA.
 template <typename T, int LEN, int MODE>
 __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
     using C = cplx<T>;
@@ -430,110 +471,52 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
     const int b = blockIdx.y;
     const int row0 = blockIdx.x * TR;
     for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
-    const C* in = a.in + (int64_t)b * a.in_rot_stride;
-    const C zero = mk(T(0), T(0));
-    for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-        const int r = idx / LEN;
-        const int pos = idx - r * LEN;
-        const int row = row0 + r;
-        C v = zero;
-        if (row < a.nrows) {
-            const C* src = in + (int64_t)row * a.in_row_stride;
-            if constexpr (MODE == ROW_FWD) {
-                int e = pos + a.s_h;
-                if (e >= LEN) e -= LEN;
-                if (e < a.len_in) v = src[e];
-            } else if constexpr (MODE == ROW_EXPAND) {
-                const int hN = a.N >> 1;
-                const int e = pos < hN ? pos : (pos >= LEN - hN ? pos - LEN + a.N : -1);
-                if (e >= 0) v = src[e];
-            } else {
-                v = src[pos];
-            }
-        }
-        buf[r * LD + pad(pos)] = v;
-    }
     __syncthreads();
-    fft_inplace<C, LEN, INV, TR>(buf, LD, tw);
-    const C* res = buf;
+    const C* in = a.in + (int64_t)b * a.in_rot_stride;
     C* out = a.out + (int64_t)b * a.out_rot_stride;
-    if constexpr (MODE == ROW_FWD) {
-        const int N = a.N, hN = N >> 1;
-        for (int idx = threadIdx.x; idx < TR * N; idx += blockDim.x) {
-            const int r = idx / N;
-            const int kp = idx - r * N;
-            const int row = row0 + r;
-            if (row < a.nrows) {
-                const int pos = kp < hN ? kp : kp - N + LEN;
-                out[(int64_t)row * a.out_row_stride + kp] = res[r * LD + pad(pos)];
-            }
+    const C zero = mk(T(0), T(0));
+    const int N = a.N, hN = N >> 1;
+    auto load = [&](int line, int pos) -> C {
+        const int row = row0 + line;
+        if (row >= a.nrows) return zero;
+        const C* src = in + (int64_t)row * a.in_row_stride;
+        if constexpr (MODE == ROW_FWD) {
+            int e = pos + a.s_h;
+            if (e >= LEN) e -= LEN;
+            return e < a.len_in ? src[e] : zero;
+        } else if constexpr (MODE == ROW_EXPAND) {
+            const int e = pos < hN ? pos : (pos >= LEN - hN ? pos - LEN + N : -1);
+            return e >= 0 ? src[e] : zero;
+        } else {
+            return src[pos];
         }
-    } else if constexpr (MODE == ROW_INV_MAP || MODE == ROW_EXPAND) {
-        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-            const int r = idx / LEN;
-            const int e = idx - r * LEN;
-            const int row = row0 + r;
-            if (row < a.nrows) out[(int64_t)row * a.out_row_stride + e] = res[r * LD + pad(e)];
+    };
+    T best = -INFINITY;
+    int bidx = INT_MAX;
+    auto emit = [&](int line, int o, C v) {
+        const int row = row0 + line;
+        if (row >= a.nrows) return;
+        if constexpr (MODE == ROW_FWD) {
+            const int kp = o < hN ? o : (o >= LEN - hN ? o - LEN + N : -1);
+            if (kp >= 0) out[(int64_t)row * a.out_row_stride + kp] = v;
+        } else if constexpr (MODE == ROW_INV_ARGMAX) {
+            argmax_merge(best, bidx, v.x, row * LEN + o);
+        } else {
+            out[(int64_t)row * a.out_row_stride + o] = v;
         }
-    } else {  // ROW_INV_ARGMAX: best (max Re, lowest index) of this tile
-        T best = -INFINITY;
-        int bidx = INT_MAX;
-        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-            const int r = idx / LEN;
-            const int e = idx - r * LEN;
-            const int row = row0 + r;
-            if (row < a.nrows) {
-                const T v = res[r * LD + pad(e)].x;
-                const int gi = row * LEN + e;
-                if (v > best || (v == best && gi < bidx)) {
-                    best = v;
-                    bidx = gi;
-                }
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const T ob = __shfl_down_sync(0xffffffffu, best, off);
-            const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-            if (ob > best || (ob == best && oi < bidx)) {
-                best = ob;
-                bidx = oi;
-            }
-        }
-        __shared__ T wb[32];
-        __shared__ int wi[32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) {
-            wb[warp] = best;
-            wi[warp] = bidx;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = (blockDim.x + 31) >> 5;
-            best = lane < nw ? wb[lane] : T(-INFINITY);
-            bidx = lane < nw ? wi[lane] : INT_MAX;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ob = __shfl_down_sync(0xffffffffu, best, off);
-                const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-                if (ob > best || (ob == best && oi < bidx)) {
-                    best = ob;
-                    bidx = oi;
-                }
-            }
-            if (lane == 0) {
-                const int64_t o = (int64_t)b * gridDim.x + blockIdx.x;
-                a.part_score[o] = (double)best;
-                a.part_idx[o] = bidx;
-            }
+    };
+    fft_lines_io<C, LEN, INV, TR, LAY_ROW, false>(buf, LD, tw, load, emit);
+    if constexpr (MODE == ROW_INV_ARGMAX) {
+        block_argmax(best, bidx);
+        if (threadIdx.x == 0) {
+            const int64_t o = (int64_t)b * gridDim.x + blockIdx.x;
+            a.part_score[o] = (double)best;
+            a.part_idx[o] = bidx;
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// column passes (lines strided; a CTA takes TC adjacent columns)
-// ---------------------------------------------------------------------------
-
+// Column passes: TC adjacent columns of one (rotation, outer) slab per CTA.
 template <typename T, int LENF, int LENI, int MODE>
 __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     using C = cplx<T>;
@@ -551,364 +534,56 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
     for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
     if constexpr (MODE == COL_FUSED)
         for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
+    __syncthreads();
     const int ncols = a.ncols;
     const C* in = a.in + (int64_t)b * a.in_rot_stride + (int64_t)outer * a.in_outer_stride;
     C* out = a.out + (int64_t)b * a.out_rot_stride + (int64_t)outer * a.out_outer_stride;
     const C zero = mk(T(0), T(0));
-    const int hN = a.N >> 1;
-    for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
-        const int col = idx % TC;
-        const int pos = idx / TC;
-        const int gcol = col0 + col;
+    const int N = a.N, hN = N >> 1;
+    constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
+    auto load = [&](int line, int pos) -> C {
+        const int gcol = col0 + line;
+        if (gcol >= ncols) return zero;
         int e;
         if constexpr (MODE == COL_FWD || MODE == COL_FUSED) {
             e = pos + a.s_h;
             if (e >= LENF) e -= LENF;
-            if (e >= a.len_in) e = -1;
+            if (e >= a.len_in) return zero;
         } else if constexpr (MODE == COL_EXPAND) {
-            e = pos < hN ? pos : (pos >= LENF - hN ? pos - LENF + a.N : -1);
+            e = pos < hN ? pos : (pos >= LENF - hN ? pos - LENF + N : -1);
+            if (e < 0) return zero;
         } else {
             e = pos;
         }
-        C v = zero;
-        if (e >= 0 && gcol < ncols) v = in[(int64_t)e * ncols + gcol];
-        buf[col * LD + pad(pos)] = v;
-    }
-    __syncthreads();
-    constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
-    fft_inplace<C, LENF, INV1, TC>(buf, LD, twF);
-    C* res = buf;
-    if constexpr (MODE == COL_FWD) {
-        for (int idx = threadIdx.x; idx < TC * a.N; idx += blockDim.x) {
-            const int col = idx % TC;
-            const int kp = idx / TC;
-            const int gcol = col0 + col;
-            if (gcol < ncols) {
-                const int pos = kp < hN ? kp : kp - a.N + LENF;
-                out[(int64_t)kp * ncols + gcol] = res[col * LD + pad(pos)];
-            }
-        }
-    } else if constexpr (MODE == COL_INV || MODE == COL_EXPAND) {
-        for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
-            const int col = idx % TC;
-            const int e = idx / TC;
-            const int gcol = col0 + col;
-            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = res[col * LD + pad(e)];
-        }
-    } else {  // COL_FUSED: keep N modes, multiply by W, inverse of length N (in place)
-        constexpr int PERX = (TC * LENI + FFT_THREADS - 1) / FFT_THREADS;
-        C v[PERX];
-#pragma unroll
-        for (int q = 0; q < PERX; ++q) {
-            const int idx = threadIdx.x + q * FFT_THREADS;
-            v[q] = zero;
-            if (idx < TC * LENI) {
-                const int col = idx % TC;
-                const int kp = idx / TC;
-                const int gcol = col0 + col;
-                if (gcol < ncols) {
-                    const int pos = kp < hN ? kp : kp - LENI + LENF;
-                    v[q] = cmul(res[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PERX; ++q) {
-            const int idx = threadIdx.x + q * FFT_THREADS;
-            if (idx < TC * LENI) buf[(idx % TC) * LD + pad(idx / TC)] = v[q];
-        }
-        __syncthreads();
-        fft_inplace<C, LENI, true, TC>(buf, LD, twI);
-        for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
-            const int col = idx % TC;
-            const int e = idx / TC;
-            const int gcol = col0 + col;
-            if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// pipelined passes: persistent CTAs that double-buffer their input tiles with
-// asynchronous 16-byte copies (cp.async), so the next tile streams in while the
-// current one is transformed
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Row passes.  Tile = TR consecutive rows of one rotation; rows are contiguous
-// (in_row_stride == len_in), so a tile is one contiguous run of TR*len_in
-// elements.  Stage layout: [row][e], dense.
-template <typename T, int LEN, int MODE>
-__global__ void __launch_bounds__(256) k_rows_p(RowArgs<T> a, int tiles_per_rot, int total_tiles) {
-    using C = cplx<T>;
-    constexpr int TR = lines_per_cta<T, LEN>();
-    constexpr int LD = line_pitch(LEN);
-    constexpr int NTW = tw_count(LEN);
-    constexpr bool INV = (MODE != ROW_FWD);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    C* tw = buf + TR * LD;
-    C* stage = tw + ((NTW + 1) & ~1);  // 16-byte aligned
-    const int stage_elems = TR * a.len_in;
-    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
-    constexpr int EPC = 16 / (int)sizeof(C);  // elements per 16-byte chunk
-
-    auto issue = [&](int t, int slot) {
-        const int b = t / tiles_per_rot;
-        const int row0 = (t - b * tiles_per_rot) * TR;
-        const int rows = min(TR, a.nrows - row0);
-        const C* src = a.in + (int64_t)b * a.in_rot_stride + (int64_t)row0 * a.len_in;
-        C* dst = stage + slot * stage_elems;
-        const int chunks = rows * a.len_in / EPC;
-        for (int q = threadIdx.x; q < chunks; q += blockDim.x) cp_async16(dst + q * EPC, src + q * EPC);
+        return in[(int64_t)e * ncols + gcol];
     };
-
-    int t = blockIdx.x;
-    if (t < total_tiles) issue(t, 0);
-    cp_async_commit();
-    for (int it = 0; t < total_tiles; ++it) {
-        const int tn = t + gridDim.x;
-        if (tn < total_tiles) issue(tn, (it + 1) & 1);
-        cp_async_commit();
-        cp_async_wait_1();
+    if constexpr (MODE == COL_FUSED) {
+        // forward: keep the N central modes, multiply by W, place them as the
+        // inverse transform's inputs
+        auto emit_fwd = [&](int line, int o, C v) {
+            const int kp = o < hN ? o : (o >= LENF - hN ? o - LENF + N : -1);
+            const int gcol = col0 + line;
+            if (kp >= 0 && gcol < ncols) buf[line * LD + pad(kp)] = cmul(v, a.W[(int64_t)kp * ncols + gcol]);
+        };
+        fft_lines_io<C, LENF, false, TC, LAY_COL, false>(buf, LD, twF, load, emit_fwd);
         __syncthreads();
-        const int b = t / tiles_per_rot;
-        const int tl = t - b * tiles_per_rot;
-        const int row0 = tl * TR;
-        const C* st = stage + (it & 1) * stage_elems;
-        const C zero = mk(T(0), T(0));
-        for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-            const int r = idx / LEN;
-            const int pos = idx - r * LEN;
-            C v = zero;
-            if (row0 + r < a.nrows) {
-                const C* src = st + r * a.len_in;
-                if constexpr (MODE == ROW_FWD) {
-                    int e = pos + a.s_h;
-                    if (e >= LEN) e -= LEN;
-                    if (e < a.len_in) v = src[e];
-                } else if constexpr (MODE == ROW_EXPAND) {
-                    const int hN = a.N >> 1;
-                    const int e = pos < hN ? pos : (pos >= LEN - hN ? pos - LEN + a.N : -1);
-                    if (e >= 0) v = src[e];
-                } else {
-                    v = src[pos];
-                }
-            }
-            buf[r * LD + pad(pos)] = v;
-        }
-        __syncthreads();
-        fft_inplace<C, LEN, INV, TR>(buf, LD, tw);
-        C* out = a.out + (int64_t)b * a.out_rot_stride;
-        if constexpr (MODE == ROW_FWD) {
-            const int N = a.N, hN = N >> 1;
-            for (int idx = threadIdx.x; idx < TR * N; idx += blockDim.x) {
-                const int r = idx / N;
-                const int kp = idx - r * N;
-                const int row = row0 + r;
-                if (row < a.nrows) {
-                    const int pos = kp < hN ? kp : kp - N + LEN;
-                    out[(int64_t)row * a.out_row_stride + kp] = buf[r * LD + pad(pos)];
-                }
-            }
-        } else if constexpr (MODE == ROW_INV_MAP || MODE == ROW_EXPAND) {
-            for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-                const int r = idx / LEN;
-                const int e = idx - r * LEN;
-                const int row = row0 + r;
-                if (row < a.nrows) out[(int64_t)row * a.out_row_stride + e] = buf[r * LD + pad(e)];
-            }
-        } else {  // ROW_INV_ARGMAX
-            T best = -INFINITY;
-            int bidx = INT_MAX;
-            for (int idx = threadIdx.x; idx < TR * LEN; idx += blockDim.x) {
-                const int r = idx / LEN;
-                const int e = idx - r * LEN;
-                const int row = row0 + r;
-                if (row < a.nrows) {
-                    const T v = buf[r * LD + pad(e)].x;
-                    const int gi = row * LEN + e;
-                    if (v > best || (v == best && gi < bidx)) {
-                        best = v;
-                        bidx = gi;
-                    }
-                }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ob = __shfl_down_sync(0xffffffffu, best, off);
-                const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-                if (ob > best || (ob == best && oi < bidx)) {
-                    best = ob;
-                    bidx = oi;
-                }
-            }
-            __shared__ T wb[32];
-            __shared__ int wi[32];
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) {
-                wb[warp] = best;
-                wi[warp] = bidx;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                const int nw = (blockDim.x + 31) >> 5;
-                best = lane < nw ? wb[lane] : T(-INFINITY);
-                bidx = lane < nw ? wi[lane] : INT_MAX;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const T ob = __shfl_down_sync(0xffffffffu, best, off);
-                    const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-                    if (ob > best || (ob == best && oi < bidx)) {
-                        best = ob;
-                        bidx = oi;
-                    }
-                }
-                if (lane == 0) {
-                    const int64_t o = (int64_t)b * tiles_per_rot + tl;
-                    a.part_score[o] = (double)best;
-                    a.part_idx[o] = bidx;
-                }
-            }
-        }
-        __syncthreads();  // buf and this stage slot are reused by the next tile
-        t = tn;
-    }
-}
-
-// Column passes.  Tile = TC adjacent columns of one (rotation, outer) slab; each
-// line element row of the tile is TC contiguous elements.  Stage layout: [e][col].
-template <typename T, int LENF, int LENI, int MODE>
-__global__ void __launch_bounds__(256) k_cols_p(ColArgs<T> a, int col_tiles, int total_tiles) {
-    using C = cplx<T>;
-    constexpr int TC = lines_per_cta<T, LENF>();
-    constexpr int LD = line_pitch(LENF);
-    constexpr int NTWF = tw_count(LENF);
-    constexpr int NTWI = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
-    constexpr int EPC = 16 / (int)sizeof(C);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    C* twF = buf + TC * LD;
-    C* twI = twF + NTWF;
-    C* stage = twI + ((NTWI + NTWF + 1) & ~1) - NTWF;  // 16-byte aligned past both tables
-    const int L = a.len_in;  // line elements loaded per column
-    const int stage_elems = L * TC;
-    for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
-    if constexpr (MODE == COL_FUSED)
-        for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
-    const int ncols = a.ncols;
-    const int per_rot = col_tiles * a.nouter;
-
-    auto issue = [&](int t, int slot) {
-        const int b = t / per_rot;
-        const int rem = t - b * per_rot;
-        const int outer = rem / col_tiles;
-        const int col0 = (rem - outer * col_tiles) * TC;
-        const int cols = min(TC, ncols - col0);
-        const int cpr = cols / EPC;  // 16-byte chunks per line element
-        const C* src = a.in + (int64_t)b * a.in_rot_stride + (int64_t)outer * a.in_outer_stride + col0;
-        C* dst = stage + slot * stage_elems;
-        const int chunks = L * cpr;
-        for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
-            const int e = q / cpr;
-            const int c = (q - e * cpr) * EPC;
-            cp_async16(dst + e * TC + c, src + (int64_t)e * ncols + c);
-        }
-    };
-
-    int t = blockIdx.x;
-    if (t < total_tiles) issue(t, 0);
-    cp_async_commit();
-    const int hN = a.N >> 1;
-    const C zero = mk(T(0), T(0));
-    for (int it = 0; t < total_tiles; ++it) {
-        const int tn = t + gridDim.x;
-        if (tn < total_tiles) issue(tn, (it + 1) & 1);
-        cp_async_commit();
-        cp_async_wait_1();
-        __syncthreads();
-        const int b = t / per_rot;
-        const int rem = t - b * per_rot;
-        const int outer = rem / col_tiles;
-        const int col0 = (rem - outer * col_tiles) * TC;
-        const C* st = stage + (it & 1) * stage_elems;
-        for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
-            const int col = idx % TC;
-            const int pos = idx / TC;
-            int e;
-            if constexpr (MODE == COL_FWD || MODE == COL_FUSED) {
-                e = pos + a.s_h;
-                if (e >= LENF) e -= LENF;
-                if (e >= L) e = -1;
-            } else if constexpr (MODE == COL_EXPAND) {
-                e = pos < hN ? pos : (pos >= LENF - hN ? pos - LENF + a.N : -1);
+        auto emit_out = [&](int line, int o, C v) {
+            const int gcol = col0 + line;
+            if (gcol < ncols) out[(int64_t)o * ncols + gcol] = v;
+        };
+        fft_lines_io<C, LENI, true, TC, LAY_COL, true>(buf, LD, twI, load, emit_out);
+    } else {
+        auto emit = [&](int line, int o, C v) {
+            const int gcol = col0 + line;
+            if (gcol >= ncols) return;
+            if constexpr (MODE == COL_FWD) {
+                const int kp = o < hN ? o : (o >= LENF - hN ? o - LENF + N : -1);
+                if (kp >= 0) out[(int64_t)kp * ncols + gcol] = v;
             } else {
-                e = pos;
+                out[(int64_t)o * ncols + gcol] = v;
             }
-            buf[col * LD + pad(pos)] = (e >= 0 && col0 + col < ncols) ? st[e * TC + col] : zero;
-        }
-        __syncthreads();
-        constexpr bool INV1 = (MODE == COL_INV || MODE == COL_EXPAND);
-        fft_inplace<C, LENF, INV1, TC>(buf, LD, twF);
-        C* out = a.out + (int64_t)b * a.out_rot_stride + (int64_t)outer * a.out_outer_stride;
-        if constexpr (MODE == COL_FWD) {
-            for (int idx = threadIdx.x; idx < TC * a.N; idx += blockDim.x) {
-                const int col = idx % TC;
-                const int kp = idx / TC;
-                const int gcol = col0 + col;
-                if (gcol < ncols) {
-                    const int pos = kp < hN ? kp : kp - a.N + LENF;
-                    out[(int64_t)kp * ncols + gcol] = buf[col * LD + pad(pos)];
-                }
-            }
-        } else if constexpr (MODE == COL_INV || MODE == COL_EXPAND) {
-            for (int idx = threadIdx.x; idx < TC * LENF; idx += blockDim.x) {
-                const int col = idx % TC;
-                const int e = idx / TC;
-                const int gcol = col0 + col;
-                if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
-            }
-        } else {  // COL_FUSED
-            constexpr int PERX = (TC * LENI + FFT_THREADS - 1) / FFT_THREADS;
-            C v[PERX];
-#pragma unroll
-            for (int q = 0; q < PERX; ++q) {
-                const int idx = threadIdx.x + q * FFT_THREADS;
-                v[q] = zero;
-                if (idx < TC * LENI) {
-                    const int col = idx % TC;
-                    const int kp = idx / TC;
-                    const int gcol = col0 + col;
-                    if (gcol < ncols) {
-                        const int pos = kp < hN ? kp : kp - LENI + LENF;
-                        v[q] = cmul(buf[col * LD + pad(pos)], a.W[(int64_t)kp * ncols + gcol]);
-                    }
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < PERX; ++q) {
-                const int idx = threadIdx.x + q * FFT_THREADS;
-                if (idx < TC * LENI) buf[(idx % TC) * LD + pad(idx / TC)] = v[q];
-            }
-            __syncthreads();
-            fft_inplace<C, LENI, true, TC>(buf, LD, twI);
-            for (int idx = threadIdx.x; idx < TC * LENI; idx += blockDim.x) {
-                const int col = idx % TC;
-                const int e = idx / TC;
-                const int gcol = col0 + col;
-                if (gcol < ncols) out[(int64_t)e * ncols + gcol] = buf[col * LD + pad(e)];
-            }
-        }
-        __syncthreads();
-        t = tn;
+        };
+        fft_lines_io<C, LENF, INV1, TC, LAY_COL, false>(buf, LD, twF, load, emit);
     }
 }
 
@@ -935,46 +610,13 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return e;
 }
 
-// Persistent grid: as many CTAs as fit on the device at once, capped by the tiles.
-// A failed query is cleared and falls back to one CTA per SM.
-template <typename K>
-static int persistent_grid(K kernel, size_t smem, int tiles) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
-        cudaGetLastError();
-        sms = 1;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm <= 0) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    return std::max(1, std::min(tiles, sms * per_sm));
-}
-
 template <typename T, int LEN, int MODE>
 static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
     using C = cplx<T>;
-    if (cudaPeekAtLastError() != cudaSuccess) return cudaErrorUnknown;  // an earlier call left an error
     constexpr int TR = lines_per_cta<T, LEN>();
     const int nb = (a.nrows + TR - 1) / TR;
     if (nparts) *nparts = nb;
     if (nb == 0 || batch == 0) return cudaSuccess;
-    const bool aligned = (a.in_row_stride == a.len_in) && ((a.len_in * (int)sizeof(C)) % 16 == 0) &&
-                         ((a.in_rot_stride * (int64_t)sizeof(C)) % 16 == 0) &&
-                         ((reinterpret_cast<uintptr_t>(a.in) & 15) == 0);
-    if (aligned) {
-        const int ntw = tw_count(LEN);
-        const size_t smem =
-            (size_t)(TR * line_pitch(LEN) + ((ntw + 1) & ~1) + 2 * TR * a.len_in) * sizeof(C);
-        auto kern = k_rows_p<T, LEN, MODE>;
-        cudaError_t e = set_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        const int total = nb * batch;
-        kern<<<persistent_grid(kern, smem, total), 256, smem, st>>>(a, nb, total);
-        note_launch();
-        return cudaGetLastError();
-    }
     const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
     auto kern = k_rows<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
@@ -987,27 +629,9 @@ static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaSt
 template <typename T, int LENF, int LENI, int MODE>
 static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     using C = cplx<T>;
-    if (cudaPeekAtLastError() != cudaSuccess) return cudaErrorUnknown;  // an earlier call left an error
     constexpr int TC = lines_per_cta<T, LENF>();
     const int nb = (a.ncols + TC - 1) / TC;
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
-    const int epc = 16 / (int)sizeof(C);
-    const bool aligned = (a.ncols % TC == 0 || (a.ncols % TC) % epc == 0) && (a.ncols % epc == 0) &&
-                         ((a.in_rot_stride * (int64_t)sizeof(C)) % 16 == 0) &&
-                         ((a.in_outer_stride * (int64_t)sizeof(C)) % 16 == 0) &&
-                         ((reinterpret_cast<uintptr_t>(a.in) & 15) == 0) && a.len_in <= LENF;
-    const int ntwf = tw_count(LENF), ntwi = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
-    if (aligned) {
-        const size_t smem =
-            (size_t)(TC * line_pitch(LENF) + ((ntwf + ntwi + 1) & ~1) + 2 * (size_t)a.len_in * TC) * sizeof(C);
-        auto kern = k_cols_p<T, LENF, LENI, MODE>;
-        cudaError_t e = set_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        const int total = nb * a.nouter * batch;
-        kern<<<persistent_grid(kern, smem, total), 256, smem, st>>>(a, nb, total);
-        note_launch();
-        return cudaGetLastError();
-    }
     const size_t smem = (size_t)(TC * line_pitch(LENF) + tw_count(LENF) + tw_count(LENI)) * sizeof(C);
     auto kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
