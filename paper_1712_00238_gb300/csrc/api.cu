@@ -489,7 +489,6 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     sa.s_h = G.s_h;
     sa.out = b0;
     sa.out_rot_stride = 0;
-    sa.direct = ctx->opt_spread_direct;
     sa.n_full = G.n;
     CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
     if (ctx->opt_spread_direct || !bins_supported(ctx->p.w)) {
@@ -681,8 +680,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             sa.s_h = G.s_h;
             sa.out = b0;
             sa.out_rot_stride = e0;
-            sa.direct = ctx->opt_spread_direct;
-            sa.n_full = G.n;
+                    sa.n_full = G.n;
             {
                 PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
                 if (use_bins) CK(ctx, launch_spread_bins<T>(sa, bn, G.dim, b, s));

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
                 }
             }
         } else {
-#pragma unroll 1
+#pragma unroll
             for (int kz = 0; kz < W; ++kz) {
                 const int64_t zb = (int64_t)ix[2][kz] * n;
 #pragma unroll

@@ -54,7 +54,6 @@ struct SpreadArgs {
     int s, s_h;           // sub-box side and half-side
     cplx<T>* out;         // batch x s^d
     int64_t out_rot_stride;
-    int direct;           // 1: one global atomic per tap (no shared-memory tile)
     int n_full;           // oversampled grid length n (s == n means periodic wrap)
 };
 template <typename T> cudaError_t launch_spread(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);

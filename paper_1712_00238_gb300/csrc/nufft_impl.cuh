@@ -102,7 +102,7 @@ __device__ __forceinline__ void spread_direct(cplx<T>* out, int s, int s_h, cons
         for (int ky = 0; ky < W; ++ky)
             spread_row<T, W>(out + (int64_t)iy[ky] * s, s, ax0, wraps, cscale(c, wt[1][ky]), wt[0]);
     } else {
-#pragma unroll 1
+#pragma unroll
         for (int kz = 0; kz < W; ++kz) {
             const C cz = cscale(c, wt[2][kz]);
             C* plane = out + (int64_t)wrap_index(u0[2] + kz + s_h, s) * s * s;
@@ -113,133 +113,48 @@ __device__ __forceinline__ void spread_direct(cplx<T>* out, int s, int s_h, cons
     }
 }
 
-// One CTA spreads 256 consecutive samples.  Because the samples are stored in
-// Morton order, their taps after rotation usually fit a small box: the CTA
-// accumulates them there in shared memory (shared atomics) and then adds the
-// box's non-zero cells to the sub-box in global memory, one vector atomic per
-// cell instead of one per tap.  A box larger than `cap_cells` (or cap_cells = 0)
-// falls back to one global atomic per tap.
-template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a, int cap_cells) {
-    using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);  // cap_cells x (re, im)
-    __shared__ T Rm[9];
-    __shared__ int wlo[8][3], whi[8][3];
-    __shared__ int box_lo[3], box_ext[3];
-    const int b = blockIdx.y;
-    if (threadIdx.x == 0) {
-        if (a.quats) {
-            quat_to_matrix<T>(a.quats + 4 * (a.rot0 + b), Rm);
-        } else {
-            for (int i = 0; i < 9; ++i) Rm[i] = (i % 4 == 0) ? T(1) : T(0);
-        }
+template <typename T>
+__device__ __forceinline__ void load_rotation(const SpreadArgs<T>& a, int b, T* Rm) {
+    if (a.quats) {
+        quat_to_matrix<T>(a.quats + 4 * (a.rot0 + b), Rm);
+    } else {
+        for (int i = 0; i < 9; ++i) Rm[i] = (i % 4 == 0) ? T(1) : T(0);
     }
+}
+
+// One thread per sample: rotate, evaluate the kernel weights, add the taps to
+// the sub-box with global vector atomics (spread_direct).
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
+    using C = cplx<T>;
+    __shared__ T Rm[9];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) load_rotation(a, b, Rm);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = j < a.m;
+    if (j >= a.m) return;
+    const vec4<T> p = a.pos[j];
+    const C c = a.c[j];
+    T y[3];
+    y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
+    y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
+    y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
+    const T half = T(W) * T(0.5);
+    const T inv_half = T(2) / T(W);
     T wt[D][W];
     int u0[D];
-    C c = mk(T(0), T(0));
-    if (live) {
-        const vec4<T> p = a.pos[j];
-        c = a.c[j];
-        T y[3];
-        y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
-        y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
-        y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
-        const T half = T(W) * T(0.5);
-        const T inv_half = T(2) / T(W);
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const T g = y[d] * a.inv_h;
-            u0[d] = (int)ceil(g - half);
+    for (int d = 0; d < D; ++d) {
+        const T g = y[d] * a.inv_h;
+        u0[d] = (int)ceil(g - half);
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const T z = (T(u0[d] + k) - g) * inv_half;
-                const T z2 = z * z;
-                wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int d = 0; d < D; ++d) u0[d] = 0;
-    }
-    // bounding box of the taps of this CTA (unwrapped grid indices)
-    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    if (live)
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            lo[d] = u0[d];
-            hi[d] = u0[d] + W - 1;
-        }
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        for (int off = 16; off > 0; off >>= 1) {
-            lo[d] = min(lo[d], __shfl_down_sync(0xffffffffu, lo[d], off));
-            hi[d] = max(hi[d], __shfl_down_sync(0xffffffffu, hi[d], off));
-        }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int d = 0; d < 3; ++d) {
-            wlo[warp][d] = lo[d];
-            whi[warp][d] = hi[d];
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int d = 0; d < 3; ++d) {
-            int l = INT_MAX, h = INT_MIN;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                l = min(l, wlo[w][d]);
-                h = max(h, whi[w][d]);
-            }
-            box_lo[d] = l;
-            box_ext[d] = (d < D && h >= l) ? h - l + 1 : 1;
+        for (int k = 0; k < W; ++k) {
+            const T z = (T(u0[d] + k) - g) * inv_half;
+            const T z2 = z * z;
+            wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
         }
     }
-    __syncthreads();
-    const int ex = box_ext[0], ey = box_ext[1], ez = box_ext[2];
-    const int64_t cells = (int64_t)ex * ey * (D == 3 ? ez : 1);
-    C* out = a.out + (int64_t)b * a.out_rot_stride;
-    const int s = a.s;
-    if (cells <= cap_cells) {
-        for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) tile[i] = T(0);
-        __syncthreads();
-        if (live) {
-            const int lx = u0[0] - box_lo[0], ly = u0[1] - box_lo[1], lz = (D == 3) ? u0[2] - box_lo[2] : 0;
-#pragma unroll 1
-            for (int kz = 0; kz < (D == 3 ? W : 1); ++kz) {
-                const C cz = (D == 3) ? cscale(c, wt[D == 3 ? 2 : 0][kz]) : c;
-#pragma unroll
-                for (int ky = 0; ky < W; ++ky) {
-                    const C cy = cscale(cz, wt[1][ky]);
-                    T* row = tile + 2 * (((int64_t)(lz + kz) * ey + (ly + ky)) * ex + lx);
-#pragma unroll
-                    for (int kx = 0; kx < W; ++kx) {
-                        atomicAdd(row + 2 * kx, cy.x * wt[0][kx]);
-                        atomicAdd(row + 2 * kx + 1, cy.y * wt[0][kx]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int64_t li = threadIdx.x; li < cells; li += blockDim.x) {
-            const C v = mk(tile[2 * li], tile[2 * li + 1]);
-            if (v.x == T(0) && v.y == T(0)) continue;
-            const int64_t q = li / ex;
-            const int cx = (int)(li - q * ex);
-            const int cy = (int)(q % ey);
-            const int cz = (int)(q / ey);
-            const int ax = wrap_index(box_lo[0] + cx + a.s_h, s);
-            const int ay = wrap_index(box_lo[1] + cy + a.s_h, s);
-            int64_t off = (int64_t)ay * s + ax;
-            if (D == 3) off += (int64_t)wrap_index(box_lo[2] + cz + a.s_h, s) * s * s;
-            atomic_cadd(out + off, v);
-        }
-        return;
-    }
-    if (!live) return;
-    spread_direct<T, D, W>(a.out + (int64_t)b * a.out_rot_stride, s, a.s_h, u0, wt, c);
+    spread_direct<T, D, W>(a.out + (int64_t)b * a.out_rot_stride, a.s, a.s_h, u0, wt, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -279,15 +194,6 @@ __device__ __forceinline__ void sample_taps(const SpreadArgs<T>& a, const T* Rm,
             wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
         }
         org[d] = wrap_index(u0 + a.s_h, a.s);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_rotation(const SpreadArgs<T>& a, int b, T* Rm) {
-    if (a.quats) {
-        quat_to_matrix<T>(a.quats + 4 * (a.rot0 + b), Rm);
-    } else {
-        for (int i = 0; i < 9; ++i) Rm[i] = (i % 4 == 0) ? T(1) : T(0);
     }
 }
 
@@ -685,21 +591,14 @@ cudaError_t launch_cols_t(int mode, const ColArgs<T>& a, int batch, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
-// Shared-memory budget of one spreading CTA (64 KiB of complex cells).
-constexpr int kSpreadTileBytes = 64 * 1024;
-
 template <typename T>
 cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st) {
     if (a.m == 0 || batch == 0) return cudaSuccess;
     const dim3 grid((unsigned)((a.m + 255) / 256), batch);
-    const int cap = a.direct ? 0 : kSpreadTileBytes / (int)sizeof(cplx<T>);
-    const size_t smem = a.direct ? 0 : (size_t)kSpreadTileBytes;
 #define SD_SPREAD_CASE(WW)                                                                   \
     case WW: {                                                                               \
         auto kern = (dim == 2) ? k_spread<T, 2, WW> : k_spread<T, 3, WW>;                    \
-        cudaError_t e = set_smem(kern, smem);                                                \
-        if (e != cudaSuccess) return e;                                                      \
-        kern<<<grid, 256, smem, st>>>(a, cap);                                               \
+        kern<<<grid, 256, 0, st>>>(a);                                                       \
         note_launch();                                                                       \
         return cudaGetLastError();                                                           \
     }
