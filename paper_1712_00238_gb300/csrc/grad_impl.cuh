@@ -53,11 +53,14 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         rp[0] = Rm[0] * p.x + Rm[1] * p.y + Rm[2] * pz;
         rp[1] = Rm[3] * p.x + Rm[4] * p.y + Rm[5] * pz;
         rp[2] = (D == 3) ? Rm[6] * p.x + Rm[7] * p.y + Rm[8] * pz : T(0);
-        T wt[D][W];
-        int ix[D][W];
+        // x and y weights and indices in registers (their loops are unrolled); the
+        // z loop stays rolled and evaluates its weight per iteration, so no array
+        // is indexed at run time
+        T wt[2][W];
+        int ix[2][W];
         const T half = T(W) * T(0.5), inv_half = T(2) / T(W);
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
+        for (int d = 0; d < 2; ++d) {
             const T g = (rp[d] + tv[d]) * a.inv_h;
             const int u0 = (int)ceil(g - half);
 #pragma unroll
@@ -84,13 +87,18 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
                 }
             }
         } else {
-#pragma unroll
+            const T gzc = (rp[2] + tv[2]) * a.inv_h;
+            const int uz0 = (int)ceil(gzc - half);
+#pragma unroll 1
             for (int kz = 0; kz < W; ++kz) {
-                const int64_t zb = (int64_t)ix[2][kz] * n;
+                const T zz = (T(uz0 + kz) - gzc) * inv_half;
+                const T z2 = zz * zz;
+                const T wz = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+                const int64_t zb = (int64_t)wrap_n(uz0 + kz, n) * n;
 #pragma unroll
                 for (int ky = 0; ky < W; ++ky) {
                     const int64_t rb = (zb + ix[1][ky]) * n;
-                    const T wzy = wt[2][kz] * wt[1][ky];
+                    const T wzy = wz * wt[1][ky];
 #pragma unroll
                     for (int kx = 0; kx < W; ++kx) {
                         const T wgt = wzy * wt[0][kx];

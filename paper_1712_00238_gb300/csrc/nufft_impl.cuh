@@ -87,9 +87,11 @@ __device__ __forceinline__ void spread_row(cplx<T>* row, int s, int ax0, bool wr
     }
 }
 
+// Taps of one sample: x/y weights in registers (unrolled loops), the z loop
+// rolled with its weight evaluated per iteration (no run-time-indexed arrays).
 template <typename T, int D, int W>
 __device__ __forceinline__ void spread_direct(cplx<T>* out, int s, int s_h, const int* u0, const T (*wt)[W],
-                                              cplx<T> c) {
+                                              cplx<T> c, T gz, T beta) {
     using C = cplx<T>;
     int ax0 = u0[0] + s_h;
     const bool wraps = (ax0 < 0) || (ax0 + W > s);
@@ -102,10 +104,15 @@ __device__ __forceinline__ void spread_direct(cplx<T>* out, int s, int s_h, cons
         for (int ky = 0; ky < W; ++ky)
             spread_row<T, W>(out + (int64_t)iy[ky] * s, s, ax0, wraps, cscale(c, wt[1][ky]), wt[0]);
     } else {
-#pragma unroll
+        const T inv_half = T(2) / T(W);
+        const int uz0 = u0[2];
+#pragma unroll 1
         for (int kz = 0; kz < W; ++kz) {
-            const C cz = cscale(c, wt[2][kz]);
-            C* plane = out + (int64_t)wrap_index(u0[2] + kz + s_h, s) * s * s;
+            const T zz = (T(uz0 + kz) - gz) * inv_half;
+            const T z2 = zz * zz;
+            const T wz = (z2 <= T(1)) ? exp(beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+            const C cz = cscale(c, wz);
+            C* plane = out + (int64_t)wrap_index(uz0 + kz + s_h, s) * s * s;
 #pragma unroll
             for (int ky = 0; ky < W; ++ky)
                 spread_row<T, W>(plane + (int64_t)iy[ky] * s, s, ax0, wraps, cscale(cz, wt[1][ky]), wt[0]);
@@ -141,10 +148,10 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
     const T half = T(W) * T(0.5);
     const T inv_half = T(2) / T(W);
-    T wt[D][W];
-    int u0[D];
+    T wt[2][W];
+    int u0[3] = {0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
+    for (int d = 0; d < 2; ++d) {
         const T g = y[d] * a.inv_h;
         u0[d] = (int)ceil(g - half);
 #pragma unroll
@@ -154,7 +161,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
             wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
         }
     }
-    spread_direct<T, D, W>(a.out + (int64_t)b * a.out_rot_stride, a.s, a.s_h, u0, wt, c);
+    const T gz = y[2] * a.inv_h;
+    if (D == 3) u0[2] = (int)ceil(gz - half);
+    spread_direct<T, D, W>(a.out + (int64_t)b * a.out_rot_stride, a.s, a.s_h, u0, wt, c, gz, a.beta);
 }
 
 // ---------------------------------------------------------------------------
