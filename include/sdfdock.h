@@ -113,7 +113,9 @@ const char* sd_last_error(const sd_ctx* ctx);
  * graph), "timing" (1: CUDA-event timing of every pass, see sd_pass_times),
  * "spread_direct" (1, the default: spread with global vector atomics per kernel
  * row; 0: sort the samples into 8^d-cell bins and accumulate each bin's taps in
- * shared memory first). */
+ * shared memory first), "sdf_cull" (1, the default: the SDF sums skip boundary
+ * tiles that lie beyond the truncation radius of every query of a block; 0: sum
+ * over every tile; results are the same). */
 int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
 
 /* ---- shapes: the sampled SDF (Section 4, Eq. 10A-17t) ------------------- */
@@ -129,16 +131,17 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
  *   out   receives a new shape holding p_i and c_i = rho(p_i) v_i
  *   rho_out  device, m x 2 real, or NULL: receives rho(p_i)
  * rho follows Eq. 13 with Eq. 15/16c and the truncation of Eq. 17t, xi from
- * Eq. 10A (nearest sample, ties to the lowest index), zeta = xi + i eta (Eq. 11),
+ * Eq. 10A (nearest sample), zeta = xi + i eta (Eq. 11),
  * cos(theta) from Eq. 12a; in 2D each element is weighted by its planar angle
- * over 2 pi.  Synchronises `stream` before returning (the shape's bounding
- * radius is read back). */
+ * over 2 pi.  The shape stores its samples in Morton (Z-curve) order of
+ * position; rho_out is in the caller's order.  Synchronises `stream`. */
 int sd_sdf_build(sd_ctx* ctx, const void* bnd, const void* nrm, const void* area, int64_t n_b,
                  const void* qry, const void* vol, int64_t m, const int8_t* pmc_override,
                  sd_shape** out, void* rho_out, void* stream);
 
 /* Make a shape directly from weighted samples (p_i device m x 4 real,
- * c_i device m x 2 real).  Copies them.  Synchronises `stream`. */
+ * c_i device m x 2 real).  Copies them, stored in Morton order of position.
+ * Synchronises `stream`. */
 int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m,
                           sd_shape** out, void* stream);
 

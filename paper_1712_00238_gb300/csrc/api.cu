@@ -58,6 +58,7 @@ struct sd_ctx {
     int opt_graph = 0;
     int opt_plain = 0;
     int opt_spread_direct = 1;  // 0: spread by bins
+    int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
     DevBuf ws[8];
     std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
     std::map<std::tuple<int, int, int, double>, double*> deconv;
@@ -844,6 +845,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "plain")) ctx->opt_plain = (int)value;
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
+    else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
     return SD_OK;
 }
@@ -856,30 +858,63 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     s->ctx = ctx;
     s->m = m;
     std::unique_ptr<sd_shape> guard(s);
+    // temporaries: nearest distances, memberships, radii, Morton orders, the
+    // sorted boundary and its tile boxes
     T* xi = nullptr;
     int8_t* pm = nullptr;
     double* rad = nullptr;
+    int32_t *perm_q = nullptr, *perm_b = nullptr;
+    vec4<T>*bnd_s = nullptr, *nrm_s = nullptr;
+    float* tbox = nullptr;
+    const int64_t n_tiles = (n_b + SDF_TILE - 1) / SDF_TILE;
     auto cleanup = [&]() {
-        if (xi) cudaFree(xi);
-        if (pm) cudaFree(pm);
-        if (rad) cudaFree(rad);
+        cudaFree(xi); cudaFree(pm); cudaFree(rad); cudaFree(perm_q); cudaFree(perm_b);
+        cudaFree(bnd_s); cudaFree(nrm_s); cudaFree(tbox);
     };
-    cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&s->pos, (size_t)std::max<int64_t>(m, 1) * sizeof(vec4<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&s->c, (size_t)std::max<int64_t>(m, 1) * sizeof(cplx<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&xi, (size_t)std::max<int64_t>(m, 1) * sizeof(T))) != cudaSuccess ||
-        (e = cudaMalloc(&pm, (size_t)std::max<int64_t>(m, 1))) != cudaSuccess ||
-        (e = cudaMalloc(&rad, sizeof(double))) != cudaSuccess) {
+    auto fail_free = [&](int code, const char* what, cudaError_t e) {
         cleanup();
         if (s->pos) cudaFree(s->pos);
         if (s->c) cudaFree(s->c);
         s->pos = s->c = nullptr;
-        return fail(ctx, SD_ERR_OOM, "sdf_build allocation failed: %s", cudaGetErrorString(e));
+        return fail(ctx, code, "sdf_build: %s: %s", what, cudaGetErrorString(e));
+    };
+    const size_t mm = (size_t)std::max<int64_t>(m, 1);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&s->pos, mm * sizeof(vec4<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&s->c, mm * sizeof(cplx<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&xi, mm * sizeof(T))) != cudaSuccess || (e = cudaMalloc(&pm, mm)) != cudaSuccess ||
+        (e = cudaMalloc(&rad, 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&perm_q, mm * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&perm_b, (size_t)n_b * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&bnd_s, (size_t)n_b * sizeof(vec4<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&nrm_s, (size_t)n_b * sizeof(vec4<T>))) != cudaSuccess ||
+        (e = cudaMalloc(&tbox, (size_t)n_tiles * 6 * sizeof(float))) != cudaSuccess)
+        return fail_free(SD_ERR_OOM, "allocation failed", e);
+    // bounding radii of the queries and of the boundary samples
+    double r2[2] = {0.0, 0.0};
+    e = launch_radius<T>((const vec4<T>*)qry, m, ctx->p.dim, rad, st);
+    if (e == cudaSuccess) e = launch_radius<T>((const vec4<T>*)bnd, n_b, ctx->p.dim, rad + 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r2, rad, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_free(SD_ERR_CUDA, "radius", e);
+    if (!isfinite(r2[0]) || !isfinite(r2[1])) {
+        cleanup();
+        cudaFree(s->pos);
+        cudaFree(s->c);
+        s->pos = s->c = nullptr;
+        return fail(ctx, SD_ERR_NONFINITE, "sdf_build: non-finite query or boundary point");
     }
+    // Morton orders: queries are processed (and the shape stored) in that order
+    e = morton_order<T>((const vec4<T>*)qry, m, sqrt(r2[0]), ctx->p.dim, perm_q, st);
+    if (e == cudaSuccess) e = morton_order<T>((const vec4<T>*)bnd, n_b, sqrt(r2[1]), ctx->p.dim, perm_b, st);
+    if (e == cudaSuccess)
+        e = launch_boundary_order<T>((const vec4<T>*)bnd, (const vec4<T>*)nrm, (const T*)area, perm_b, n_b,
+                                     ctx->p.dim, bnd_s, nrm_s, tbox, st);
+    if (e != cudaSuccess) return fail_free(SD_ERR_CUDA, "ordering", e);
     SdfArgs<T> a{};
-    a.bnd = (const vec4<T>*)bnd;
-    a.nrm = (const vec4<T>*)nrm;
-    a.area = (const T*)area;
+    a.bnd = bnd_s;
+    a.nrm = nrm_s;
+    a.area = nullptr;
     a.n_b = n_b;
     a.qry = (const vec4<T>*)qry;
     a.vol = (const T*)vol;
@@ -894,21 +929,14 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     a.c_out = (cplx<T>*)s->c;
     a.rho_out = (cplx<T>*)rho_out;
     a.pos_out = (vec4<T>*)s->pos;
+    a.perm_q = perm_q;
+    a.tile_box = ctx->opt_sdf_cull ? tbox : nullptr;
+    a.n_tiles = n_tiles;
     e = launch_sdf<T>(a, ctx->p.dim, st);
-    if (e == cudaSuccess) e = launch_radius<T>((const vec4<T>*)s->pos, m, ctx->p.dim, rad, st);
-    double r2 = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&r2, rad, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_free(SD_ERR_CUDA, "kernels", e);
     cleanup();
-    if (e != cudaSuccess) {
-        cudaFree(s->pos);
-        cudaFree(s->c);
-        s->pos = s->c = nullptr;
-        return fail(ctx, SD_ERR_CUDA, "sdf_build: %s", cudaGetErrorString(e));
-    }
-    if (!isfinite(r2)) return fail(ctx, SD_ERR_NONFINITE, "sdf_build: non-finite query point");
-    s->radius = sqrt(r2);
-    CK(ctx, sort_by_morton<T>((vec4<T>*)s->pos, (cplx<T>*)s->c, m, s->radius, ctx->p.dim, st));
+    s->radius = sqrt(r2[0]);
     *out = guard.release();
     return SD_OK;
 }

@@ -30,9 +30,19 @@ struct SdfArgs {
     T* xi_abs;            // m: nearest distance
     int8_t* pmc;          // m: +1 / -1
     cplx<T>* c_out;       // m: rho * vol
-    cplx<T>* rho_out;     // m or null
-    vec4<T>* pos_out;     // m: copy of the query points for the shape
+    cplx<T>* rho_out;     // m or null (caller order)
+    vec4<T>* pos_out;     // m: copy of the query points for the shape (processing order)
+    const int32_t* perm_q;  // processing order of the queries (caller index), or null
+    const float* tile_box;  // boundary tile boxes (n_tiles x 6: lo, hi), or null
+    int64_t n_tiles;        // boundary tiles of SDF_TILE samples
 };
+// Boundary samples gathered into Morton order: positions, normals with the
+// area in .w, and the bounding box of every tile of SDF_TILE samples.
+template <typename T>
+cudaError_t launch_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T* area, const int32_t* perm,
+                                  int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box,
+                                  cudaStream_t st);
+constexpr int SDF_TILE = 256;
 template <typename T> cudaError_t launch_sdf(const SdfArgs<T>& a, int dim, cudaStream_t st);
 
 // max |p| over m points (result in *out, device double)
@@ -153,6 +163,10 @@ struct RescoreArgs {
 };
 template <typename T> cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st);
 int rescore_tiles(int64_t m2);
+
+// Morton order (permutation) of points inside the cube [-radius, radius]^d.
+template <typename T>
+cudaError_t morton_order(const vec4<T>* pos, int64_t m, double radius, int dim, int32_t* perm, cudaStream_t st);
 
 // Reorder a shape's samples by the Morton code of their position (in place).
 template <typename T>

@@ -60,44 +60,60 @@ __global__ void k_permute(const int32_t* perm, const vec4<T>* pin, const cplx<T>
     cout[i] = cin[j];
 }
 
-// Reorders pos and c in place (through temporaries) by the Morton code of pos.
+// perm[i] = index of the sample with the i-th smallest Morton code of pos
+// inside the cube [-radius, radius]^d (a stable order).
 template <typename T>
-cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, int dim, cudaStream_t st) {
-    if (m < 2) return cudaSuccess;
+cudaError_t morton_order(const vec4<T>* pos, int64_t m, double radius, int dim, int32_t* perm, cudaStream_t st) {
+    if (m < 1) return cudaSuccess;
     const double R = radius > 0 ? radius * (1.0 + 1e-6) : 1.0;
     const double scale = ((dim == 3) ? 1024.0 : 65536.0) / (2.0 * R);
     uint32_t *k0 = nullptr, *k1 = nullptr;
-    int32_t *v0 = nullptr, *v1 = nullptr;
-    vec4<T>* pt = nullptr;
-    cplx<T>* ct = nullptr;
+    int32_t* v0 = nullptr;
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
     cudaError_t e = cudaSuccess;
     auto done = [&](cudaError_t r) {
-        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(pt); cudaFree(ct); cudaFree(tmp);
+        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(tmp);
         return r;
     };
     if ((e = cudaMalloc(&k0, m * sizeof(uint32_t))) != cudaSuccess) return done(e);
     if ((e = cudaMalloc(&k1, m * sizeof(uint32_t))) != cudaSuccess) return done(e);
     if ((e = cudaMalloc(&v0, m * sizeof(int32_t))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&v1, m * sizeof(int32_t))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&pt, m * sizeof(vec4<T>))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&ct, m * sizeof(cplx<T>))) != cudaSuccess) return done(e);
     const unsigned nb = (unsigned)((m + 255) / 256);
     k_morton_keys<T><<<nb, 256, 0, st>>>(pos, m, -R, scale, dim, k0, v0);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
     const int bits = (dim == 3) ? 30 : 32;
-    e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k0, k1, v0, v1, (int)m, 0, bits, st);
+    e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k0, k1, v0, perm, (int)m, 0, bits, st);
     if (e != cudaSuccess) return done(e);
     if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) return done(e);
-    e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, v0, v1, (int)m, 0, bits, st);
+    e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, v0, perm, (int)m, 0, bits, st);
     if (e != cudaSuccess) return done(e);
+    e = cudaStreamSynchronize(st);
+    return done(e);
+}
+
+// Reorders pos and c in place (through temporaries) by the Morton code of pos.
+template <typename T>
+cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, int dim, cudaStream_t st) {
+    if (m < 2) return cudaSuccess;
+    int32_t* perm = nullptr;
+    vec4<T>* pt = nullptr;
+    cplx<T>* ct = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto done = [&](cudaError_t r) {
+        cudaFree(perm); cudaFree(pt); cudaFree(ct);
+        return r;
+    };
+    if ((e = cudaMalloc(&perm, m * sizeof(int32_t))) != cudaSuccess) return done(e);
+    if ((e = cudaMalloc(&pt, m * sizeof(vec4<T>))) != cudaSuccess) return done(e);
+    if ((e = cudaMalloc(&ct, m * sizeof(cplx<T>))) != cudaSuccess) return done(e);
+    if ((e = morton_order<T>(pos, m, radius, dim, perm, st)) != cudaSuccess) return done(e);
     if ((e = cudaMemcpyAsync(pt, pos, m * sizeof(vec4<T>), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return done(e);
     if ((e = cudaMemcpyAsync(ct, c, m * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return done(e);
-    k_permute<T><<<nb, 256, 0, st>>>(v1, pt, ct, pos, c, m);
+    k_permute<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(perm, pt, ct, pos, c, m);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
     e = cudaStreamSynchronize(st);
@@ -106,5 +122,7 @@ cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, i
 
 template cudaError_t sort_by_morton<float>(vec4<float>*, cplx<float>*, int64_t, double, int, cudaStream_t);
 template cudaError_t sort_by_morton<double>(vec4<double>*, cplx<double>*, int64_t, double, int, cudaStream_t);
+template cudaError_t morton_order<float>(const vec4<float>*, int64_t, double, int, int32_t*, cudaStream_t);
+template cudaError_t morton_order<double>(const vec4<double>*, int64_t, double, int, int32_t*, cudaStream_t);
 
 }  // namespace sd

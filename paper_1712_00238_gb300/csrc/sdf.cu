@@ -12,13 +12,24 @@
 // eta/|xi| - 1 <= eps (Eq. 17t).  In 2D every element is weighted by its planar
 // angle over 2 pi, i.e. the 3D summand times 2 eta.
 // Both passes stage boundary tiles in shared memory; one query point per thread.
+#include <float.h>
 #include <math.h>
 
 #include "kernels.cuh"
 
 namespace sd {
 
-constexpr int SDF_TILE = 256;
+// Queries are processed in Morton order (perm_q) and the boundary samples are
+// pre-sorted the same way, so a CTA's 256 queries and a tile's 256 samples are
+// each spatially compact.  Pass 2 skips every tile whose bounding box lies
+// farther than (1 + eps) max|xi| from the CTA's box: all its pairs would fail
+// the truncation test of Eq. 17t anyway (the restriction to eps-approximate
+// nearest neighbours of Section 4), so the sum is unchanged.
+
+template <typename T>
+__device__ __forceinline__ T recip(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 
 template <typename T, int D>
 __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
@@ -26,8 +37,9 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
     __shared__ vec4<T> sn[SDF_TILE];  // normal with the area in .w
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.m;
+    const int64_t src = live ? (a.perm_q ? (int64_t)a.perm_q[i] : i) : 0;
     vec4<T> p;
-    if (live) p = a.qry[i];
+    if (live) p = a.qry[src];
     else { p.x = p.y = p.z = p.w = T(0); }
     T dmin = INFINITY;
     T wind = T(0);
@@ -35,9 +47,7 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
         const int64_t j = t0 + threadIdx.x;
         if (j < a.n_b) {
             sq[threadIdx.x] = a.bnd[j];
-            vec4<T> nn = a.nrm[j];
-            nn.w = a.area[j];
-            sn[threadIdx.x] = nn;
+            sn[threadIdx.x] = a.nrm[j];
         }
         __syncthreads();
         const int cnt = (int)min((int64_t)SDF_TILE, a.n_b - t0);
@@ -48,16 +58,20 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
             const T d2 = dx * dx + dy * dy + dz * dz;
             dmin = d2 < dmin ? d2 : dmin;
             const T dot = dx * nn.x + dy * nn.y + dz * nn.z;
-            if (D == 3) wind += nn.w * dot / (d2 * sqrt(d2));
-            else wind += nn.w * dot / d2;
+            if (D == 3) {
+                const T r = rsqrt(d2);
+                wind += nn.w * dot * r * r * r;
+            } else {
+                wind += nn.w * dot * recip(d2);
+            }
         }
         __syncthreads();
     }
     if (!live) return;
     const T S = (D == 3) ? T(4.0 * M_PI) : T(2.0 * M_PI);
     a.xi_abs[i] = sqrt(dmin);
-    int8_t m = (wind / S > T(0.5)) ? int8_t(-1) : int8_t(1);
-    if (a.pmc_override) m = a.pmc_override[i] < 0 ? int8_t(-1) : int8_t(1);
+    int8_t m = (wind > T(0.5) * S) ? int8_t(-1) : int8_t(1);
+    if (a.pmc_override) m = a.pmc_override[src] < 0 ? int8_t(-1) : int8_t(1);
     a.pmc[i] = m;
 }
 
@@ -74,30 +88,65 @@ template <typename T, int D>
 __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
     __shared__ vec4<T> sq[SDF_TILE];
     __shared__ vec4<T> sn[SDF_TILE];
+    __shared__ float wred[SDF_TILE / 32][7];
+    __shared__ float box[7];  // lo[3], hi[3], reach
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.m;
+    const int64_t src = live ? (a.perm_q ? (int64_t)a.perm_q[i] : i) : 0;
     vec4<T> p;
     T xabs = T(1), xi = T(1);
     if (live) {
-        p = a.qry[i];
+        p = a.qry[src];
         xabs = a.xi_abs[i];
         xi = a.pmc[i] < 0 ? -xabs : xabs;
     } else {
         p.x = p.y = p.z = p.w = T(0);
     }
+    // CTA box and cutoff radius (1 + eps) max|xi| for the tile test
+    const bool cull = a.tile_box != nullptr && a.eps >= T(0);
+    if (cull) {
+        float v[7] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f};
+        if (live) {
+            v[0] = v[3] = (float)p.x;
+            v[1] = v[4] = (float)p.y;
+            v[2] = v[5] = (D == 3) ? (float)p.z : 0.f;
+            v[6] = (float)xabs;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            for (int d = 0; d < 3; ++d) v[d] = fminf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
+            for (int d = 3; d < 7; ++d) v[d] = fmaxf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
+        }
+        if ((threadIdx.x & 31) == 0)
+            for (int d = 0; d < 7; ++d) wred[threadIdx.x >> 5][d] = v[d];
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            float r = wred[0][threadIdx.x];
+            for (int w = 1; w < SDF_TILE / 32; ++w)
+                r = threadIdx.x < 3 ? fminf(r, wred[w][threadIdx.x]) : fmaxf(r, wred[w][threadIdx.x]);
+            if (threadIdx.x == 6) r = r * (1.f + (float)a.eps) * (1.f + 1e-4f) + 1e-6f;
+            box[threadIdx.x] = r;
+        }
+        __syncthreads();
+    }
     const T lam = xi > T(0) ? a.lam1 : -a.lam2;
     const T pref = lam / (T(2.0 * M_PI) * a.sigma);  // lambda/sqrt(2 pi) * 1/(sqrt(2 pi) sigma)
-    const T inv_xabs = T(1) / xabs;
-    const T inv_2s2 = T(1) / (T(2) * a.sigma * a.sigma);
+    const T inv_xabs = recip(xabs);
+    const T inv_2s2 = recip(T(2) * a.sigma * a.sigma);
     const T xi2 = xi * xi;
     T sr = 0, cr = 0, si = 0, ci = 0;
-    for (int64_t t0 = 0; t0 < a.n_b; t0 += SDF_TILE) {
+    for (int64_t t0 = 0, tile = 0; t0 < a.n_b; t0 += SDF_TILE, ++tile) {
+        if (cull) {
+            const float* tb = a.tile_box + tile * 6;
+            const float g0 = fmaxf(0.f, fmaxf(tb[0] - box[3], box[0] - tb[3]));
+            const float g1 = fmaxf(0.f, fmaxf(tb[1] - box[4], box[1] - tb[4]));
+            const float g2 = (D == 3) ? fmaxf(0.f, fmaxf(tb[2] - box[5], box[2] - tb[5])) : 0.f;
+            if (g0 * g0 + g1 * g1 + g2 * g2 > box[6] * box[6]) continue;  // same in every thread
+        }
         const int64_t j = t0 + threadIdx.x;
+        __syncthreads();
         if (j < a.n_b) {
             sq[threadIdx.x] = a.bnd[j];
-            vec4<T> nn = a.nrm[j];
-            nn.w = a.area[j];
-            sn[threadIdx.x] = nn;
+            sn[threadIdx.x] = a.nrm[j];
         }
         __syncthreads();
         const int cnt = (int)min((int64_t)SDF_TILE, a.n_b - t0);
@@ -110,10 +159,10 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
             if (a.eps >= T(0) && rm1 > a.eps) continue;
             const vec4<T> nn = sn[k];
             const T E = exp(-rm1 * rm1 * inv_2s2);
-            const T cos_t = (dx * nn.x + dy * nn.y + dz * nn.z) / eta;
+            const T cos_t = (dx * nn.x + dy * nn.y + dz * nn.z) * recip(eta);
             // zeta^-2 = (xi - i eta)^2 / (xi^2 + eta^2)^2
             const T den = xi2 + d2;
-            const T inv_den2 = T(1) / (den * den);
+            const T inv_den2 = recip(den * den);
             const T zr = (xi2 - d2) * inv_den2;
             const T zi = T(-2) * xi * eta * inv_den2;
             T f = pref * E * cos_t * nn.w;
@@ -121,15 +170,59 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
             kahan_add(sr, cr, f * zr);
             kahan_add(si, ci, f * zi);
         }
-        __syncthreads();
     }
     if (!live) return;
-    const T v = a.vol[i];
+    const T v = a.vol[src];
     a.c_out[i] = mk(sr * v, si * v);
-    if (a.rho_out) a.rho_out[i] = mk(sr, si);
+    if (a.rho_out) a.rho_out[src] = mk(sr, si);
     vec4<T> po = p;
     po.w = T(0);
     a.pos_out[i] = po;
+}
+
+template <typename T>
+__global__ void k_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T* area, const int32_t* perm,
+                                 int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box) {
+    __shared__ float wred[SDF_TILE / 32][6];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (i < n_b) {
+        const int32_t j = perm[i];
+        const vec4<T> q = bnd[j];
+        vec4<T> nn = nrm[j];
+        nn.w = area[j];
+        bnd_s[i] = q;
+        nrm_s[i] = nn;
+        v[0] = v[3] = (float)q.x;
+        v[1] = v[4] = (float)q.y;
+        v[2] = v[5] = (dim == 3) ? (float)q.z : 0.f;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int d = 0; d < 3; ++d) v[d] = fminf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
+        for (int d = 3; d < 6; ++d) v[d] = fmaxf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int d = 0; d < 6; ++d) wred[threadIdx.x >> 5][d] = v[d];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float r = wred[0][threadIdx.x];
+        for (int w = 1; w < SDF_TILE / 32; ++w)
+            r = threadIdx.x < 3 ? fminf(r, wred[w][threadIdx.x]) : fmaxf(r, wred[w][threadIdx.x]);
+        // widen by a float ulp-scale margin so the tile test stays conservative
+        const float m = 1e-6f * (fabsf(r) + 1.f);
+        tile_box[blockIdx.x * 6 + threadIdx.x] = threadIdx.x < 3 ? r - m : r + m;
+    }
+}
+
+template <typename T>
+cudaError_t launch_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T* area, const int32_t* perm,
+                                  int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box,
+                                  cudaStream_t st) {
+    if (n_b == 0) return cudaSuccess;
+    k_boundary_order<T><<<(unsigned)((n_b + SDF_TILE - 1) / SDF_TILE), SDF_TILE, 0, st>>>(bnd, nrm, area, perm, n_b,
+                                                                                        dim, bnd_s, nrm_s, tile_box);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -177,5 +270,10 @@ template cudaError_t launch_sdf<float>(const SdfArgs<float>&, int, cudaStream_t)
 template cudaError_t launch_sdf<double>(const SdfArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_radius<float>(const vec4<float>*, int64_t, int, double*, cudaStream_t);
 template cudaError_t launch_radius<double>(const vec4<double>*, int64_t, int, double*, cudaStream_t);
+template cudaError_t launch_boundary_order<float>(const vec4<float>*, const vec4<float>*, const float*, const int32_t*,
+                                                  int64_t, int, vec4<float>*, vec4<float>*, float*, cudaStream_t);
+template cudaError_t launch_boundary_order<double>(const vec4<double>*, const vec4<double>*, const double*,
+                                                   const int32_t*, int64_t, int, vec4<double>*, vec4<double>*, float*,
+                                                   cudaStream_t);
 
 }  // namespace sd

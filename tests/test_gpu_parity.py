@@ -23,6 +23,7 @@ from synth import configs, rotations
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-4, "f64": 2e-5}
+LAM_DEFAULT = (1.0, 3.0, 0.5, 1.5)  # lambda1, lambda2, sigma_t, eps (Section 6)
 
 
 def make_ctx(w, precision=None, **kw):
@@ -351,4 +352,50 @@ def test_argument_errors_are_reported():
     cand = ctx.score_rotations(fx, mv, q, grid_of(w))
     assert torch.isfinite(sd.decode_cands(cand)[0]).all()
     other.close()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# docking-shaped inputs: grids with radix-3 line lengths (96 -> 192, 192 -> 384)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,L,n1,n2", [(96, 77.4, 3000, 1200), (192, 153.6, 1500, 600)])
+def test_maps_docking_grids(N, L, n1, n2):
+    # a small sphere-union pair (200 and 60 spheres); seeded subsets of its SDF
+    # sample positions carry seeded synthetic weights
+    fx_in, mv_in = configs.docking_pair(200, 60, 5)
+    rng = np.random.default_rng(N)
+    p1 = fx_in.query.pos[np.sort(rng.choice(fx_in.query.m, n1, replace=False))]
+    p2 = mv_in.query.pos[np.sort(rng.choice(mv_in.query.m, n2, replace=False))]
+    c1 = synthetic_weights(n1, 3)
+    c2 = synthetic_weights(n2, 4)
+    sg = 0.6
+    ctx = sd.Context(3, "f32", 0, sigma_g=sg)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    quats = rotations.super_fibonacci(40)[[3, 17]]
+    q = quats_dev(quats)
+    g = sd.Grid(N, L)
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, quats, N, L, sg)
+    cand = sd.decode_cands(ctx.score_rotations(fx, mv, q, g))
+    for r in range(len(quats)):
+        assert rel_err(maps[r], ref[r]) < 1e-4
+        if top1_margin_ok(ref[r].real):
+            assert cand[2][r].item() == int(np.argmax(ref[r].real))
+    ctx.close()
+
+
+def test_sdf_docking_pair_sampled_points():
+    fx_in, mv_in = configs.docking_pair(200, 60, 5)
+    ctx = sd.Context(3, "f32", 0, sigma_g=0.6)
+    rng = np.random.default_rng(1)
+    for s in (fx_in, mv_in):
+        _, rho = gpu_shape(ctx, s, return_rho=True)
+        got = rho.cpu().numpy()
+        sel = rng.choice(s.query.m, 300, replace=False)
+        b = s.boundary
+        ref = osdf.sdf_rho(s.query.pos[sel], b.pos, b.normal, b.area, LAM_DEFAULT[0], LAM_DEFAULT[1],
+                           LAM_DEFAULT[2], LAM_DEFAULT[3])
+        assert rel_err(got[sel, 0] + 1j * got[sel, 1], ref) < 1e-4
     ctx.close()
