@@ -367,9 +367,14 @@ def run_ours(args):
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# search passes from one ncu capture of this workload, keyed by (pass, sub-box
-# side, N); absent entries report null.
-TRAFFIC_PER_LAUNCH: dict = {}
+# search passes from one ncu capture of a 34-rotation launch of this workload
+# (the bench's own launches also hold 34 rotations), keyed by (pass, sub-box side,
+# N); absent entries report null.
+TRAFFIC_PER_LAUNCH: dict = {
+    ("fused", 108, 128): 553426688 + 531017984,
+    ("fwd_y", 108, 128): 406161920 + 432556032,
+    ("inv_y", 108, 128): 570464768 + 510324480,
+}
 
 
 # ---------------------------------------------------------------------------
