@@ -173,6 +173,18 @@ struct DeviceGuard {
 
 static size_t real_size(const sd_ctx* ctx) { return ctx->p.precision == SD_F64 ? 8 : 4; }
 
+// Per-call and per-shape buffers come from the device's stream-ordered memory
+// pool (its release threshold is raised when a context is created), so repeated
+// shape builds and table preparations reuse memory instead of paying for
+// cudaMalloc/cudaFree and their device synchronisation.
+cudaError_t sd::pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    return cudaMallocAsync(p, bytes ? bytes : 1, st);
+}
+void sd::pool_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
 // Captured graphs hold raw workspace and table pointers: drop them before any
 // of those buffers is freed.
 static void drop_graphs(sd_ctx* ctx) {
@@ -471,11 +483,11 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     const int64_t sz1 = (G.dim == 2) ? (int64_t)G.s * G.N : (int64_t)G.s * G.s * G.N;
     const int64_t sz2 = (G.dim == 2) ? 0 : (int64_t)G.s * G.N * G.N;
     C *b0 = nullptr, *b1 = nullptr, *b2 = nullptr, *B1 = nullptr, *W = nullptr;
-    CK(ctx, cudaMalloc(&b0, sz0 * sizeof(C)));
-    CK(ctx, cudaMalloc(&b1, sz1 * sizeof(C)));
-    if (sz2) CK(ctx, cudaMalloc(&b2, sz2 * sizeof(C)));
-    CK(ctx, cudaMalloc(&B1, Nd * sizeof(C)));
-    CK(ctx, cudaMalloc(&W, Nd * sizeof(C)));
+    CK(ctx, pool_alloc((void**)&b0, sz0 * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&b1, sz1 * sizeof(C), st));
+    if (sz2) CK(ctx, pool_alloc((void**)&b2, sz2 * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&B1, Nd * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&W, Nd * sizeof(C), st));
     SpreadArgs<T> sa{};
     sa.pos = (const vec4<T>*)fx->pos;
     sa.c = (const C*)fx->c;
@@ -507,10 +519,10 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
         CK(ctx, pass_last<T>(COL_FWD, G, tw, b1, 0, B1, 0, nullptr, 1, st));
     }
     CK(ctx, launch_wtable<T>(B1, D, G.N, G.dim, G.L, ctx->p.sigma_g, 1, -1, W, st));
+    pool_free(b0, st);
+    pool_free(b1, st);
+    pool_free(b2, st);
     CK(ctx, cudaStreamSynchronize(st));
-    cudaFree(b0);
-    cudaFree(b1);
-    if (b2) cudaFree(b2);
     Prep p;
     p.N = g->N;
     p.L = g->L;
@@ -543,11 +555,11 @@ static int prep_fields(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, 
     const int64_t sx = (G.dim == 2) ? (int64_t)N * n : (int64_t)N * N * n;
     const int64_t sy = (G.dim == 2) ? 0 : (int64_t)N * n * n;
     C *F = nullptr, *X = nullptr, *Y = nullptr, *Z = nullptr, *Gf = nullptr;
-    CK(ctx, cudaMalloc(&F, Nd * sizeof(C)));
-    CK(ctx, cudaMalloc(&X, sx * sizeof(C)));
-    if (sy) CK(ctx, cudaMalloc(&Y, sy * sizeof(C)));
-    CK(ctx, cudaMalloc(&Z, nd * sizeof(C)));
-    CK(ctx, cudaMalloc(&Gf, 4 * nd * sizeof(C)));
+    CK(ctx, pool_alloc((void**)&F, Nd * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&X, sx * sizeof(C), st));
+    if (sy) CK(ctx, pool_alloc((void**)&Y, sy * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&Z, nd * sizeof(C), st));
+    CK(ctx, pool_alloc((void**)&Gf, 4 * nd * sizeof(C), st));
     CK(ctx, cudaMemsetAsync(Gf, 0, 4 * nd * sizeof(C), st));
     for (int f = 0; f <= G.dim; ++f) {
         CK(ctx, launch_wtable<T>((const C*)p->B1, D, N, G.dim, G.L, ctx->p.sigma_g, 0, f - 1, F, st));
@@ -592,11 +604,11 @@ static int prep_fields(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, 
         }
         CK(ctx, launch_interleave<T>(Z, Gf, nd, f, st));
     }
+    pool_free(F, st);
+    pool_free(X, st);
+    pool_free(Y, st);
+    pool_free(Z, st);
     CK(ctx, cudaStreamSynchronize(st));
-    cudaFree(F);
-    cudaFree(X);
-    if (Y) cudaFree(Y);
-    cudaFree(Z);
     p->G = Gf;
     *out = p;
     return SD_OK;
@@ -812,6 +824,19 @@ int sd_create(sd_ctx** out, int device, const sd_params* p) {
         cudaGetLastError();
         return fail(nullptr, SD_ERR_CUDA, "CUDA device %d not available", device);
     }
+    {
+        // keep freed pool memory for reuse by later calls on this device
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(device);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+        if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    }
     sd_ctx* c = new sd_ctx();
     c->device = device;
     c->p = *p;
@@ -868,27 +893,28 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     float* tbox = nullptr;
     const int64_t n_tiles = (n_b + SDF_TILE - 1) / SDF_TILE;
     auto cleanup = [&]() {
-        cudaFree(xi); cudaFree(pm); cudaFree(rad); cudaFree(perm_q); cudaFree(perm_b);
-        cudaFree(bnd_s); cudaFree(nrm_s); cudaFree(tbox);
+        pool_free(xi, st); pool_free(pm, st); pool_free(rad, st); pool_free(perm_q, st); pool_free(perm_b, st);
+        pool_free(bnd_s, st); pool_free(nrm_s, st); pool_free(tbox, st);
     };
     auto fail_free = [&](int code, const char* what, cudaError_t e) {
         cleanup();
-        if (s->pos) cudaFree(s->pos);
-        if (s->c) cudaFree(s->c);
+        pool_free(s->pos, st);
+        pool_free(s->c, st);
         s->pos = s->c = nullptr;
         return fail(ctx, code, "sdf_build: %s: %s", what, cudaGetErrorString(e));
     };
     const size_t mm = (size_t)std::max<int64_t>(m, 1);
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&s->pos, mm * sizeof(vec4<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&s->c, mm * sizeof(cplx<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&xi, mm * sizeof(T))) != cudaSuccess || (e = cudaMalloc(&pm, mm)) != cudaSuccess ||
-        (e = cudaMalloc(&rad, 2 * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&perm_q, mm * sizeof(int32_t))) != cudaSuccess ||
-        (e = cudaMalloc(&perm_b, (size_t)n_b * sizeof(int32_t))) != cudaSuccess ||
-        (e = cudaMalloc(&bnd_s, (size_t)n_b * sizeof(vec4<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&nrm_s, (size_t)n_b * sizeof(vec4<T>))) != cudaSuccess ||
-        (e = cudaMalloc(&tbox, (size_t)n_tiles * 6 * sizeof(float))) != cudaSuccess)
+    if ((e = pool_alloc(&s->pos, mm * sizeof(vec4<T>), st)) != cudaSuccess ||
+        (e = pool_alloc(&s->c, mm * sizeof(cplx<T>), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&xi, mm * sizeof(T), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&pm, mm, st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&rad, 2 * sizeof(double), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&perm_q, mm * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&perm_b, (size_t)n_b * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&bnd_s, (size_t)n_b * sizeof(vec4<T>), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&nrm_s, (size_t)n_b * sizeof(vec4<T>), st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&tbox, (size_t)n_tiles * 6 * sizeof(float), st)) != cudaSuccess)
         return fail_free(SD_ERR_OOM, "allocation failed", e);
     // bounding radii of the queries and of the boundary samples
     double r2[2] = {0.0, 0.0};
@@ -899,8 +925,8 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     if (e != cudaSuccess) return fail_free(SD_ERR_CUDA, "radius", e);
     if (!isfinite(r2[0]) || !isfinite(r2[1])) {
         cleanup();
-        cudaFree(s->pos);
-        cudaFree(s->c);
+        pool_free(s->pos, st);
+        pool_free(s->c, st);
         s->pos = s->c = nullptr;
         return fail(ctx, SD_ERR_NONFINITE, "sdf_build: non-finite query or boundary point");
     }
@@ -936,6 +962,7 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail_free(SD_ERR_CUDA, "kernels", e);
     cleanup();
+    CK(ctx, cudaStreamSynchronize(st));
     s->radius = sqrt(r2[0]);
     *out = guard.release();
     return SD_OK;
@@ -971,11 +998,12 @@ int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m
     std::unique_ptr<sd_shape> guard(s);
     double* rad = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&s->pos, std::max<int64_t>(m, 1) * 4 * rs)) != cudaSuccess ||
-        (e = cudaMalloc(&s->c, std::max<int64_t>(m, 1) * 2 * rs)) != cudaSuccess ||
-        (e = cudaMalloc(&rad, sizeof(double))) != cudaSuccess) {
-        if (s->pos) cudaFree(s->pos);
-        if (s->c) cudaFree(s->c);
+    if ((e = pool_alloc(&s->pos, std::max<int64_t>(m, 1) * 4 * rs, st)) != cudaSuccess ||
+        (e = pool_alloc(&s->c, std::max<int64_t>(m, 1) * 2 * rs, st)) != cudaSuccess ||
+        (e = pool_alloc((void**)&rad, sizeof(double), st)) != cudaSuccess) {
+        pool_free(s->pos, st);
+        pool_free(s->c, st);
+        pool_free(rad, st);
         s->pos = s->c = nullptr;
         return fail(ctx, SD_ERR_OOM, "shape_from_samples: %s", cudaGetErrorString(e));
     }
@@ -987,10 +1015,10 @@ int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m
                                          : launch_radius<float>((const float4*)s->pos, m, ctx->p.dim, rad, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r2, rad, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(rad);
+    pool_free(rad, st);
     if (e != cudaSuccess) {
-        cudaFree(s->pos);
-        cudaFree(s->c);
+        pool_free(s->pos, st);
+        pool_free(s->c, st);
         s->pos = s->c = nullptr;
         return fail(ctx, SD_ERR_CUDA, "shape_from_samples: %s", cudaGetErrorString(e));
     }
@@ -999,6 +1027,7 @@ int sd_shape_from_samples(sd_ctx* ctx, const void* pos, const void* c, int64_t m
     e = (ctx->p.precision == SD_F64)
             ? sort_by_morton<double>((double4_32a*)s->pos, (double2*)s->c, m, s->radius, ctx->p.dim, st)
             : sort_by_morton<float>((float4*)s->pos, (float2*)s->c, m, s->radius, ctx->p.dim, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(ctx, SD_ERR_CUDA, "shape_from_samples: ordering failed: %s", cudaGetErrorString(e));
     *out = guard.release();
     return SD_OK;
@@ -1015,12 +1044,15 @@ int sd_shape_free(sd_shape* s) {
     if (!s) return SD_OK;
     DeviceGuard dg(s->ctx ? s->ctx->device : 0);
     if (s->ctx) drop_graphs(s->ctx);
-    if (s->pos) cudaFree(s->pos);
-    if (s->c) cudaFree(s->c);
+    // the shape's buffers may still be read by work on any stream: wait for the
+    // device, then hand them back to the pool
+    cudaDeviceSynchronize();
+    pool_free(s->pos, nullptr);
+    pool_free(s->c, nullptr);
     for (auto& p : s->preps) {
-        if (p.B1) cudaFree(p.B1);
-        if (p.W) cudaFree(p.W);
-        if (p.G) cudaFree(p.G);
+        pool_free(p.B1, nullptr);
+        pool_free(p.W, nullptr);
+        pool_free(p.G, nullptr);
     }
     delete s;
     return SD_OK;

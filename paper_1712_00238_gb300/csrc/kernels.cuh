@@ -14,6 +14,10 @@
 
 namespace sd {
 
+// Stream-ordered allocation from the device's memory pool (defined in api.cu).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
+
 // ---- SDF (Eq. 10A-17t) ------------------------------------------------------
 template <typename T>
 struct SdfArgs {

@@ -73,12 +73,12 @@ cudaError_t morton_order(const vec4<T>* pos, int64_t m, double radius, int dim, 
     size_t tmp_bytes = 0;
     cudaError_t e = cudaSuccess;
     auto done = [&](cudaError_t r) {
-        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(tmp);
+        pool_free(k0, st); pool_free(k1, st); pool_free(v0, st); pool_free(tmp, st);
         return r;
     };
-    if ((e = cudaMalloc(&k0, m * sizeof(uint32_t))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&k1, m * sizeof(uint32_t))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&v0, m * sizeof(int32_t))) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&k0, m * sizeof(uint32_t), st)) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&k1, m * sizeof(uint32_t), st)) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&v0, m * sizeof(int32_t), st)) != cudaSuccess) return done(e);
     const unsigned nb = (unsigned)((m + 255) / 256);
     k_morton_keys<T><<<nb, 256, 0, st>>>(pos, m, -R, scale, dim, k0, v0);
     note_launch();
@@ -86,10 +86,8 @@ cudaError_t morton_order(const vec4<T>* pos, int64_t m, double radius, int dim, 
     const int bits = (dim == 3) ? 30 : 32;
     e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k0, k1, v0, perm, (int)m, 0, bits, st);
     if (e != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) return done(e);
+    if ((e = pool_alloc(&tmp, tmp_bytes, st)) != cudaSuccess) return done(e);
     e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k0, k1, v0, perm, (int)m, 0, bits, st);
-    if (e != cudaSuccess) return done(e);
-    e = cudaStreamSynchronize(st);
     return done(e);
 }
 
@@ -102,12 +100,12 @@ cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, i
     cplx<T>* ct = nullptr;
     cudaError_t e = cudaSuccess;
     auto done = [&](cudaError_t r) {
-        cudaFree(perm); cudaFree(pt); cudaFree(ct);
+        pool_free(perm, st); pool_free(pt, st); pool_free(ct, st);
         return r;
     };
-    if ((e = cudaMalloc(&perm, m * sizeof(int32_t))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&pt, m * sizeof(vec4<T>))) != cudaSuccess) return done(e);
-    if ((e = cudaMalloc(&ct, m * sizeof(cplx<T>))) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&perm, m * sizeof(int32_t), st)) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&pt, m * sizeof(vec4<T>), st)) != cudaSuccess) return done(e);
+    if ((e = pool_alloc((void**)&ct, m * sizeof(cplx<T>), st)) != cudaSuccess) return done(e);
     if ((e = morton_order<T>(pos, m, radius, dim, perm, st)) != cudaSuccess) return done(e);
     if ((e = cudaMemcpyAsync(pt, pos, m * sizeof(vec4<T>), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return done(e);
@@ -115,8 +113,7 @@ cudaError_t sort_by_morton(vec4<T>* pos, cplx<T>* c, int64_t m, double radius, i
         return done(e);
     k_permute<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(perm, pt, ct, pos, c, m);
     note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
-    e = cudaStreamSynchronize(st);
+    e = cudaGetLastError();
     return done(e);
 }
 
