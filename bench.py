@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
     ap.add_argument("--spread-direct", type=int, default=1, help="1: global vector atomics; 0: spread by bins")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
+    ap.add_argument("--workload", choices=["peg_in_bore_3d", "docking_2000_500", "refine_256"],
+                    default="peg_in_bore_3d")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -129,15 +131,28 @@ class ClockSampler:
 # workload
 # ---------------------------------------------------------------------------
 
-def load_workload(n_rot: int = 0):
+def load_workload(n_rot: int = 0, name: str = "peg_in_bore_3d"):
     import copy
 
     from synth import configs
-    w = configs.peg_in_bore_3d()
+    w = getattr(configs, name)()
+    if name == "docking_2000_500" and not n_rot:
+        n_rot = w.extra["rot_per_launch"]  # one launch batch of 3,000 rotations per step
     if n_rot and n_rot < w.n_rot:
         w = copy.copy(w)
         w.quats = w.quats[:n_rot]
     return w
+
+
+WORKLOAD_TEXT = {
+    "peg_in_bore_3d": "peg_in_bore_3d: cylinder r1 l3 into 6x6x4 block, bore r1.02 depth 2.5; 20k boundary + "
+                      "~50k SDF samples per shape; 128^3 translations, n=256; 576 Hopf rotations; top-10 + FP64 "
+                      "re-score; 20-step gradient refinement",
+    "docking_2000_500": "docking_2000_500: sphere unions of 2,000 and 500 spheres (radii U[1.2,2.0], confined "
+                        "self-avoiding walks), 2 samples/A^2, ~80k/20k SDF samples; 192^3 translations at 0.8 A, "
+                        "n=384; 3,000 super-Fibonacci rotations (one launch batch of the 54,000); top-100 + FP64 "
+                        "re-score; 20-step gradient refinement of the top-10",
+}
 
 
 def host_inputs(w, torch):
@@ -195,7 +210,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = load_workload(args.rotations)
+    w = load_workload(args.rotations, args.workload)
+    top_k = w.top_k
     ctx = sd.Context(3, "f32", local, lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps,
                      sigma_g=w.sigma_g, w=w.w)
     ctx.set_option("batch", args.batch)
@@ -224,8 +240,9 @@ def run_ours(args):
         e1 = mark()
         ctx.score_rotations(fx, mv, inp["quats"], grid, out=cand)
         e2 = mark()
-        poses = ctx.top_k_poses(cand, TOP_K, fx, mv, inp["quats"], grid, rescore_fp64=True)
+        poses = ctx.top_k_poses(cand, top_k, fx, mv, inp["quats"], grid, rescore_fp64=True)
         e3 = mark()
+        poses = poses[:TOP_K]
         rots = torch.tensor([p["rot"] for p in poses], device=dev)
         q0 = inp["quats"][rots].float()
         t0 = torch.tensor([p["t"] for p in poses], dtype=torch.float32, device=dev)
@@ -304,7 +321,7 @@ def run_ours(args):
     # inputs, plus the pose indices / translations sent back for refinement
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + TOP_K * (8 + 12)
     # top-k candidates and FP64 re-scores, then the refined scores
-    d2h = TOP_K * (16 + 16) + TOP_K * 4
+    d2h = top_k * (16 + 16) + TOP_K * 4
 
     # roofline of the dominant search pass (live CUDA-event times of the timed steps)
     radius = float(np.linalg.norm(w.moving.query.pos, axis=1).max())
@@ -338,9 +355,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "peg_in_bore_3d: cylinder r1 l3 into 6x6x4 block, bore r1.02 depth 2.5; "
-                               "20k boundary + ~50k SDF samples per shape; 128^3 translations, n=256; "
-                               "576 Hopf rotations; top-10 + FP64 re-score; 20-step gradient refinement",
+        "config": {"workload": WORKLOAD_TEXT[args.workload],
                    "rotations": n_rot, "translations": w.N ** 3, "sub_box": s,
                    "batch": args.batch, "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
                    "spread": "global vector atomics" if args.spread_direct else "binned shared-memory tiles",
@@ -357,7 +372,7 @@ def run_ours(args):
         "top1": {"score": merged[0][0], "rot": merged[0][1], "idx": merged[0][2]},
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "peg_in_bore_3d":
         result["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -439,10 +454,121 @@ def run_reference(args):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# gradient refinement (score + gradient evaluations per second)
+# ---------------------------------------------------------------------------
+
+def run_refine(args):
+    """256 poses x 50 gradient-ascent steps on the docking pair, per step of the bench."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1712_00238_gb300 import sdfdock as sd
+    from synth import configs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = configs.docking_2000_500(1)
+    q0, t0 = configs.refine_poses_256()
+    poses, iters = len(q0), 50
+    ctx = sd.Context(3, "f32", local, lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps,
+                     sigma_g=w.sigma_g, w=w.w)
+    grid = sd.Grid(w.N, w.L)
+    shapes = []
+    for s in (w.fixed, w.moving):
+        b, q = s.boundary, s.query
+        shapes.append(ctx.sdf_build(b.pos, b.normal, b.area, q.pos, q.vol))
+    fx, mv = shapes
+    hq = torch.tensor(q0, dtype=torch.float32).pin_memory()
+    ht = torch.tensor(t0, dtype=torch.float32).pin_memory()
+    dq, dt = hq.to(dev), ht.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def run(k, e2e):
+        times, last = [], None
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                qi, ti = (hq.to(dev, non_blocking=True), ht.to(dev, non_blocking=True)) if e2e else (dq, dt)
+                _, _, hist = sd.refine_poses(ctx, fx, mv, grid, qi, ti, steps=iters, lr_t=0.2, lr_q=0.01)
+                last = hist[-1].cpu() if e2e else hist
+                b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return times, last
+
+    run(max(args.warmup, 1), False)
+    if world > 1:
+        dist.barrier()
+    l0 = sd.launch_count()
+    clocks = ClockSampler(local)
+    times, hist = run(args.steps, False)
+    clk = clocks.stop()
+    launches = sd.launch_count() - l0
+    e2e_times, _ = run(args.steps, True)
+    ms, ms_e2e = statistics.mean(times), statistics.mean(e2e_times)
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = t.tolist()
+    evals = poses * iters
+    gain = (hist[-1] - hist[0]).float()
+    result = {
+        "metric": "score+grad evals/s", "value": world * evals / (ms * 1e-3), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "refine_256: docking pair (2,000 / 500 spheres), 192^3 band-limited field on the "
+                               "n=384 grid; 256 random poses (seed 3), 50 gradient-ascent steps per bench step "
+                               "(type-2 gather score + gradient, autograd Function)",
+                   "poses": poses, "iterations": iters, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * evals / (ms_e2e * 1e-3), "unit": "evals/s",
+                "h2d_bytes_per_step": int(hq.numel() * 4 + ht.numel() * 4), "d2h_bytes_per_step": poses * 4},
+        "gpu_launches": int(launches // max(args.steps, 1)),
+        "roofline": None,
+        "score_gain": {"median": float(gain.median()), "min": float(gain.min())},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = refine_cpu_baseline(w, q0, t0)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def refine_cpu_baseline(w, q0, t0, n1=4000, n2=1000):
+    """The oracle's band-limited score + gradient on seeded sample subsets, scaled to full size."""
+    from oracle import score as oscore
+    rng = np.random.default_rng(np.random.SeedSequence([7, 98]))
+    p1 = w.fixed.query.pos[rng.choice(w.fixed.query.m, n1, replace=False)]
+    p2 = w.moving.query.pos[rng.choice(w.moving.query.m, n2, replace=False)]
+    c1 = rng.standard_normal(n1) + 1j * rng.standard_normal(n1)
+    c2 = rng.standard_normal(n2) + 1j * rng.standard_normal(n2)
+    t = time.perf_counter()
+    oscore.pair_grad_fN(p1, c1, p2, c2, q0[0], t0[0], w.N, w.L, w.sigma_g)
+    dt = time.perf_counter() - t
+    scale = (w.fixed.query.m * w.moving.query.m) / (n1 * n2)
+    return {"value": 1.0 / (dt * scale), "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one pose: FP64 pair sums of the band-limited kernel and its gradient over a seeded "
+                      f"{n1} x {n2} subset of the SDF samples, time scaled by the full pair count"}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "refine_256":
+        run_refine(args)
     else:
         run_ours(args)
 
