@@ -1,4 +1,4 @@
-// Batched line FFTs in shared memory: mixed radix (2, 3, 4, 8, 16) Stockham
+// Batched line FFTs in shared memory: mixed radix (2, 3, 4, 8, 12, 16, 24) Stockham
 // autosort stages (Van Loan, "Computational Frameworks for the FFT", 1992).
 //
 // Each stage of radix R over a line of LEN points takes, for every butterfly
@@ -27,11 +27,11 @@ __host__ __device__ constexpr int plan_radix(int len, int s) {
         case 32: return s == 0 ? 8 : (s == 1 ? 4 : 0);
         case 48: return s == 0 ? 16 : (s == 1 ? 3 : 0);
         case 64: return s == 0 ? 8 : (s == 1 ? 8 : 0);
-        case 96: return s == 0 ? 8 : (s == 1 ? 4 : (s == 2 ? 3 : 0));
+        case 96: return s == 0 ? 8 : (s == 1 ? 12 : 0);
         case 128: return s == 0 ? 16 : (s == 1 ? 8 : 0);
-        case 192: return s == 0 ? 16 : (s == 1 ? 4 : (s == 2 ? 3 : 0));
+        case 192: return s == 0 ? 16 : (s == 1 ? 12 : 0);
         case 256: return s == 0 ? 16 : (s == 1 ? 16 : 0);
-        case 384: return s == 0 ? 16 : (s == 1 ? 8 : (s == 2 ? 3 : 0));
+        case 384: return s == 0 ? 16 : (s == 1 ? 24 : 0);
         case 512: return s == 0 ? 8 : (s == 1 ? 8 : (s == 2 ? 8 : 0));
         default: return 0;
     }
@@ -76,6 +76,59 @@ __host__ __device__ __forceinline__ C w16(int m) {
         default: cr = 1; si = 0; break;  // not used by dft16
     }
     return INV ? mk(cr, si) : mk(cr, -si);
+}
+
+// exp(-+2 pi i m / 24), m in [0, 24): the angle r * 15 degrees of its quadrant
+// (r = m mod 6) rotated by -+i per quadrant.  cos 15 = (sqrt 6 + sqrt 2) / 4,
+// sin 15 = (sqrt 6 - sqrt 2) / 4.
+template <bool INV, typename C>
+__host__ __device__ __forceinline__ C w24(int m) {
+    using T = decltype(C{}.x);
+    const T c15 = T(0.96592582628906828675), s15 = T(0.25881904510252076235);
+    const T c30 = T(0.86602540378443864676), r = T(0.70710678118654752440);
+    T c, s;  // cos and sin of (m mod 6) * 15 degrees
+    switch (m % 6) {
+        case 0: c = 1; s = 0; break;
+        case 1: c = c15; s = s15; break;
+        case 2: c = c30; s = T(0.5); break;
+        case 3: c = r; s = r; break;
+        case 4: c = T(0.5); s = c30; break;
+        default: c = s15; s = c15; break;
+    }
+    T x, y;  // exp(-i theta) rotated by (-i)^quadrant
+    switch ((m / 6) & 3) {
+        case 0: x = c; y = -s; break;
+        case 1: x = -s; y = -c; break;
+        case 2: x = -c; y = s; break;
+        default: x = s; y = c; break;
+    }
+    return INV ? mk(x, -y) : mk(x, y);
+}
+
+template <int R, bool INV, typename C>
+__host__ __device__ __forceinline__ void dft(C* v);
+
+// R = 3 Q points (Q = 4 or 8) by one Cooley-Tukey split: input n = Q n1 + n2,
+// output k = k1 + 3 k2; 3-point DFTs over n1, twiddles w_R^(n2 k1), Q-point
+// DFTs over n2.
+template <int Q, bool INV, typename C>
+__host__ __device__ __forceinline__ void dft3q(C* v) {
+    constexpr int R = 3 * Q;
+    C b[3][Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        C t[3] = {v[n2], v[Q + n2], v[2 * Q + n2]};
+        dft<3, INV>(t);
+        b[0][n2] = t[0];
+#pragma unroll
+        for (int k1 = 1; k1 < 3; ++k1) b[k1][n2] = n2 == 0 ? t[k1] : cmul(t[k1], w24<INV, C>((24 / R) * n2 * k1));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        dft<Q, INV>(b[k1]);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + 3 * k2] = b[k1][k2];
+    }
 }
 
 template <int R, bool INV, typename C>
@@ -127,6 +180,10 @@ __host__ __device__ __forceinline__ void dft(C* v) {
             dft4<INV>(x0, x1, x2, x3);
             v[k1] = x0; v[k1 + 4] = x1; v[k1 + 8] = x2; v[k1 + 12] = x3;
         }
+    } else if constexpr (R == 12) {
+        dft3q<4, INV>(v);
+    } else if constexpr (R == 24) {
+        dft3q<8, INV>(v);
     }
 }
 
@@ -193,45 +250,6 @@ __host__ __device__ __forceinline__ void stockham_store(C* __restrict__ line, in
 }
 
 #ifdef __CUDACC__
-// In-place transform of NL lines held at buf + line*ld by a block of exactly
-// 256 threads: each stage loads its butterflies into registers, synchronises,
-// and stores them back.  `tw` is the stage-ordered table of LEN.  Contains
-// __syncthreads(); every thread of the block must call it.
-constexpr int FFT_THREADS = 256;
-
-template <typename C, int LEN, bool INV, int NL, int S = 0, int P = 1>
-__device__ __forceinline__ void fft_inplace(C* buf, int ld, const C* tw) {
-    constexpr int R = plan_radix(LEN, S);
-    if constexpr (R != 0) {
-        constexpr int NB = LEN / R;
-        constexpr int TOT = NL * NB;
-        constexpr int PER = (TOT + FFT_THREADS - 1) / FFT_THREADS;
-        const C* tws = tw + tw_offset(LEN, S);
-        C v[PER][R];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int t = threadIdx.x + q * FFT_THREADS;
-            if (TOT % FFT_THREADS == 0 || t < TOT) {
-                const int line = t / NB;
-                stockham_load<C, LEN, R, P, INV>(buf + line * ld, t - line * NB, tws, v[q]);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int t = threadIdx.x + q * FFT_THREADS;
-            if (TOT % FFT_THREADS == 0 || t < TOT) {
-                const int line = t / NB;
-                stockham_store<C, LEN, R, P>(buf + line * ld, t - line * NB, v[q]);
-            }
-        }
-        __syncthreads();
-        fft_inplace<C, LEN, INV, NL, S + 1, P * R>(buf, ld, tw);
-    }
-}
-#endif
-
-#ifdef __CUDACC__
 // Line transforms whose first stage reads its inputs through a loader (global
 // memory, registers in flight) and whose last stage hands its outputs to an
 // emitter (global memory or the next step), so only the stages in between go
@@ -239,7 +257,8 @@ __device__ __forceinline__ void fft_inplace(C* buf, int ld, const C* tw) {
 //
 // LAY_ROW: lines are contiguous (a warp's lanes take consecutive butterflies of
 // one line); LAY_COL: lines are columns (lanes take consecutive lines).  NL lines
-// per block of FFT_THREADS threads.  load(line, pos) returns input `pos`;
+// per block of NT threads; a stage with fewer butterflies than NT leaves the
+// rest of the threads idle until its barrier.  load(line, pos) returns input `pos`;
 // emit(line, o, v) receives output `o` (natural order).  SRC_SMEM: the inputs
 // are already in `buf` (pitch ld, padded) and are read from there.
 enum { LAY_ROW = 0, LAY_COL = 1 };
@@ -255,20 +274,20 @@ __device__ __forceinline__ void butterfly_of(int t, int& line, int& i) {
     }
 }
 
-template <typename C, int LEN, bool INV, int NL, int LAY, bool SRC_SMEM, int S = 0, int P = 1, typename Load,
-          typename Emit>
+template <typename C, int LEN, bool INV, int NL, int NT, int LAY, bool SRC_SMEM, int S = 0, int P = 1,
+          typename Load, typename Emit>
 __device__ __forceinline__ void fft_lines_io(C* buf, int ld, const C* tw, Load& load, Emit& emit) {
     constexpr int R = plan_radix(LEN, S);
     constexpr bool first = (S == 0);
     constexpr bool last = (plan_radix(LEN, S + 1) == 0);
     constexpr int NB = LEN / R;
     constexpr int TOT = NL * NB;
-    constexpr int PER = (TOT + FFT_THREADS - 1) / FFT_THREADS;
+    constexpr int PER = (TOT + NT - 1) / NT;
     C v[PER][R];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int t = threadIdx.x + q * FFT_THREADS;
-        if (TOT % FFT_THREADS == 0 || t < TOT) {
+        const int t = threadIdx.x + q * NT;
+        if (TOT % NT == 0 || t < TOT) {
             int line, i;
             butterfly_of<LAY, NL, NB>(t, line, i);
             if constexpr (first && !SRC_SMEM) {
@@ -283,8 +302,8 @@ __device__ __forceinline__ void fft_lines_io(C* buf, int ld, const C* tw, Load& 
     if constexpr (!first || SRC_SMEM) __syncthreads();  // every read of buf before any write
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-        const int t = threadIdx.x + q * FFT_THREADS;
-        if (TOT % FFT_THREADS == 0 || t < TOT) {
+        const int t = threadIdx.x + q * NT;
+        if (TOT % NT == 0 || t < TOT) {
             int line, i;
             butterfly_of<LAY, NL, NB>(t, line, i);
             if constexpr (last) {
@@ -297,7 +316,7 @@ __device__ __forceinline__ void fft_lines_io(C* buf, int ld, const C* tw, Load& 
     }
     if constexpr (!last) {
         __syncthreads();
-        fft_lines_io<C, LEN, INV, NL, LAY, SRC_SMEM, S + 1, P * R>(buf, ld, tw, load, emit);
+        fft_lines_io<C, LEN, INV, NL, NT, LAY, SRC_SMEM, S + 1, P * R>(buf, ld, tw, load, emit);
     }
 }
 #endif

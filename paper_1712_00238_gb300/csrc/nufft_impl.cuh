@@ -39,6 +39,22 @@ __host__ __device__ constexpr int lines_per_cta() {
     return (LEN * (int)sizeof(cplx<T>) > 4096) ? 8 : 16;
 }
 
+// Threads of a line-pass CTA: the butterflies of the plan's widest stage over
+// the CTA's lines (one butterfly per thread per stage), rounded up to whole
+// warps, at least 64.  Wider than 384 butterflies (512-point lines) the CTA
+// keeps 256 threads with two butterflies each: registers would otherwise allow
+// only one CTA per SM.
+template <typename T, int LEN>
+__host__ __device__ constexpr int cta_threads() {
+    int most = 0;
+    for (int s = 0; plan_radix(LEN, s) != 0; ++s) {
+        const int nb = lines_per_cta<T, LEN>() * (LEN / plan_radix(LEN, s));
+        most = nb > most ? nb : most;
+    }
+    most = (most + 31) / 32 * 32;
+    return most < 64 ? 64 : (most > 384 ? 256 : most);
+}
+
 // ---------------------------------------------------------------------------
 // spreading
 // ---------------------------------------------------------------------------
@@ -374,7 +390,7 @@ __device__ __forceinline__ void block_argmax(T& best, int& bidx) {
 
 // Row passes: TR consecutive rows of one rotation per CTA.
 template <typename T, int LEN, int MODE>
-__global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), cta_threads<T, LEN>() == 384 ? 3 : 1) k_rows(RowArgs<T> a) {
     using C = cplx<T>;
     constexpr int TR = lines_per_cta<T, LEN>();
     constexpr int LD = line_pitch(LEN);
@@ -420,7 +436,7 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
             out[(int64_t)row * a.out_row_stride + o] = v;
         }
     };
-    fft_lines_io<C, LEN, INV, TR, LAY_ROW, false>(buf, LD, tw, load, emit);
+    fft_lines_io<C, LEN, INV, TR, cta_threads<T, LEN>(), LAY_ROW, false>(buf, LD, tw, load, emit);
     if constexpr (MODE == ROW_INV_ARGMAX) {
         block_argmax(best, bidx);
         if (threadIdx.x == 0) {
@@ -433,9 +449,10 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> a) {
 
 // Column passes: TC adjacent columns of one (rotation, outer) slab per CTA.
 template <typename T, int LENF, int LENI, int MODE>
-__global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
+__global__ void __launch_bounds__(cta_threads<T, LENF>(), cta_threads<T, LENF>() == 384 ? 3 : 1) k_cols(ColArgs<T> a) {
     using C = cplx<T>;
     constexpr int TC = lines_per_cta<T, LENF>();
+    constexpr int NT = cta_threads<T, LENF>();
     constexpr int LD = line_pitch(LENF);
     constexpr int NTWF = tw_count(LENF);
     constexpr int NTWI = (MODE == COL_FUSED) ? tw_count(LENI) : 0;
@@ -480,13 +497,13 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
             const int gcol = col0 + line;
             if (kp >= 0 && gcol < ncols) buf[line * LD + pad(kp)] = cmul(v, a.W[(int64_t)kp * ncols + gcol]);
         };
-        fft_lines_io<C, LENF, false, TC, LAY_COL, false>(buf, LD, twF, load, emit_fwd);
+        fft_lines_io<C, LENF, false, TC, NT, LAY_COL, false>(buf, LD, twF, load, emit_fwd);
         __syncthreads();
         auto emit_out = [&](int line, int o, C v) {
             const int gcol = col0 + line;
             if (gcol < ncols) out[(int64_t)o * ncols + gcol] = v;
         };
-        fft_lines_io<C, LENI, true, TC, LAY_COL, true>(buf, LD, twI, load, emit_out);
+        fft_lines_io<C, LENI, true, TC, NT, LAY_COL, true>(buf, LD, twI, load, emit_out);
     } else {
         auto emit = [&](int line, int o, C v) {
             const int gcol = col0 + line;
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(256) k_cols(ColArgs<T> a) {
                 out[(int64_t)o * ncols + gcol] = v;
             }
         };
-        fft_lines_io<C, LENF, INV1, TC, LAY_COL, false>(buf, LD, twF, load, emit);
+        fft_lines_io<C, LENF, INV1, TC, NT, LAY_COL, false>(buf, LD, twF, load, emit);
     }
 }
 
@@ -536,7 +553,7 @@ static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaSt
     auto kern = k_rows<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nb, batch), 256, smem, st>>>(a);
+    kern<<<dim3(nb, batch), cta_threads<T, LEN>(), smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
@@ -551,7 +568,7 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     auto kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nb, a.nouter, batch), 256, smem, st>>>(a);
+    kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LENF>(), smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
