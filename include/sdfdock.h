@@ -115,7 +115,12 @@ const char* sd_last_error(const sd_ctx* ctx);
  * row; 0: sort the samples into 8^d-cell bins and accumulate each bin's taps in
  * shared memory first), "sdf_cull" (1, the default: the SDF sums skip boundary
  * tiles that lie beyond the truncation radius of every query of a block; 0: sum
- * over every tile; results are the same). */
+ * over every tile; results are the same), "autotune" (1: before a scoring job
+ * runs, time its candidate plans -- rotations per batch from a quarter to
+ * twice the automatic choice, direct or binned spreading -- on its first
+ * rotations and keep the fastest; the choice is cached per precision, grid,
+ * sub-box size and sample-count octave; ignored when "batch" or "plain" is
+ * set; results do not depend on the plan beyond FP32 rounding). */
 int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
 
 /* ---- shapes: the sampled SDF (Section 4, Eq. 10A-17t) ------------------- */
@@ -171,6 +176,45 @@ int sd_score_rotations(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movin
 int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving,
                   const double* quats, int64_t n_r, const sd_grid* g, void* map_out,
                   void* stream);
+
+/* One scoring job of sd_score_pairs: a pair of shapes of this context, its
+ * grid, its rotations (device, n_r x 4 double) and its per-rotation argmax
+ * output (device, n_r sd_cand), as for sd_score_rotations with k_r = 1. */
+typedef struct sd_pair_job {
+    const sd_shape* fixed;
+    const sd_shape* moving;
+    const double* quats;
+    int64_t n_r;
+    sd_grid grid;
+    sd_cand* cand_out;
+} sd_pair_job;
+
+/* Per-job report of sd_score_pairs. */
+typedef struct sd_pair_stat {
+    double ms;            /* device time of the job within the call */
+    int32_t batch;        /* rotations per batch of its plan */
+    int32_t spread_bins;  /* 1 if its plan spreads by bins */
+    int32_t n;            /* oversampled grid size per axis */
+    int32_t s;            /* sub-box side of its moving shape */
+} sd_pair_stat;
+
+/* Score many shape pairs, each on its own grid and rotation list, in one
+ * launch sequence on `stream` (Section 5's search applied to a batch of
+ * problems).  Each job runs with its own plan (autotuned when the "autotune"
+ * option is on); the workspace is sized once for the largest job.  The first
+ * call with a given job list runs eagerly; later calls with the same list
+ * replay one captured CUDA graph holding every job.  Results equal
+ * sd_score_rotations on each job.
+ *   jobs   host, n_jobs sd_pair_job; pointers inside stay valid while the
+ *          context may replay the graph (until sd_shape_free or sd_destroy)
+ *   stats  host, n_jobs sd_pair_stat, or NULL.  When given, the call
+ *          synchronises on the end of the sequence and fills each job's time
+ *          (from events around each job) and plan; otherwise it is
+ *          asynchronous.
+ * Errors: SD_ERR_ARG for a bad job (NULL pointer, n_r < 1, a shape of another
+ * context), as sd_score_rotations otherwise. */
+int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats,
+                   void* stream);
 
 /* Global top-k over per-rotation candidates, ordered by score descending,
  * then rotation ascending, then translation index ascending; optionally each

@@ -38,6 +38,13 @@ struct Prep {  // fixed-shape tables for one grid
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> events;  // event nodes of a multi-job graph (owned)
+    long long kernels = 0;            // kernel launches captured (counted again at every replay)
+};
+
+struct Plan {      // launch plan of one scoring job
+    int B = 1;     // rotations per launch sequence
+    int bins = 0;  // 1: bin-sorted spreading, 0: direct
 };
 
 struct TimerRec {
@@ -59,6 +66,8 @@ struct sd_ctx {
     int opt_plain = 0;
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
+    int opt_autotune = 0;       // 1: time candidate plans per job geometry
+    std::map<std::string, Plan> tuned;
     DevBuf ws[8];
     std::map<std::pair<int, int>, void*> twiddles;  // (len, precision)
     std::map<std::tuple<int, int, int, double>, double*> deconv;
@@ -188,7 +197,10 @@ void sd::pool_free(void* p, cudaStream_t st) {
 // Captured graphs hold raw workspace and table pointers: drop them before any
 // of those buffers is freed.
 static void drop_graphs(sd_ctx* ctx) {
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto e : kv.second.events) cudaEventDestroy(e);
+    }
     ctx->graphs.clear();
     ctx->seen.clear();
 }
@@ -436,13 +448,17 @@ static cudaError_t pass_y_inv(const Geo& G, const Tw<T>& tw, cplx<T>* buf, int64
     return launch_cols<T>(COL_INV, c, batch, st);
 }
 
-// Bin workspace of one spread batch (slot 6).
-static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* bn) {
+// Bin workspace of one spread batch (slot 6): its size and its layout.
+static size_t bins_bytes(int s, int dim, int64_t m, int batch) {
     const int nb = (s + 7) / 8;
     const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
     const size_t ints = (size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m;
-    void* p = nullptr;
-    CKI(ws_get(ctx, 6, ints * sizeof(int) + 1024, &p));
+    return ints * sizeof(int) + 1024;
+}
+
+static void bins_layout(void* p, int s, int dim, int64_t m, int batch, BinArgs* bn) {
+    const int nb = (s + 7) / 8;
+    const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
     int* q = (int*)p;
     bn->nb = nb;
     bn->nbins = nbins;
@@ -455,6 +471,12 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* 
     bn->rank = q;
     q += (size_t)batch * m;
     bn->sorted = q;
+}
+
+static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* bn) {
+    void* p = nullptr;
+    CKI(ws_get(ctx, 6, bins_bytes(s, dim, m, batch), &p));
+    bins_layout(p, s, dim, m, batch, bn);
     return SD_OK;
 }
 
@@ -642,135 +664,277 @@ static int choose_batch(sd_ctx* ctx, const Geo& G, int64_t n_r) {
     return (int)b;
 }
 
-// Runs the batched passes for rotations [0, n_r).  mode 0: argmax candidates; 1: maps.
+// One scoring job (a fixed shape, a moving shape, a grid and a rotation list)
+// with its launch plan and, once bound, its workspace pointers.
+template <typename T>
+struct Search {
+    const sd_shape* moving = nullptr;
+    const double* quats = nullptr;
+    int64_t n_r = 0;
+    Geo G{};
+    Tw<T> tw{};
+    const cplx<T>* W = nullptr;
+    void* out = nullptr;
+    int maps = 0;
+    Plan plan{};
+    int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
+    cplx<T>* b0 = nullptr;
+    cplx<T>* b1 = nullptr;
+    double* ps = nullptr;
+    int* pi = nullptr;
+    BinArgs bn{};
+};
+
+// Fixed-shape tables, geometry, twiddles and the default plan of a job (may
+// synchronise the stream the first time a fixed shape meets a grid).
+template <typename T>
+static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
+                        const sd_grid* g, void* out, int maps, cudaStream_t st, Search<T>* S) {
+    Prep* prep = nullptr;
+    CKI(prep_fixed<T>(ctx, const_cast<sd_shape*>(fixed), g, &prep, st));
+    CKI(make_geo(ctx, g, moving->radius, &S->G));
+    CKI(get_tw<T>(ctx, S->G, &S->tw, st));
+    S->moving = moving;
+    S->quats = quats;
+    S->n_r = n_r;
+    S->W = (const cplx<T>*)prep->W;
+    S->out = out;
+    S->maps = maps;
+    S->plan.B = choose_batch<T>(ctx, S->G, n_r);
+    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx->p.w)) ? 1 : 0;
+    per_rot_elems<T>(S->G, &S->e0, &S->e1);
+    S->rows_last = (S->G.dim == 2) ? S->G.N : (int64_t)S->G.N * S->G.N;
+    S->Nd = (S->G.dim == 2) ? (int64_t)S->G.N * S->G.N : (int64_t)S->G.N * S->G.N * S->G.N;
+    return SD_OK;
+}
+
+// Workspace bytes per slot of a job under its plan (maximum into need[]).
+template <typename T>
+static void search_need(const Search<T>& S, size_t need[8]) {
+    const size_t B = (size_t)S.plan.B;
+    need[0] = std::max(need[0], B * S.e0 * sizeof(cplx<T>));
+    need[1] = std::max(need[1], B * S.e1 * sizeof(cplx<T>));
+    need[2] = std::max(need[2], B * S.rows_last * sizeof(double));  // at most one partial per row
+    need[3] = std::max(need[3], B * S.rows_last * sizeof(int));
+    if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B));
+}
+
+static int ws_reserve(sd_ctx* ctx, const size_t need[8]) {
+    void* p;
+    for (int k = 0; k < 8; ++k)
+        if (need[k]) CKI(ws_get(ctx, k, need[k], &p));
+    return SD_OK;
+}
+
+// Points a job at the (reserved) workspace.
+template <typename T>
+static void search_bind(sd_ctx* ctx, Search<T>* S) {
+    S->b0 = (cplx<T>*)ctx->ws[0].p;
+    S->b1 = (cplx<T>*)ctx->ws[1].p;
+    S->ps = (double*)ctx->ws[2].p;
+    S->pi = (int*)ctx->ws[3].p;
+    if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, &S->bn);
+}
+
+// Launch sequence of rotations [r_lo, r_hi), plan.B rotations at a time.
+// mode 0 writes per-rotation argmax candidates, mode 1 whole maps.
+template <typename T>
+static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t r_hi, cudaStream_t s, bool timed) {
+    using C = cplx<T>;
+    const Geo& G = S.G;
+    const int B = S.plan.B;
+    for (int64_t r0 = r_lo; r0 < r_hi; r0 += B) {
+        const int b = (int)std::min<int64_t>(B, r_hi - r0);
+        {
+            PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
+            CK(ctx, cudaMemsetAsync(S.b0, 0, (size_t)b * S.e0 * sizeof(C), s));
+        }
+        SpreadArgs<T> sa{};
+        sa.pos = (const vec4<T>*)S.moving->pos;
+        sa.c = (const C*)S.moving->c;
+        sa.m = S.moving->m;
+        sa.quats = S.quats;
+        sa.rot0 = r0;
+        sa.sign = T(-1);
+        sa.inv_h = (T)G.inv_h;
+        sa.beta = (T)ctx->p.beta;
+        sa.w = ctx->p.w;
+        sa.s = G.s;
+        sa.s_h = G.s_h;
+        sa.out = S.b0;
+        sa.out_rot_stride = S.e0;
+        sa.n_full = G.n;
+        {
+            PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
+            if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
+            else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
+        }
+        {
+            PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
+            CK(ctx, pass_x_fwd<T>(G, S.tw, S.b0, S.e0, S.b1, S.e1, b, s));
+        }
+        C* fin;
+        int64_t fin_rs;
+        if (G.dim == 3) {
+            {
+                PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
+                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s));
+            }
+            {
+                PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
+                CK(ctx, pass_last<T>(COL_FUSED, G, S.tw, S.b0, S.e0, S.b1, S.e1, S.W, b, s));
+            }
+            {
+                PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
+                CK(ctx, pass_y_inv<T>(G, S.tw, S.b1, S.e1, b, s));
+            }
+            fin = S.b1;
+            fin_rs = S.e1;
+        } else {
+            PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
+            CK(ctx, pass_last<T>(COL_FUSED, G, S.tw, S.b1, S.e1, S.b0, S.e0, S.W, b, s));
+            fin = S.b0;
+            fin_rs = S.e0;
+        }
+        RowArgs<T> r{};
+        r.in = fin;
+        r.in_rot_stride = fin_rs;
+        r.nrows = (int)S.rows_last;
+        r.in_row_stride = G.N;
+        r.out_row_stride = G.N;
+        r.len_in = G.N;
+        r.N = G.N;
+        r.n = G.n;
+        r.tw = S.tw.N;
+        if (S.maps) {
+            r.out = (C*)S.out + r0 * S.Nd;
+            r.out_rot_stride = S.Nd;
+            PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
+            CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
+        } else {
+            int nparts = 0;
+            r.part_score = S.ps;
+            r.part_idx = S.pi;
+            {
+                PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
+                CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
+            }
+            PassTimer pt(ctx, SD_PASS_REDUCE, s, timed);
+            CK(ctx, launch_reduce_argmax(S.ps, S.pi, nparts, b, r0, S.out, s));
+        }
+    }
+    return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: per job geometry, the plan (rotations per launch, spreading
+// variant) with the lowest measured time per rotation
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static std::string plan_key(sd_ctx* ctx, const Search<T>& S) {
+    // jobs of one grid whose sub-boxes and sample counts are close share a plan
+    int lg = 0;
+    for (int64_t m = S.moving->m; m > 1; m >>= 1) ++lg;
+    char key[128];
+    snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%d", ctx->p.precision, S.G.dim, S.G.N, S.G.n, S.G.s / 16, lg);
+    return key;
+}
+
+// Times each candidate plan on the job's own first rotations (CUDA events on
+// the stream, after one untimed run) and keeps the fastest per rotation.  The
+// job's outputs for those rotations are overwritten when it runs.
+template <typename T>
+static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
+    const std::string key = plan_key(ctx, *S);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        S->plan.B = (int)std::min<int64_t>(it->second.B, std::max<int64_t>(S->n_r, 1));
+        S->plan.bins = it->second.bins;
+        return SD_OK;
+    }
+    const int b0 = S->plan.B;
+    std::vector<Plan> cand;
+    for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
+        if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
+        for (int bins = 0; bins <= (bins_supported(ctx->p.w) ? 1 : 0); ++bins) {
+            bool dup = false;
+            for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
+            if (!dup) cand.push_back(Plan{B, bins});
+        }
+    }
+    int most = 1;
+    for (auto& c : cand) most = std::max(most, c.B);
+    const int64_t n_trial = std::min<int64_t>(S->n_r, 2 * (int64_t)most);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(ctx, cudaEventCreate(&e0));
+    CK(ctx, cudaEventCreate(&e1));
+    Plan best = S->plan;
+    double best_ms = INFINITY;
+    int rc = SD_OK;
+    for (auto& c : cand) {
+        Search<T> t = *S;
+        t.plan = c;
+        size_t need[8] = {};
+        search_need(t, need);
+        if ((rc = ws_reserve(ctx, need)) != SD_OK) break;
+        search_bind(ctx, &t);
+        if ((rc = search_enqueue(ctx, t, 0, std::min<int64_t>(n_trial, c.B), st, false)) != SD_OK) break;
+        cudaEventRecord(e0, st);
+        if ((rc = search_enqueue(ctx, t, 0, n_trial, st, false)) != SD_OK) break;
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(ctx, SD_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        const double per = ms / (double)n_trial;
+        if (per < best_ms) {
+            best_ms = per;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SD_OK) return rc;
+    ctx->tuned[key] = best;
+    S->plan = best;
+    return SD_OK;
+}
+
+// Runs one job: workspace, then the launch sequence (eager, or replayed from a
+// captured graph when the "graph" option is on).
 template <typename T>
 static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
                       const sd_grid* g, void* out, int maps, cudaStream_t st) {
-    using C = cplx<T>;
-    Prep* prep = nullptr;
-    CKI(prep_fixed<T>(ctx, const_cast<sd_shape*>(fixed), g, &prep, st));
-    Geo G;
-    CKI(make_geo(ctx, g, moving->radius, &G));
-    Tw<T> tw;
-    CKI(get_tw<T>(ctx, G, &tw, st));
-    const int B = choose_batch<T>(ctx, G, n_r);
-    int64_t e0, e1;
-    per_rot_elems<T>(G, &e0, &e1);
-    void *b0v, *b1v, *psv, *piv;
-    CKI(ws_get(ctx, 0, (size_t)B * e0 * sizeof(C), &b0v));
-    CKI(ws_get(ctx, 1, (size_t)B * e1 * sizeof(C), &b1v));
-    const int64_t rows_last = (G.dim == 2) ? G.N : (int64_t)G.N * G.N;
-    const int64_t max_parts = rows_last;  // at most one partial per row
-    CKI(ws_get(ctx, 2, (size_t)B * max_parts * sizeof(double), &psv));
-    CKI(ws_get(ctx, 3, (size_t)B * max_parts * sizeof(int), &piv));
-    C* b0 = (C*)b0v;
-    C* b1 = (C*)b1v;
-    const C* W = (const C*)prep->W;
-    const bool use_bins = !ctx->opt_spread_direct && bins_supported(ctx->p.w);
-    BinArgs bn{};
-    if (use_bins) CKI(bins_for(ctx, G.s, G.dim, moving->m, B, &bn));
-    const int64_t Nd = (G.dim == 2) ? (int64_t)G.N * G.N : (int64_t)G.N * G.N * G.N;
-
-    // One launch sequence per batch; optionally replayed from a captured graph.
-    auto enqueue = [&](cudaStream_t s, bool timed) -> int {
-        for (int64_t r0 = 0; r0 < n_r; r0 += B) {
-            const int b = (int)std::min<int64_t>(B, n_r - r0);
-            {
-                PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
-                CK(ctx, cudaMemsetAsync(b0, 0, (size_t)b * e0 * sizeof(C), s));
-            }
-            SpreadArgs<T> sa{};
-            sa.pos = (const vec4<T>*)moving->pos;
-            sa.c = (const C*)moving->c;
-            sa.m = moving->m;
-            sa.quats = quats;
-            sa.rot0 = r0;
-            sa.sign = T(-1);
-            sa.inv_h = (T)G.inv_h;
-            sa.beta = (T)ctx->p.beta;
-            sa.w = ctx->p.w;
-            sa.s = G.s;
-            sa.s_h = G.s_h;
-            sa.out = b0;
-            sa.out_rot_stride = e0;
-                    sa.n_full = G.n;
-            {
-                PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
-                if (use_bins) CK(ctx, launch_spread_bins<T>(sa, bn, G.dim, b, s));
-                else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
-            }
-            {
-                PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
-                CK(ctx, pass_x_fwd<T>(G, tw, b0, e0, b1, e1, b, s));
-            }
-            C* fin;
-            int64_t fin_rs;
-            if (G.dim == 3) {
-                {
-                    PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
-                    CK(ctx, pass_y_fwd<T>(G, tw, b1, e1, b0, e0, b, s));
-                }
-                {
-                    PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                    CK(ctx, pass_last<T>(COL_FUSED, G, tw, b0, e0, b1, e1, W, b, s));
-                }
-                {
-                    PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
-                    CK(ctx, pass_y_inv<T>(G, tw, b1, e1, b, s));
-                }
-                fin = b1;
-                fin_rs = e1;
-            } else {
-                PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                CK(ctx, pass_last<T>(COL_FUSED, G, tw, b1, e1, b0, e0, W, b, s));
-                fin = b0;
-                fin_rs = e0;
-            }
-            RowArgs<T> r{};
-            r.in = fin;
-            r.in_rot_stride = fin_rs;
-            r.nrows = (int)rows_last;
-            r.in_row_stride = G.N;
-            r.out_row_stride = G.N;
-            r.len_in = G.N;
-            r.N = G.N;
-            r.n = G.n;
-            r.tw = tw.N;
-            if (maps) {
-                r.out = (C*)out + r0 * Nd;
-                r.out_rot_stride = Nd;
-                PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
-                CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
-            } else {
-                int nparts = 0;
-                r.part_score = (double*)psv;
-                r.part_idx = (int*)piv;
-                {
-                    PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
-                    CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
-                }
-                PassTimer pt(ctx, SD_PASS_REDUCE, s, timed);
-                CK(ctx, launch_reduce_argmax((const double*)psv, (const int*)piv, nparts, b, r0, out, s));
-            }
-        }
-        return SD_OK;
-    };
+    Search<T> S;
+    CKI(search_setup<T>(ctx, fixed, moving, quats, n_r, g, out, maps, st, &S));
+    if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) CKI(autotune<T>(ctx, &S, st));
+    size_t need[8] = {};
+    search_need(S, need);
+    CKI(ws_reserve(ctx, need));
+    search_bind(ctx, &S);
 
     if (ctx->opt_graph && !ctx->opt_plain && st != nullptr) {
         char key[256];
-        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d", (const void*)fixed, (const void*)moving,
-                 (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, B);
+        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d", (const void*)fixed, (const void*)moving,
+                 (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B, S.plan.bins);
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
-            if (ctx->seen[k]++ == 0) return enqueue(st, true);  // first call runs eagerly (sets kernel attributes)
+            if (ctx->seen[k]++ == 0) return search_enqueue(ctx, S, 0, n_r, st, true);  // first call runs eagerly
             cudaGraph_t graph;
+            const long long l0 = g_launches.load();
             CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue(st, false);
+            int rc = search_enqueue(ctx, S, 0, n_r, st, false);
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (rc != SD_OK) return rc;
             CK(ctx, ec);
             GraphEntry ge;
+            ge.kernels = g_launches.load() - l0;
+            g_launches.fetch_sub(ge.kernels);  // counted when the graph runs
             ec = cudaGraphInstantiate(&ge.exec, graph, 0);
             cudaGraphDestroy(graph);
             CK(ctx, ec);
@@ -780,9 +944,113 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             PassTimer pt(ctx, SD_PASS_GRAPH, st, true);
             CK(ctx, cudaGraphLaunch(it->second.exec, st));
         }
+        note_launch((int)it->second.kernels);
         return SD_OK;
     }
-    return enqueue(st, true);
+    return search_enqueue(ctx, S, 0, n_r, st, true);
+}
+
+// Many jobs in one launch sequence.  Each job gets its own plan (tuned when the
+// "autotune" option is on); the workspace is reserved once for the largest.
+// The first call with a given job list runs eagerly, later calls replay one
+// captured CUDA graph that holds every job, with an event node between jobs
+// for the per-job device times.
+template <typename T>
+static int run_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats, cudaStream_t st) {
+    std::vector<Search<T>> S((size_t)n_jobs);
+    std::string k = "pairs";
+    for (int64_t j = 0; j < n_jobs; ++j) {
+        const sd_pair_job& J = jobs[j];
+        CKI(search_setup<T>(ctx, J.fixed, J.moving, J.quats, J.n_r, &J.grid, J.cand_out, 0, st, &S[j]));
+        if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) CKI(autotune<T>(ctx, &S[j], st));
+        char part[256];
+        snprintf(part, sizeof part, "|%p,%p,%p,%lld,%d,%.17g,%p,%d,%d", (const void*)J.fixed, (const void*)J.moving,
+                 (const void*)J.quats, (long long)J.n_r, J.grid.N, J.grid.L, (void*)J.cand_out, S[j].plan.B,
+                 S[j].plan.bins);
+        k += part;
+    }
+    char tail[64];
+    snprintf(tail, sizeof tail, "|%p", (void*)st);
+    k += tail;
+    size_t need[8] = {};
+    for (auto& x : S) search_need(x, need);
+    CKI(ws_reserve(ctx, need));
+    for (auto& x : S) search_bind(ctx, &x);
+
+    // events around every job: eager records, or event nodes of the graph
+    auto it = ctx->graphs.find(k);
+    const bool replay = it != ctx->graphs.end();
+    const bool capture = !replay && st != nullptr && ctx->seen[k]++ > 0;
+    std::vector<cudaEvent_t> evs;
+    if (replay) {
+        evs = it->second.events;
+    } else {
+        evs.resize((size_t)n_jobs + 1, nullptr);
+        for (auto& e : evs) CK(ctx, cudaEventCreate(&e));
+    }
+    int rc = SD_OK;
+    if (!replay) {
+        cudaGraph_t graph = nullptr;
+        const long long l0 = g_launches.load();
+        if (capture) CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int64_t j = 0; j < n_jobs && rc == SD_OK; ++j) {
+            cudaError_t e = capture ? cudaEventRecordWithFlags(evs[j], st, cudaEventRecordExternal)
+                                    : cudaEventRecord(evs[j], st);
+            if (e != cudaSuccess) rc = fail(ctx, SD_ERR_CUDA, "event record failed: %s", cudaGetErrorString(e));
+            if (rc == SD_OK) rc = search_enqueue(ctx, S[j], 0, S[j].n_r, st, !capture);
+        }
+        if (rc == SD_OK) {
+            cudaError_t e = capture ? cudaEventRecordWithFlags(evs[n_jobs], st, cudaEventRecordExternal)
+                                    : cudaEventRecord(evs[n_jobs], st);
+            if (e != cudaSuccess) rc = fail(ctx, SD_ERR_CUDA, "event record failed: %s", cudaGetErrorString(e));
+        }
+        if (capture) {
+            cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (rc == SD_OK && ec != cudaSuccess)
+                rc = fail(ctx, SD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+            GraphEntry ge;
+            if (rc == SD_OK) {
+                ec = cudaGraphInstantiate(&ge.exec, graph, 0);
+                if (ec != cudaSuccess) rc = fail(ctx, SD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ec));
+            }
+            if (graph) cudaGraphDestroy(graph);
+            ge.kernels = g_launches.load() - l0;
+            g_launches.fetch_sub(ge.kernels);  // counted when the graph runs
+            if (rc == SD_OK) {
+                ge.events = evs;
+                it = ctx->graphs.emplace(k, ge).first;
+            }
+        }
+        if (rc != SD_OK) {
+            for (auto e : evs) cudaEventDestroy(e);
+            return rc;
+        }
+    }
+    if (replay || capture) {
+        {
+            PassTimer pt(ctx, SD_PASS_GRAPH, st, true);
+            CK(ctx, cudaGraphLaunch(it->second.exec, st));
+        }
+        note_launch((int)it->second.kernels);
+    }
+    if (stats) {
+        CK(ctx, cudaEventSynchronize(evs[n_jobs]));
+        for (int64_t j = 0; j < n_jobs; ++j) {
+            float ms = NAN;
+            if (cudaEventElapsedTime(&ms, evs[j], evs[j + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                ms = NAN;
+            }
+            stats[j].ms = ms;
+            stats[j].batch = S[j].plan.B;
+            stats[j].spread_bins = S[j].plan.bins;
+            stats[j].n = S[j].G.n;
+            stats[j].s = S[j].G.s;
+        }
+    }
+    if (!replay && !capture)  // eager events are not kept (released once they complete)
+        for (auto e : evs) cudaEventDestroy(e);
+    return SD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -871,6 +1139,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
+    else if (!strcmp(key, "autotune")) ctx->opt_autotune = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
     return SD_OK;
 }
@@ -1091,6 +1360,23 @@ int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
     cudaStream_t st = (cudaStream_t)stream;
     if (ctx->p.precision == SD_F64) return run_search<double>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
     return run_search<float>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
+}
+
+int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, SD_ERR_ARG, "score_pairs: bad job list");
+    if (n_jobs == 0) return SD_OK;
+    for (int64_t j = 0; j < n_jobs; ++j) {
+        CKI(check_pair(ctx, jobs[j].fixed, jobs[j].moving));
+        if (jobs[j].n_r < 1 || jobs[j].n_r > (int64_t)INT32_MAX)
+            return fail(ctx, SD_ERR_ARG, "score_pairs: job %lld has a bad rotation count", (long long)j);
+        if (!jobs[j].quats || !jobs[j].cand_out)
+            return fail(ctx, SD_ERR_ARG, "score_pairs: job %lld has a NULL pointer", (long long)j);
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64) return run_pairs<double>(ctx, jobs, n_jobs, stats, st);
+    return run_pairs<float>(ctx, jobs, n_jobs, stats, st);
 }
 
 template <typename T>

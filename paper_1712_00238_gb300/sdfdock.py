@@ -56,6 +56,16 @@ class sd_pose(ct.Structure):
                 ("rot", ct.c_int32), ("idx", ct.c_int32), ("t", ct.c_double * 3)]
 
 
+class sd_pair_job(ct.Structure):
+    _fields_ = [("fixed", ct.c_void_p), ("moving", ct.c_void_p), ("quats", ct.c_void_p), ("n_r", ct.c_int64),
+                ("grid", sd_grid), ("cand_out", ct.c_void_p)]
+
+
+class sd_pair_stat(ct.Structure):
+    _fields_ = [("ms", ct.c_double), ("batch", ct.c_int32), ("spread_bins", ct.c_int32), ("n", ct.c_int32),
+                ("s", ct.c_int32)]
+
+
 CAND_BYTES = 16  # sd_cand: double score, int32 rot, int32 idx
 
 _LIB = None
@@ -77,6 +87,8 @@ _SIGS = {
                                       ct.POINTER(sd_grid), ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_score_maps": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64,
                                  ct.POINTER(sd_grid), ct.c_void_p, ct.c_void_p]),
+    "sd_score_pairs": (ct.c_int, [ct.c_void_p, ct.POINTER(sd_pair_job), ct.c_int64, ct.POINTER(sd_pair_stat),
+                                  ct.c_void_p]),
     "sd_top_k_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_int, ct.c_void_p,
                                   ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.POINTER(sd_pose),
                                   ct.c_void_p]),
@@ -280,6 +292,30 @@ class Context:
         self._check(self.lib.sd_score_maps(self.handle, fixed.handle, moving.handle, _ptr(quats), n_r,
                                            ct.byref(g), _ptr(out), _stream(self.device)))
         return torch.view_as_complex(out)
+
+    def score_pairs(self, jobs, outs: list | None = None, stats: bool = True):
+        """Score many (fixed, moving, quats, grid) jobs in one launch sequence (a captured
+        CUDA graph from the second call with the same job list on).  Returns the per-job
+        candidate buffers (uint8 (n_r, 16)) and, if ``stats``, per-job dicts with the
+        device time and the plan; the buffers must stay alive while the list is reused."""
+        n = len(jobs)
+        arr = (sd_pair_job * n)()
+        if outs is None:
+            outs = [torch.empty((q.shape[0], CAND_BYTES), dtype=torch.uint8, device=self.device)
+                    for _, _, q, _ in jobs]
+        for j, (fx, mv, q, grid) in enumerate(jobs):
+            self._need(q, torch.float64, "quats")
+            arr[j].fixed = fx.handle
+            arr[j].moving = mv.handle
+            arr[j].quats = _ptr(q)
+            arr[j].n_r = q.shape[0]
+            arr[j].grid = grid.c()
+            arr[j].cand_out = _ptr(outs[j])
+        st = (sd_pair_stat * n)() if stats else None
+        self._check(self.lib.sd_score_pairs(self.handle, arr, n, st, _stream(self.device)))
+        if not stats:
+            return outs, None
+        return outs, [dict(ms=x.ms, batch=x.batch, spread_bins=x.spread_bins, n=x.n, s=x.s) for x in st]
 
     def top_k_poses(self, cand: torch.Tensor, k: int, fixed: Shape = None, moving: Shape = None,
                     quats: torch.Tensor = None, grid: Grid = None, rescore_fp64: bool = True) -> list[dict]:

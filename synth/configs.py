@@ -138,12 +138,16 @@ def _sphere_shape(name, n_spheres, seed, per_sphere=40, band=2.0, density=2.0):
         from scipy.spatial import cKDTree
         tree = cKDTree(su.centers)
         kq = min(16, n_spheres)
+        # Spheres farther than band + max radius cannot decide a kept point
+        # (|d| <= band); points with none nearer get d = inf and are dropped.
+        bound = band + float(su.radii.max())
+        radii = np.append(su.radii, 0.0)
 
         def sdist(p):
-            d, i = tree.query(p, k=kq)
+            d, i = tree.query(p, k=kq, distance_upper_bound=bound, workers=-1)
             d = np.atleast_2d(d.T).T if kq == 1 else d
             i = np.atleast_2d(i.T).T if kq == 1 else i
-            return (d - su.radii[i]).min(axis=1)
+            return (d - radii[i]).min(axis=1)
     except ImportError:  # pragma: no cover - scipy is present on both machines
         def sdist(p):
             return sh.sd_sphere_union(p, su)

@@ -246,12 +246,28 @@ def self_avoiding_walk(n: int, seed: int, step=3.8, min_sep=2.8, conf_scale=3.0,
     centres stay at least ``min_sep`` apart.  After ``tries`` failed attempts
     the walk backtracks one step.  The returned centres are shifted so their
     mean is the origin.
+
+    Centres are kept in a hash grid of cells wider than step + min_sep, so a
+    trial step is compared only with the centres of the 27 cells around the
+    previous centre: every other centre is farther than min_sep from any
+    point on the step sphere, and the accepted walk is the one an all-pairs
+    comparison gives.
     """
     rng = np.random.default_rng(np.random.SeedSequence([seed, 3, n]))
     rc = conf_scale * n ** (1.0 / 3.0)
     cen = np.zeros((n, 3))
+    cell = step + min_sep + 1e-6
+    grid: dict = {}
+
+    def key(i):
+        return tuple(int(v) for v in np.floor(cen[i] / cell))
+
+    def add(i):
+        grid.setdefault(key(i), []).append(i)
+
+    add(0)
+    offsets = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
     k = 1
-    fails = np.zeros(n, dtype=np.int64)
     guard = 0
     while k < n:
         guard += 1
@@ -262,14 +278,19 @@ def self_avoiding_walk(n: int, seed: int, step=3.8, min_sep=2.8, conf_scale=3.0,
         cand = cen[k - 1] + step * d
         ok = np.linalg.norm(cand, axis=1) <= rc
         if k >= 2:
-            dd = np.linalg.norm(cand[:, None, :] - cen[None, : k - 1, :], axis=2)
-            ok &= (dd >= min_sep).all(axis=1)
+            kx, ky, kz = key(k - 1)
+            near = [i for a, b, c in offsets for i in grid.get((kx + a, ky + b, kz + c), ()) if i < k - 1]
+            if near:
+                dd = np.linalg.norm(cand[:, None, :] - cen[None, near, :], axis=2)
+                ok &= (dd >= min_sep).all(axis=1)
         idx = np.flatnonzero(ok)
         if len(idx):
             cen[k] = cand[idx[0]]
+            add(k)
             k += 1
         else:
-            fails[k] += 1
+            if k >= 2:
+                grid[key(k - 1)].remove(k - 1)
             k = max(1, k - 1)
     return cen - cen.mean(0)
 
@@ -290,7 +311,10 @@ def sphere_union_boundary(su: SphereUnion, density=2.0, seed=2) -> Boundary:
     """Samples at ``density`` points per unit area on each sphere, radial normals.
 
     Samples buried inside another sphere are dropped, so what is left samples the
-    union's surface; each keeps the area share of its own sphere.
+    union's surface; each keeps the area share of its own sphere.  Only spheres
+    whose centre lies within the largest radius of a sample can bury it; a k-d
+    tree finds them (centres are at least 2.8 apart, so a few neighbours cover
+    every such sphere), and the test itself is the exact distance comparison.
     """
     rng = np.random.default_rng(np.random.SeedSequence([seed, 5, len(su.radii)]))
     pos, nrm, area = [], [], []
@@ -306,10 +330,29 @@ def sphere_union_boundary(su: SphereUnion, density=2.0, seed=2) -> Boundary:
     nrm = np.vstack(nrm)
     area = np.concatenate(area)
     keep = np.ones(len(pos), bool)
-    # buried test in chunks
-    for s in range(0, len(pos), 4096):
-        d = np.linalg.norm(pos[s:s + 4096, None, :] - su.centers[None], axis=2) - su.radii[None]
-        keep[s:s + 4096] = (d >= -1e-6).all(axis=1)
+    rmax = float(su.radii.max())
+    ns = len(su.radii)
+    try:
+        from scipy.spatial import cKDTree
+    except ImportError:  # pragma: no cover - scipy is present on both machines
+        cKDTree = None
+    if cKDTree is not None and ns > 16:
+        tree = cKDTree(su.centers)
+        _, nb = tree.query(pos, k=16, distance_upper_bound=rmax * (1 + 1e-9) + 1e-9)
+        # a full row of 16 neighbours would mean more may exist: fall back for those
+        full = nb[:, -1] < ns
+        for s in range(0, len(pos), 65536):
+            sl = slice(s, s + 65536)
+            j = np.where(nb[sl] < ns, nb[sl], 0)
+            d = np.linalg.norm(pos[sl, None, :] - su.centers[j], axis=2) - su.radii[j]
+            keep[sl] = np.where(nb[sl] < ns, d >= -1e-6, True).all(axis=1)
+        for i in np.flatnonzero(full):
+            d = np.linalg.norm(pos[i, None, :] - su.centers, axis=1) - su.radii
+            keep[i] = (d >= -1e-6).all()
+    else:
+        for s in range(0, len(pos), 4096):
+            d = np.linalg.norm(pos[s:s + 4096, None, :] - su.centers[None], axis=2) - su.radii[None]
+            keep[s:s + 4096] = (d >= -1e-6).all(axis=1)
     return Boundary(pos[keep], nrm[keep], area[keep])
 
 
