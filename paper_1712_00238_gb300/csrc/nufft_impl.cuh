@@ -55,6 +55,18 @@ __host__ __device__ constexpr int cta_threads() {
     return most < 64 ? 64 : (most > 384 ? 256 : most);
 }
 
+// Resident CTAs per SM that a pass's register allocation is bounded for, 0 for
+// the compiler's own choice.  The 384-point FP32 passes (384 threads) take 3
+// (at most 56 registers a thread; 66-70 otherwise, which allows two); the
+// 512-point FP32 passes take 2 (at most 128; 150-170 otherwise, one CTA).  Every
+// other pass keeps the compiler's choice, which already allows four or more
+// CTAs of 256 threads: an explicit minimum there makes it take more registers
+// than it needs.
+template <typename T, int LEN>
+__host__ __device__ constexpr int min_ctas_per_sm() {
+    return sizeof(T) != 4 ? 0 : (LEN == 384 ? 3 : (LEN == 512 ? 2 : 0));
+}
+
 // ---------------------------------------------------------------------------
 // spreading
 // ---------------------------------------------------------------------------
@@ -390,7 +402,7 @@ __device__ __forceinline__ void block_argmax(T& best, int& bidx) {
 
 // Row passes: TR consecutive rows of one rotation per CTA.
 template <typename T, int LEN, int MODE>
-__global__ void __launch_bounds__(cta_threads<T, LEN>(), cta_threads<T, LEN>() == 384 ? 3 : 1) k_rows(RowArgs<T> a) {
+__device__ __forceinline__ void rows_body(const RowArgs<T>& a) {
     using C = cplx<T>;
     constexpr int TR = lines_per_cta<T, LEN>();
     constexpr int LD = line_pitch(LEN);
@@ -447,9 +459,19 @@ __global__ void __launch_bounds__(cta_threads<T, LEN>(), cta_threads<T, LEN>() =
     }
 }
 
+template <typename T, int LEN, int MODE>
+__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows(RowArgs<T> a) {
+    rows_body<T, LEN, MODE>(a);
+}
+
+template <typename T, int LEN, int MODE, int MB>
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), MB) k_rows_mb(RowArgs<T> a) {
+    rows_body<T, LEN, MODE>(a);
+}
+
 // Column passes: TC adjacent columns of one (rotation, outer) slab per CTA.
 template <typename T, int LENF, int LENI, int MODE>
-__global__ void __launch_bounds__(cta_threads<T, LENF>(), cta_threads<T, LENF>() == 384 ? 3 : 1) k_cols(ColArgs<T> a) {
+__device__ __forceinline__ void cols_body(const ColArgs<T>& a) {
     using C = cplx<T>;
     constexpr int TC = lines_per_cta<T, LENF>();
     constexpr int NT = cta_threads<T, LENF>();
@@ -519,6 +541,16 @@ __global__ void __launch_bounds__(cta_threads<T, LENF>(), cta_threads<T, LENF>()
     }
 }
 
+template <typename T, int LENF, int LENI, int MODE>
+__global__ void __launch_bounds__(cta_threads<T, LENF>()) k_cols(ColArgs<T> a) {
+    cols_body<T, LENF, LENI, MODE>(a);
+}
+
+template <typename T, int LENF, int LENI, int MODE, int MB>
+__global__ void __launch_bounds__(cta_threads<T, LENF>(), MB) k_cols_mb(ColArgs<T> a) {
+    cols_body<T, LENF, LENI, MODE>(a);
+}
+
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
@@ -550,7 +582,9 @@ static cudaError_t rows_impl(const RowArgs<T>& a, int batch, int* nparts, cudaSt
     if (nparts) *nparts = nb;
     if (nb == 0 || batch == 0) return cudaSuccess;
     const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
-    auto kern = k_rows<T, LEN, MODE>;
+    void (*kern)(RowArgs<T>);
+    if constexpr (min_ctas_per_sm<T, LEN>() > 0) kern = k_rows_mb<T, LEN, MODE, min_ctas_per_sm<T, LEN>()>;
+    else kern = k_rows<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(nb, batch), cta_threads<T, LEN>(), smem, st>>>(a);
@@ -565,7 +599,9 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     const int nb = (a.ncols + TC - 1) / TC;
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
     const size_t smem = (size_t)(TC * line_pitch(LENF) + tw_count(LENF) + tw_count(LENI)) * sizeof(C);
-    auto kern = k_cols<T, LENF, LENI, MODE>;
+    void (*kern)(ColArgs<T>);
+    if constexpr (min_ctas_per_sm<T, LENF>() > 0) kern = k_cols_mb<T, LENF, LENI, MODE, min_ctas_per_sm<T, LENF>()>;
+    else kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LENF>(), smem, st>>>(a);
