@@ -681,8 +681,9 @@ def refine_cpu_baseline(w, q0, t0, n1=4000, n2=1000):
     dt = time.perf_counter() - t
     scale = (w.fixed.query.m * w.moving.query.m) / (n1 * n2)
     return {"value": 1.0 / (dt * scale), "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one pose: FP64 pair sums of the band-limited kernel and its gradient over a seeded "
-                      f"{n1} x {n2} subset of the SDF samples, time scaled by the full pair count"}
+            "sample": f"one pose: the oracle's direct FP64 pair sums of the band-limited kernel and its "
+                      f"gradient (no grid) over a seeded {n1} x {n2} subset of the SDF samples, time scaled "
+                      f"by the full pair count"}
 
 
 def main():
