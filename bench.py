@@ -52,7 +52,10 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0, help="rotations per batch (0: automatic)")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
-    ap.add_argument("--spread-direct", type=int, default=1, help="1: global vector atomics; 0: spread by bins")
+    ap.add_argument("--spread-direct", type=int, default=1,
+                    help="with --autotune 0: 1 global vector atomics, 0 spread by bins")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: the library times candidate plans (batch, spreading) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--workload", choices=["peg_in_bore_3d", "docking_2000_500", "refine_256", "uneven_batch"],
                     default="peg_in_bore_3d")
@@ -219,7 +222,9 @@ def run_ours(args):
     ctx.set_option("plain", args.plain)
     ctx.set_option("graph", 0 if args.plain else args.graph)
     ctx.set_option("spread_direct", args.spread_direct)
+    ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
+    plan_used = {}
     host = host_inputs(w, torch)
     devin = {k: v.to(dev) for k, v in host.items()}
     n_rot = w.n_rot
@@ -241,6 +246,7 @@ def run_ours(args):
         e1 = mark()
         ctx.score_rotations(fx, mv, inp["quats"], grid, out=cand)
         e2 = mark()
+        plan_used.update(ctx.search_plan(mv, grid, n_rot))
         poses = ctx.top_k_poses(cand, top_k, fx, mv, inp["quats"], grid, rescore_fp64=True)
         e3 = mark()
         poses = poses[:TOP_K]
@@ -346,7 +352,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "peak_source": src,
                     "algorithmic_bytes_per_launch": int(per_launch),
-                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, s, w.N)),
+                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, s, w.N, plan_used.get("batch"))),
                     "avg_launch_us": round(avg_s * 1e6, 2)}
     search_ms = None
     if passes:
@@ -358,8 +364,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload],
                    "rotations": n_rot, "translations": w.N ** 3, "sub_box": s,
-                   "batch": args.batch, "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": "global vector atomics" if args.spread_direct else "binned shared-memory tiles",
+                   "batch": plan_used.get("batch"), "autotune": bool(args.autotune),
+                   "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
+                   "spread": "binned shared-memory tiles" if plan_used.get("spread_bins") else "global vector atomics",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -383,13 +390,13 @@ def run_ours(args):
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# search passes from one ncu capture of a 34-rotation launch of this workload
-# (the bench's own launches also hold 34 rotations), keyed by (pass, sub-box side,
-# N); absent entries report null.
+# search passes from one ncu capture of a 34-rotation launch of this workload,
+# keyed by (pass, sub-box side, N, rotations per launch); a launch of another
+# shape reports null.
 TRAFFIC_PER_LAUNCH: dict = {
-    ("fused", 108, 128): 553426688 + 531017984,
-    ("fwd_y", 108, 128): 406161920 + 432556032,
-    ("inv_y", 108, 128): 570464768 + 510324480,
+    ("fused", 108, 128, 34): 553426688 + 531017984,
+    ("fwd_y", 108, 128, 34): 406161920 + 432556032,
+    ("inv_y", 108, 128, 34): 570464768 + 510324480,
 }
 
 

@@ -216,6 +216,13 @@ typedef struct sd_pair_stat {
 int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats,
                    void* stream);
 
+/* The plan a search of n_r rotations of `moving` on grid g would run with now:
+ * rotations per batch and 1 for binned spreading (0: direct).  With the
+ * "autotune" option it is the cached choice for this geometry if there is one
+ * (the first search of a geometry makes it), else the default.  No device work. */
+int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
+                   int32_t* spread_bins);
+
 /* Global top-k over per-rotation candidates, ordered by score descending,
  * then rotation ascending, then translation index ascending; optionally each
  * pose is re-scored in FP64 by direct pair sums of the continuous score

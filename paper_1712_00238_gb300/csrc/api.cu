@@ -480,7 +480,8 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* 
     return SD_OK;
 }
 
-static bool bins_supported(int w) { return w >= 4 && w <= 7; }
+// Binned spreading exists for FP32 and kernel widths 4-7 (tiles of 8 + w - 1 cells).
+static bool bins_supported(const sd_ctx* ctx) { return ctx->p.precision == SD_F32 && ctx->p.w >= 4 && ctx->p.w <= 7; }
 
 // ---------------------------------------------------------------------------
 // fixed-shape preparation for a grid
@@ -526,7 +527,7 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
     sa.out_rot_stride = 0;
     sa.n_full = G.n;
     CK(ctx, cudaMemsetAsync(b0, 0, sz0 * sizeof(C), st));
-    if (ctx->opt_spread_direct || !bins_supported(ctx->p.w)) {
+    if (ctx->opt_spread_direct || !bins_supported(ctx)) {
         CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
     } else {
         BinArgs bn;
@@ -701,7 +702,7 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     S->out = out;
     S->maps = maps;
     S->plan.B = choose_batch<T>(ctx, S->G, n_r);
-    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx->p.w)) ? 1 : 0;
+    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? 1 : 0;
     per_rot_elems<T>(S->G, &S->e0, &S->e1);
     S->rows_last = (S->G.dim == 2) ? S->G.N : (int64_t)S->G.N * S->G.N;
     S->Nd = (S->G.dim == 2) ? (int64_t)S->G.N * S->G.N : (int64_t)S->G.N * S->G.N * S->G.N;
@@ -857,7 +858,7 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     std::vector<Plan> cand;
     for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
         if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
-        for (int bins = 0; bins <= (bins_supported(ctx->p.w) ? 1 : 0); ++bins) {
+        for (int bins = 0; bins <= (bins_supported(ctx) ? 1 : 0); ++bins) {
             bool dup = false;
             for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
             if (!dup) cand.push_back(Plan{B, bins});
@@ -1360,6 +1361,34 @@ int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
     cudaStream_t st = (cudaStream_t)stream;
     if (ctx->p.precision == SD_F64) return run_search<double>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
     return run_search<float>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
+}
+
+int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
+                   int32_t* spread_bins) {
+    if (!ctx) return SD_ERR_ARG;
+    if (!moving || moving->ctx != ctx) return fail(ctx, SD_ERR_ARG, "search_plan: bad moving shape");
+    if (n_r < 1) return fail(ctx, SD_ERR_ARG, "search_plan: bad rotation count");
+    auto plan = [&](auto tag) -> int {
+        using T = decltype(tag);
+        Search<T> S;
+        CKI(make_geo(ctx, g, moving->radius, &S.G));
+        S.moving = moving;
+        S.n_r = n_r;
+        S.plan.B = choose_batch<T>(ctx, S.G, n_r);
+        S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? 1 : 0;
+        if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) {
+            auto it = ctx->tuned.find(plan_key(ctx, S));
+            if (it != ctx->tuned.end()) {
+                S.plan.B = (int)std::min<int64_t>(it->second.B, n_r);
+                S.plan.bins = it->second.bins;
+            }
+        }
+        if (batch) *batch = S.plan.B;
+        if (spread_bins) *spread_bins = S.plan.bins;
+        return SD_OK;
+    };
+    if (ctx->p.precision == SD_F64) return plan(double{});
+    return plan(float{});
 }
 
 int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats, void* stream) {

@@ -301,58 +301,147 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
     bn.sorted[(int64_t)b * m + pos] = (int32_t)j;
 }
 
-// One CTA per bin: its samples' taps all fall in the bin grown by W - 1 cells,
-// accumulated in shared memory (every sample once, taps unrolled), then added to
-// the sub-box with one vector atomic per non-zero cell.
-template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<T> a, BinArgs bn) {
-    using C = cplx<T>;
+// One CTA per (bin, rotation): the taps of the bin's samples all fall in the
+// bin grown by W - 1 cells, a PS^d tile (PS = 8 + W - 1) accumulated in shared
+// memory, then added to the sub-box with one 16-byte atomic per pair of
+// x-adjacent tile cells that is not zero.
+//
+// Accumulation is warp-cooperative: the CTA stages up to 256 of the bin's
+// samples (kernel weights, weight value, tap-box offset in the tile; one per
+// thread) in shared memory, then its warps take the staged samples round-robin
+// and add each with the lanes on consecutive taps, so the shared atomics of one
+// instruction hit distinct cells (for the 13-cell pitch of W = 6, at most two
+// lanes share a bank) and a bin of a few dozen samples still keeps every warp
+// busy.  A sample whose tap box does not
+// lie in the tile (not possible when the counting pass and this one agree, as
+// they evaluate the same function) is added with global atomics instead.
+template <int D, int W>
+__global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
     constexpr int PS = SPREAD_BIN + W - 1;
-    constexpr int CELLS = (D == 3) ? PS * PS * PS : PS * PS;
-    __shared__ T tile[2 * CELLS];
-    __shared__ T Rm[9];
+    constexpr int PS2 = PS * PS;
+    constexpr int CELLS = (D == 3) ? PS2 * PS : PS2;
+    constexpr int TAPS = (D == 3) ? W * W * W : W * W;
+    constexpr int ROUNDS = (TAPS + 31) / 32;
+    constexpr int REC = D * W + 4;  // D*W weights, c.x, c.y, tile offset (-1: outside), packed origin
+    constexpr int NWARP = 8;
+    __shared__ float tre[CELLS];
+    __shared__ float tim[CELLS];
+    __shared__ float stage[NWARP * 32 * REC];
+    __shared__ float Rm[9];
     const int b = blockIdx.y;
     const int t = blockIdx.x;
     const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
     const int lo = off[t], hi = off[t + 1];
     if (lo == hi) return;  // empty bin (uniform over the block)
-    for (int i = threadIdx.x; i < 2 * CELLS; i += blockDim.x) tile[i] = T(0);
+    for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
+        tre[i] = 0.f;
+        tim[i] = 0.f;
+    }
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
     __syncthreads();
     const int nb = bn.nb, s = a.s;
     const int org0[3] = {(t % nb) * SPREAD_BIN, ((t / nb) % nb) * SPREAD_BIN,
                          (D == 3) ? (t / (nb * nb)) * SPREAD_BIN : 0};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this lane's tap in each round: tile offset (10 bits) and kx, ky, kz (4 bits each)
+    int tap_of[ROUNDS];
+#pragma unroll
+    for (int q = 0; q < ROUNDS; ++q) {
+        const int tap = min(q * 32 + lane, TAPS - 1);
+        const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
+        tap_of[q] = (kx + PS * ky + PS2 * kz) | (kx << 12) | (ky << 16) | (kz << 20);
+    }
+    float2* out = a.out + (int64_t)b * a.out_rot_stride;
     const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-        int org[D];
-        T wt[D][W];
-        C c;
-        sample_taps<T, D, W>(a, Rm, sorted[p], org, wt, c);
-        const int lx = org[0] - org0[0], ly = org[1] - org0[1], lz = (D == 3) ? org[2] - org0[2] : 0;
+    constexpr int CHUNK = NWARP * 32;
+    for (int p0 = lo; p0 < hi; p0 += CHUNK) {
+        // every thread stages one sample of the chunk ...
+        const int nj = min(CHUNK, hi - p0);
+        if ((int)threadIdx.x < nj) {
+            int org[D];
+            float wt[D][W];
+            float2 c;
+            sample_taps<float, D, W>(a, Rm, sorted[p0 + threadIdx.x], org, wt, c);
+            bool inside = true;
+            int base = 0, mul = 1, packed = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const int l = org[d] - org0[d];
+                inside &= (l >= 0 && l < SPREAD_BIN);
+                base += l * mul;
+                mul *= PS;
+                packed |= org[d] << (10 * d);
+            }
+            float* r = stage + threadIdx.x * REC;
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+#pragma unroll
+                for (int k = 0; k < W; ++k) r[d * W + k] = wt[d][k];
+            r[D * W] = c.x;
+            r[D * W + 1] = c.y;
+            r[D * W + 2] = __int_as_float(inside ? base : -1);
+            r[D * W + 3] = __int_as_float(packed);
+        }
+        __syncthreads();
+        // ... and the warps add the staged samples round-robin, one at a time
+        for (int j = warp; j < nj; j += NWARP) {
+            const float* r = stage + j * REC;
+            const float cx = r[D * W], cy = r[D * W + 1];
+            const int base = __float_as_int(r[D * W + 2]);
+            if (base >= 0) {  // uniform over the warp
+#pragma unroll
+                for (int q = 0; q < ROUNDS; ++q) {
+                    if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
+                        const int tp = tap_of[q];
+                        float w = r[(tp >> 12) & 15] * r[W + ((tp >> 16) & 15)];
+                        if (D == 3) w *= r[2 * W + ((tp >> 20) & 15)];
+                        const int cell = base + (tp & 4095);
+                        atomicAdd(tre + cell, cx * w);
+                        atomicAdd(tim + cell, cy * w);
+                    }
+                }
+            } else {  // safety net (a tap box outside the tile): global atomics on the sub-box
+                const int packed = __float_as_int(r[D * W + 3]);
 #pragma unroll 1
-        for (int kz = 0; kz < (D == 3 ? W : 1); ++kz) {
-            const C cz = (D == 3) ? cscale(c, wt[D == 3 ? 2 : 0][kz]) : c;
-#pragma unroll
-            for (int ky = 0; ky < W; ++ky) {
-                const C cy = cscale(cz, wt[1][ky]);
-                T* row = tile + 2 * (((lz + kz) * PS + (ly + ky)) * PS + lx);
-#pragma unroll
-                for (int kx = 0; kx < W; ++kx) {
-                    atomicAdd(row + 2 * kx, cy.x * wt[0][kx]);
-                    atomicAdd(row + 2 * kx + 1, cy.y * wt[0][kx]);
+                for (int q = 0; q < ROUNDS; ++q) {
+                    if (q * 32 + lane < TAPS) {
+                        const int tp = tap_of[q];
+                        const int kx = (tp >> 12) & 15, ky = (tp >> 16) & 15, kz = (tp >> 20) & 15;
+                        float w = r[kx] * r[W + ky];
+                        int64_t o = (int64_t)wrap_index(((packed >> 10) & 1023) + ky, s) * s +
+                                    wrap_index((packed & 1023) + kx, s);
+                        if (D == 3) {
+                            w *= r[2 * W + kz];
+                            o += (int64_t)wrap_index(((packed >> 20) & 1023) + kz, s) * s * s;
+                        }
+                        atomic_cadd(out + o, make_float2(cx * w, cy * w));
+                    }
                 }
             }
         }
+        __syncthreads();  // the stage is refilled by the next chunk
     }
     __syncthreads();
-    C* out = a.out + (int64_t)b * a.out_rot_stride;
-    for (int li = threadIdx.x; li < CELLS; li += blockDim.x) {
-        const C v = mk(tile[2 * li], tile[2 * li + 1]);
-        if (v.x == T(0) && v.y == T(0)) continue;
-        const int x = li % PS, y = (li / PS) % PS, z = li / (PS * PS);
-        int64_t o = (int64_t)wrap_index(org0[1] + y, s) * s + wrap_index(org0[0] + x, s);
+    // flush: pairs of x-adjacent tile cells (global x even: bins start at multiples of 8)
+    constexpr int XP = (PS + 1) / 2;
+    constexpr int PAIRS = (D == 3) ? XP * PS2 : XP * PS;
+    for (int i = threadIdx.x; i < PAIRS; i += blockDim.x) {
+        const int xp = i % XP, row = i / XP;  // row = y + PS z
+        const int x = 2 * xp;
+        const int li = row * PS + x;
+        const float2 v0 = make_float2(tre[li], tim[li]);
+        const float2 v1 = (x + 1 < PS) ? make_float2(tre[li + 1], tim[li + 1]) : make_float2(0.f, 0.f);
+        if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
+        const int y = row % PS, z = row / PS;
+        int64_t o = (int64_t)wrap_index(org0[1] + y, s) * s;
         if (D == 3) o += (int64_t)wrap_index(org0[2] + z, s) * s * s;
-        atomic_cadd(out + o, v);
+        const int gx = org0[0] + x;
+        if (gx + 1 < s) {
+            add_pair(out + o + gx, v0, v1);
+        } else {
+            atomic_cadd(out + o + wrap_index(gx, s), v0);
+            if (x + 1 < PS) atomic_cadd(out + o + wrap_index(gx + 1, s), v1);
+        }
     }
 }
 
@@ -675,6 +764,9 @@ cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStre
 template <typename T>
 cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
+    if constexpr (sizeof(T) != 4) {
+        return launch_spread_t<T>(a, dim, batch, st);  // binned spreading is FP32 only
+    } else {
     cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
     if (e != cudaSuccess) return e;
     const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
@@ -691,8 +783,8 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
             k_bin_scan<<<batch, 1024, 0, st>>>(bn);                                \
             note_launch();                                                        \
         }                                                                         \
-        if (dim == 2) k_spread_tiles<T, 2, WW><<<gtiles, 256, 0, st>>>(a, bn);     \
-        else k_spread_tiles<T, 3, WW><<<gtiles, 256, 0, st>>>(a, bn);              \
+        if (dim == 2) k_spread_tiles<2, WW><<<gtiles, 256, 0, st>>>(a, bn);        \
+        else k_spread_tiles<3, WW><<<gtiles, 256, 0, st>>>(a, bn);                 \
         note_launch();                                                            \
         return cudaGetLastError();
     switch (a.w) {
@@ -700,6 +792,7 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
     }
 #undef SD_BIN_CASE
     return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------------------

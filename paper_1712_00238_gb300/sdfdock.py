@@ -89,6 +89,8 @@ _SIGS = {
                                  ct.POINTER(sd_grid), ct.c_void_p, ct.c_void_p]),
     "sd_score_pairs": (ct.c_int, [ct.c_void_p, ct.POINTER(sd_pair_job), ct.c_int64, ct.POINTER(sd_pair_stat),
                                   ct.c_void_p]),
+    "sd_search_plan": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_int64,
+                                  ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
     "sd_top_k_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_int, ct.c_void_p,
                                   ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.POINTER(sd_pose),
                                   ct.c_void_p]),
@@ -292,6 +294,14 @@ class Context:
         self._check(self.lib.sd_score_maps(self.handle, fixed.handle, moving.handle, _ptr(quats), n_r,
                                            ct.byref(g), _ptr(out), _stream(self.device)))
         return torch.view_as_complex(out)
+
+    def search_plan(self, moving: Shape, grid: Grid, n_r: int) -> dict:
+        """The plan a search would use now: rotations per batch and binned (1) or direct spreading."""
+        b, s = ct.c_int32(), ct.c_int32()
+        g = grid.c()
+        self._check(self.lib.sd_search_plan(self.handle, moving.handle, ct.byref(g), n_r, ct.byref(b),
+                                            ct.byref(s)))
+        return {"batch": b.value, "spread_bins": s.value}
 
     def score_pairs(self, jobs, outs: list | None = None, stats: bool = True):
         """Score many (fixed, moving, quats, grid) jobs in one launch sequence (a captured

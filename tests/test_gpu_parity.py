@@ -124,6 +124,34 @@ def test_maps_match_oracle_all_rotations(name, prec, N):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,N,swap", [("tiny_2d", 48, False), ("tiny_3d", 16, False), ("tiny_3d", 32, False),
+                                         ("tiny_3d", 8, True)])
+def test_binned_spreading_matches_oracle(name, N, swap):
+    # spread by 8^d-cell bins with warp-cooperative shared-memory tiles; with the
+    # block as the moving shape on the 8^3 grid the sub-box is the whole periodic
+    # 16^3 grid, so tiles wrap around its faces
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    if swap:
+        p1, c1, p2, c2 = p2, c2, p1, c1
+    ctx = make_ctx(w, "f32")
+    ctx.set_option("spread_direct", 0)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], ref[r]) < TOL["f32"], r
+    s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g)))
+    for r in range(w.n_rot):
+        assert abs(s[r] - maps[r].real.max()) <= 1e-6 * np.abs(maps[r].real).max()
+        if top1_margin_ok(ref[r].real):
+            assert idx[r] == int(np.argmax(ref[r].real))
+    ctx.close()
+
+
 def test_maps_full_size_peg_in_bore():
     # 128^3 translations, n = 256 oversampled grid, ~50,000 samples per shape;
     # weights are seeded synthetic values shared by both sides.
@@ -376,13 +404,15 @@ def test_maps_docking_grids(N, L, n1, n2):
     quats = rotations.super_fibonacci(40)[[3, 17]]
     q = quats_dev(quats)
     g = sd.Grid(N, L)
-    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
     ref = oracle_maps(p1, c1, p2, c2, quats, N, L, sg)
-    cand = sd.decode_cands(ctx.score_rotations(fx, mv, q, g))
-    for r in range(len(quats)):
-        assert rel_err(maps[r], ref[r]) < 1e-4
-        if top1_margin_ok(ref[r].real):
-            assert cand[2][r].item() == int(np.argmax(ref[r].real))
+    for direct in (1, 0):  # global vector atomics, then binned shared-memory tiles
+        ctx.set_option("spread_direct", direct)
+        maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+        cand = sd.decode_cands(ctx.score_rotations(fx, mv, q, g))
+        for r in range(len(quats)):
+            assert rel_err(maps[r], ref[r]) < 1e-4, (direct, r)
+            if top1_margin_ok(ref[r].real):
+                assert cand[2][r].item() == int(np.argmax(ref[r].real)), (direct, r)
     ctx.close()
 
 
