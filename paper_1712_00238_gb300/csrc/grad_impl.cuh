@@ -23,6 +23,23 @@ __device__ __forceinline__ int wrap_n(int a, int n) {
     return a < 0 ? a + n : a;
 }
 
+// The four fields of cell i (Phi, d/dx, d/dy, d/dz Phi; 32 bytes for FP32, at a
+// 32-byte aligned address) as two 16-byte read-only loads; FP64 cells load
+// field by field.
+__device__ __forceinline__ void load_cell(const cplx<float>* G, int64_t i, cplx<float> f[4]) {
+    const float4* p = reinterpret_cast<const float4*>(G + 4 * i);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    f[0] = mk(a.x, a.y);
+    f[1] = mk(a.z, a.w);
+    f[2] = mk(b.x, b.y);
+    f[3] = mk(b.z, b.w);
+}
+__device__ __forceinline__ void load_cell(const cplx<double>* G, int64_t i, cplx<double> f[4]) {
+    const cplx<double>* p = G + 4 * i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[k] = p[k];
+}
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
     using C = cplx<T>;
@@ -80,10 +97,11 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
 #pragma unroll
                 for (int kx = 0; kx < W; ++kx) {
                     const T wgt = wt[1][ky] * wt[0][kx];
-                    const C* cell = a.G + 4 * (rb + ix[0][kx]);
-                    phi = cadd(phi, cscale(cell[0], wgt));
-                    g0 = cadd(g0, cscale(cell[1], wgt));
-                    g1 = cadd(g1, cscale(cell[2], wgt));
+                    C f[4];
+                    load_cell(a.G, rb + ix[0][kx], f);
+                    phi = cadd(phi, cscale(f[0], wgt));
+                    g0 = cadd(g0, cscale(f[1], wgt));
+                    g1 = cadd(g1, cscale(f[2], wgt));
                 }
             }
         } else {
@@ -102,11 +120,12 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
 #pragma unroll
                     for (int kx = 0; kx < W; ++kx) {
                         const T wgt = wzy * wt[0][kx];
-                        const C* cell = a.G + 4 * (rb + ix[0][kx]);
-                        phi = cadd(phi, cscale(cell[0], wgt));
-                        g0 = cadd(g0, cscale(cell[1], wgt));
-                        g1 = cadd(g1, cscale(cell[2], wgt));
-                        g2 = cadd(g2, cscale(cell[3], wgt));
+                        C f[4];
+                        load_cell(a.G, rb + ix[0][kx], f);
+                        phi = cadd(phi, cscale(f[0], wgt));
+                        g0 = cadd(g0, cscale(f[1], wgt));
+                        g1 = cadd(g1, cscale(f[2], wgt));
+                        g2 = cadd(g2, cscale(f[3], wgt));
                     }
                 }
             }
