@@ -23,28 +23,52 @@ __device__ __forceinline__ int wrap_n(int a, int n) {
     return a < 0 ? a + n : a;
 }
 
-// The four fields of cell i (Phi, d/dx, d/dy, d/dz Phi; 32 bytes for FP32, at a
-// 32-byte aligned address) as two 16-byte read-only loads; FP64 cells load
-// field by field.
-__device__ __forceinline__ void load_cell(const cplx<float>* G, int64_t i, cplx<float> f[4]) {
-    const float4* p = reinterpret_cast<const float4*>(G + 4 * i);
-    const float4 a = __ldg(p), b = __ldg(p + 1);
+// The fields of cell i, stored as two planes of cells: plane 0 holds (Phi,
+// dPhi/dx), plane 1 (dPhi/dy, dPhi/dz) -- 16 bytes per cell and plane for FP32,
+// read with one 16-byte read-only load each.
+__device__ __forceinline__ void load_cell(const cplx<float>* G, int64_t cells, int64_t i, cplx<float> f[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(G) + i);
+    const float4 b = __ldg(reinterpret_cast<const float4*>(G + 2 * cells) + i);
     f[0] = mk(a.x, a.y);
     f[1] = mk(a.z, a.w);
     f[2] = mk(b.x, b.y);
     f[3] = mk(b.z, b.w);
 }
-__device__ __forceinline__ void load_cell(const cplx<double>* G, int64_t i, cplx<double> f[4]) {
-    const cplx<double>* p = G + 4 * i;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) f[k] = p[k];
+__device__ __forceinline__ void load_cell(const cplx<double>* G, int64_t cells, int64_t i, cplx<double> f[4]) {
+    f[0] = G[2 * i];
+    f[1] = G[2 * i + 1];
+    f[2] = G[2 * cells + 2 * i];
+    f[3] = G[2 * cells + 2 * i + 1];
+}
+
+// One CTA per (pose, chunk of CHUNK samples).  Each thread stages one sample
+// (kernel weights, weight value, rotated position, tap-box origin); the warps
+// then take the staged samples round-robin and gather each with their lanes on
+// consecutive taps, so a load instruction reads a few rows of adjacent cells
+// instead of one cell per sample.  A lane keeps, per sample, the weighted sums
+// of the four fields over its taps, applies c and the torque arm R p2 to them,
+// and accumulates score, force and torque over its samples; lanes and warps are
+// summed in FP64 and added to the pose's accumulators.
+// Samples per CTA: as many as fit a 40 KiB stage, at most one per thread.
+template <typename T, int D, int W>
+__host__ __device__ constexpr int gather_chunk() {
+    constexpr int rec = D * W + 7;
+    constexpr int fit = (40 * 1024) / (rec * (int)sizeof(T)) / 32 * 32;
+    return fit < GA_THREADS ? fit : GA_THREADS;
 }
 
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
     using C = cplx<T>;
+    constexpr int TAPS = (D == 3) ? W * W * W : W * W;
+    constexpr int ROUNDS = (TAPS + 31) / 32;
+    constexpr bool TABLE = ROUNDS <= 8;  // per-lane tap table in registers (else derived per round)
+    constexpr int CHUNK = gather_chunk<T, D, W>();
+    constexpr int NWARP = GA_THREADS / 32;
+    constexpr int REC = D * W + 7;  // weights, c (2), R p2 (3), origin cell, packed wrapped origin (-1: no wrap)
+    __shared__ T stage[CHUNK * REC];
     __shared__ T Rm[9], tv[3];
-    __shared__ double red[GA_THREADS / 32][7];
+    __shared__ double red[NWARP][7];
     const int pose = blockIdx.y;
     if (threadIdx.x == 0) {
         const T* q = a.quats + 4 * (int64_t)pose;
@@ -60,9 +84,13 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         tv[2] = (D == 3) ? t[2] : T(0);
     }
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    if (j < a.m2) {
+    const int n = a.n;
+    const int64_t cells = (D == 3) ? (int64_t)n * n * n : (int64_t)n * n;
+    const int64_t j0 = (int64_t)blockIdx.x * CHUNK;
+    const int nj = (int)((a.m2 - j0) < (int64_t)CHUNK ? (a.m2 - j0) : (int64_t)CHUNK);
+    // stage: one sample per thread
+    if ((int)threadIdx.x < nj) {
+        const int64_t j = j0 + threadIdx.x;
         const vec4<T> p = a.p2[j];
         const C c = a.c2[j];
         const T pz = (D == 3) ? p.z : T(0);
@@ -70,76 +98,108 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         rp[0] = Rm[0] * p.x + Rm[1] * p.y + Rm[2] * pz;
         rp[1] = Rm[3] * p.x + Rm[4] * p.y + Rm[5] * pz;
         rp[2] = (D == 3) ? Rm[6] * p.x + Rm[7] * p.y + Rm[8] * pz : T(0);
-        // x and y weights and indices in registers (their loops are unrolled); the
-        // z loop stays rolled and evaluates its weight per iteration, so no array
-        // is indexed at run time
-        T wt[2][W];
-        int ix[2][W];
+        T* r = stage + threadIdx.x * REC;
         const T half = T(W) * T(0.5), inv_half = T(2) / T(W);
+        bool wraps = false;
+        int64_t base = 0, mul = 1;
+        int packed = 0;
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
+        for (int d = 0; d < D; ++d) {
             const T g = (rp[d] + tv[d]) * a.inv_h;
             const int u0 = (int)ceil(g - half);
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 const T zz = (T(u0 + k) - g) * inv_half;
                 const T z2 = zz * zz;
-                wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
-                ix[d][k] = wrap_n(u0 + k, a.n);
+                r[d * W + k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+            }
+            wraps |= (u0 < 0 || u0 + W > n);
+            const int uw = wrap_n(u0, n);
+            base += uw * mul;
+            mul *= n;
+            packed |= uw << (10 * d);
+        }
+        r[D * W] = c.x;
+        r[D * W + 1] = c.y;
+        r[D * W + 2] = rp[0];
+        r[D * W + 3] = rp[1];
+        r[D * W + 4] = rp[2];
+        // cell indices below 2^31 (n <= 512 in 3D) travel as the bits of a T
+        int* ri = reinterpret_cast<int*>(r + D * W + 5);
+        ri[0] = (int)base;
+        ri[sizeof(T) / sizeof(int)] = wraps ? packed : -1;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this lane's tap in each round: offset in the grid and (kx, ky, kz)
+    constexpr int NT = TABLE ? ROUNDS : 1;
+    int toff[NT];  // grid offsets of taps: below n^3 <= 2^27
+    int tk[NT];
+    auto tap_of = [&](int q, int& kx, int& ky, int& kz) {
+        const int tap = min(q * 32 + lane, TAPS - 1);
+        kx = tap % W;
+        ky = (tap / W) % W;
+        kz = (D == 3) ? tap / (W * W) : 0;
+    };
+    if constexpr (TABLE) {
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q) {
+            int kx, ky, kz;
+            tap_of(q, kx, ky, kz);
+            toff[q] = kx + n * (ky + n * kz);
+            tk[q] = kx | (ky << 8) | (kz << 16);
+        }
+    }
+    T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int jj = warp; jj < nj; jj += NWARP) {
+        const T* r = stage + jj * REC;
+        const int* ri = reinterpret_cast<const int*>(r + D * W + 5);
+        const int64_t base = ri[0];
+        const int packed = ri[sizeof(T) / sizeof(int)];
+        C f0 = mk(T(0), T(0)), f1 = f0, f2 = f0, f3 = f0;
+#pragma unroll(TABLE ? ROUNDS : 1)
+        for (int q = 0; q < ROUNDS; ++q) {
+            if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
+                int kx, ky, kz;
+                int64_t off;
+                if constexpr (TABLE) {
+                    kx = tk[q] & 255;
+                    ky = (tk[q] >> 8) & 255;
+                    kz = tk[q] >> 16;
+                    off = toff[q];
+                } else {
+                    tap_of(q, kx, ky, kz);
+                    off = kx + (int64_t)n * (ky + (int64_t)n * kz);
+                }
+                T wgt = r[kx] * r[W + ky];
+                if (D == 3) wgt *= r[2 * W + kz];
+                int64_t cell;
+                if (packed < 0) {  // uniform over the warp
+                    cell = base + off;
+                } else {
+                    cell = wrap_n((packed & 1023) + kx, n) + (int64_t)n * wrap_n(((packed >> 10) & 1023) + ky, n);
+                    if (D == 3) cell += (int64_t)n * n * wrap_n(((packed >> 20) & 1023) + kz, n);
+                }
+                C f[4];
+                load_cell(a.G, cells, cell, f);
+                f0 = cadd(f0, cscale(f[0], wgt));
+                f1 = cadd(f1, cscale(f[1], wgt));
+                f2 = cadd(f2, cscale(f[2], wgt));
+                if (D == 3) f3 = cadd(f3, cscale(f[3], wgt));
             }
         }
-        C phi = mk(T(0), T(0)), g0 = phi, g1 = phi, g2 = phi;
-        const int n = a.n;
-        if constexpr (D == 2) {
-#pragma unroll
-            for (int ky = 0; ky < W; ++ky) {
-                const int64_t rb = (int64_t)ix[1][ky] * n;
-#pragma unroll
-                for (int kx = 0; kx < W; ++kx) {
-                    const T wgt = wt[1][ky] * wt[0][kx];
-                    C f[4];
-                    load_cell(a.G, rb + ix[0][kx], f);
-                    phi = cadd(phi, cscale(f[0], wgt));
-                    g0 = cadd(g0, cscale(f[1], wgt));
-                    g1 = cadd(g1, cscale(f[2], wgt));
-                }
-            }
-        } else {
-            const T gzc = (rp[2] + tv[2]) * a.inv_h;
-            const int uz0 = (int)ceil(gzc - half);
-#pragma unroll 1
-            for (int kz = 0; kz < W; ++kz) {
-                const T zz = (T(uz0 + kz) - gzc) * inv_half;
-                const T z2 = zz * zz;
-                const T wz = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
-                const int64_t zb = (int64_t)wrap_n(uz0 + kz, n) * n;
-#pragma unroll
-                for (int ky = 0; ky < W; ++ky) {
-                    const int64_t rb = (zb + ix[1][ky]) * n;
-                    const T wzy = wz * wt[1][ky];
-#pragma unroll
-                    for (int kx = 0; kx < W; ++kx) {
-                        const T wgt = wzy * wt[0][kx];
-                        C f[4];
-                        load_cell(a.G, rb + ix[0][kx], f);
-                        phi = cadd(phi, cscale(f[0], wgt));
-                        g0 = cadd(g0, cscale(f[1], wgt));
-                        g1 = cadd(g1, cscale(f[2], wgt));
-                        g2 = cadd(g2, cscale(f[3], wgt));
-                    }
-                }
-            }
-        }
-        const T gx = c.x * g0.x - c.y * g0.y;
-        const T gy = c.x * g1.x - c.y * g1.y;
-        const T gz = (D == 3) ? c.x * g2.x - c.y * g2.y : T(0);
-        acc[0] = c.x * phi.x - c.y * phi.y;
-        acc[1] = gx;
-        acc[2] = gy;
-        acc[3] = gz;
-        acc[4] = rp[1] * gz - rp[2] * gy;
-        acc[5] = rp[2] * gx - rp[0] * gz;
-        acc[6] = rp[0] * gy - rp[1] * gx;
+        const T cx = r[D * W], cy = r[D * W + 1];
+        const T rx = r[D * W + 2], ry = r[D * W + 3], rz = r[D * W + 4];
+        const T gx = cx * f1.x - cy * f1.y;
+        const T gy = cx * f2.x - cy * f2.y;
+        const T gz = (D == 3) ? cx * f3.x - cy * f3.y : T(0);
+        acc[0] += cx * f0.x - cy * f0.y;
+        acc[1] += gx;
+        acc[2] += gy;
+        acc[3] += gz;
+        acc[4] += ry * gz - rz * gy;
+        acc[5] += rz * gx - rx * gz;
+        acc[6] += rx * gy - ry * gx;
     }
     double v[7];
 #pragma unroll
@@ -147,13 +207,12 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         v[k] = (double)acc[k];
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
         for (int k = 0; k < 7; ++k) red[warp][k] = v[k];
     __syncthreads();
     if (threadIdx.x < 7) {
         double s = 0.0;
-        for (int w = 0; w < GA_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < NWARP; ++w) s += red[w][threadIdx.x];
         atomicAdd(a.acc + 8 * (int64_t)pose + threadIdx.x, s);
     }
 }
@@ -162,12 +221,12 @@ template <typename T>
 cudaError_t launch_gather(const GatherArgs<T>& a, int dim, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(a.acc, 0, sizeof(double) * 8 * (a.P > 0 ? a.P : 1), st);
     if (e != cudaSuccess || a.P == 0 || a.m2 == 0) return e;
-    const dim3 grid((unsigned)((a.m2 + GA_THREADS - 1) / GA_THREADS), (unsigned)a.P);
-#define SD_GATHER_CASE(WW)                                                      \
-    case WW:                                                                    \
-        if (dim == 2) k_gather<T, 2, WW><<<grid, GA_THREADS, 0, st>>>(a);        \
-        else k_gather<T, 3, WW><<<grid, GA_THREADS, 0, st>>>(a);                 \
-        note_launch();                                                          \
+    auto grid = [&](int chunk) { return dim3((unsigned)((a.m2 + chunk - 1) / chunk), (unsigned)a.P); };
+#define SD_GATHER_CASE(WW)                                                                          \
+    case WW:                                                                                        \
+        if (dim == 2) k_gather<T, 2, WW><<<grid(gather_chunk<T, 2, WW>()), GA_THREADS, 0, st>>>(a); \
+        else k_gather<T, 3, WW><<<grid(gather_chunk<T, 3, WW>()), GA_THREADS, 0, st>>>(a);          \
+        note_launch();                                                                              \
         return cudaGetLastError();
     switch (a.w) {
         SD_GATHER_CASE(4) SD_GATHER_CASE(5) SD_GATHER_CASE(6) SD_GATHER_CASE(7) SD_GATHER_CASE(8)

@@ -183,7 +183,7 @@ struct GatherArgs {
     const T* quats;           // P x 4
     const T* trans;           // P x 3
     int64_t P;
-    const cplx<T>* G;         // n^d x 4 (Phi, dPhi/dx, dPhi/dy, dPhi/dz)
+    const cplx<T>* G;         // two planes of n^d cells: (Phi, dPhi/dx), (dPhi/dy, dPhi/dz)
     int n;
     T inv_h, beta;
     int w;

@@ -854,10 +854,12 @@ __global__ void k_wtable(const cplx<T>* B1, const double* D, int N, int dim, dou
     W[i] = mk(T(vr), T(vi));
 }
 
+// Field f (0: Phi, 1-3: its gradient) of the type-2 tables into its plane:
+// plane f / 2 holds fields (2k, 2k + 1) of every cell side by side.
 template <typename T>
 __global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cells) dst[4 * i + f] = src[i];
+    if (i < cells) dst[(f >> 1) * 2 * cells + 2 * i + (f & 1)] = src[i];
 }
 
 template <typename T>
