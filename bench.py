@@ -151,7 +151,7 @@ def load_workload(n_rot: int = 0, name: str = "peg_in_bore_3d"):
 WORKLOAD_TEXT = {
     "peg_in_bore_3d": "peg_in_bore_3d: cylinder r1 l3 into 6x6x4 block, bore r1.02 depth 2.5; 20k boundary + "
                       "~50k SDF samples per shape; 128^3 translations, n=256; 576 Hopf rotations; top-10 + FP64 "
-                      "re-score; 20-step gradient refinement",
+                      "re-score; 20-step on-device gradient refinement of the top 10",
     "docking_2000_500": "docking_2000_500: sphere unions of 2,000 and 500 spheres (radii U[1.2,2.0], confined "
                         "self-avoiding walks), 2 samples/A^2, ~80k/20k SDF samples; 192^3 translations at 0.8 A, "
                         "n=384; 3,000 super-Fibonacci rotations (one launch batch of the 54,000); top-100 + FP64 "
@@ -253,7 +253,7 @@ def run_ours(args):
         rots = torch.tensor([p["rot"] for p in poses], device=dev)
         q0 = inp["quats"][rots].float()
         t0 = torch.tensor([p["t"] for p in poses], dtype=torch.float32, device=dev)
-        q, t, hist = sd.refine_poses(ctx, fx, mv, grid, q0, t0, steps=REFINE_STEPS, lr_t=0.01, lr_q=0.005)
+        q, t, hist = ctx.refine_poses(fx, mv, grid, q0, t0, steps=REFINE_STEPS, lr_t=0.01, lr_q=0.005)
         e4 = mark()
         e4.synchronize()
         for k, (a_, b_) in zip(phase_ms, ((e0, e1), (e1, e2), (e2, e3), (e3, e4))):

@@ -249,6 +249,21 @@ int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
                   const void* quats, const void* trans, int64_t P, void* score, void* dq,
                   void* dt, void* stream);
 
+/* Gradient ascent on Re f_N from P starting poses, all on the device (the
+ * gradient-driven search of Section 6): each of `steps` steps evaluates the
+ * score and gradient as sd_score_grad does, then moves each translation by
+ * lr_t * dt / max|dt| and each quaternion by lr_q * dq / max|dq| (so a pose's
+ * largest move per step is lr_t, resp. lr_q, in its own units) and normalises
+ * the quaternion.
+ *   quats  device, P x 4 real (raw quaternions, updated in place)
+ *   trans  device, P x 3 real (updated in place; 2D: z ignored)
+ *   hist   device, (steps + 1) x P real, or NULL: the score before each step
+ *          and after the last
+ * Asynchronous on `stream`; one gather and one small kernel per step. */
+int sd_refine_poses(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g,
+                    void* quats, void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist,
+                    void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------- */
 
 /* Largest candidate count accepted by sd_top_k_static. */

@@ -1511,6 +1511,50 @@ static int score_grad_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     return SD_OK;
 }
 
+template <typename T>
+static int refine_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
+                    void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist, cudaStream_t st) {
+    Prep* p = nullptr;
+    CKI(prep_fields<T>(ctx, const_cast<sd_shape*>(fixed), g, &p, st));
+    void* acc;
+    CKI(ws_get(ctx, 4, (size_t)P * 8 * sizeof(double) + 256, &acc));
+    GatherArgs<T> a{};
+    a.p2 = (const vec4<T>*)moving->pos;
+    a.c2 = (const cplx<T>*)moving->c;
+    a.m2 = moving->m;
+    a.quats = (const T*)quats;
+    a.trans = (const T*)trans;
+    a.P = P;
+    a.G = (const cplx<T>*)p->G;
+    a.n = ctx->p.alpha * g->N;
+    a.inv_h = (T)(a.n / g->L);
+    a.beta = (T)ctx->p.beta;
+    a.w = ctx->p.w;
+    a.acc = (double*)acc;
+    for (int k = 0; k <= steps; ++k) {
+        CK(ctx, launch_gather<T>(a, ctx->p.dim, st));
+        T* h = hist ? (T*)hist + (int64_t)k * P : nullptr;
+        CK(ctx, launch_refine_step<T>((const double*)acc, (T*)quats, (T*)trans, P, ctx->p.dim, lr_t, lr_q, h,
+                                      k == steps, st));
+    }
+    return SD_OK;
+}
+
+int sd_refine_poses(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
+                    void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist, void* stream) {
+    if (!ctx) return SD_ERR_ARG;
+    CKI(check_pair(ctx, fixed, moving));
+    if (P < 0 || steps < 0) return fail(ctx, SD_ERR_ARG, "refine_poses: negative pose or step count");
+    if (P == 0) return SD_OK;
+    if (!quats || !trans) return fail(ctx, SD_ERR_ARG, "refine_poses: NULL pointer");
+    if (!(lr_t >= 0.0) || !(lr_q >= 0.0) || !isfinite(lr_t) || !isfinite(lr_q))
+        return fail(ctx, SD_ERR_ARG, "refine_poses: step sizes must be finite and non-negative");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->p.precision == SD_F64) return refine_t<double>(ctx, fixed, moving, g, quats, trans, P, steps, lr_t, lr_q, hist, st);
+    return refine_t<float>(ctx, fixed, moving, g, quats, trans, P, steps, lr_t, lr_q, hist, st);
+}
+
 int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, const void* quats,
                   const void* trans, int64_t P, void* score, void* dq, void* dt, void* stream) {
     if (!ctx) return SD_ERR_ARG;

@@ -262,6 +262,46 @@ __global__ void k_grad_finalize(const double* acc, const T* quats, int64_t P, in
     dq[4 * p + 3] = (T)(2.0 * sz * inv);
 }
 
+// One step of gradient ascent on P poses from the gather's accumulators: the
+// score goes to hist (if given); unless `last`, the translation moves by
+// lr_t * dt / max|dt| and the quaternion by lr_q * dq / max|dq| and is
+// renormalised (each pose's largest move per step is lr_t, resp. lr_q).
+template <typename T>
+__global__ void k_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim, double lr_t, double lr_q,
+                              T* hist, int last) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const double* a = acc + 8 * p;
+    if (hist) hist[p] = (T)a[0];
+    if (last) return;
+    T* q = quats + 4 * p;
+    T* t = trans + 3 * p;
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double nq = sqrt(w * w + x * x + y * y + z * z);
+    const double inv = nq > 0 ? 1.0 / nq : 0.0;
+    const double u0 = w * inv, ux = x * inv, uy = y * inv, uz = z * inv;
+    const double tx = a[4], ty = a[5], tz = a[6];
+    double dq[4] = {2.0 * inv * -(tx * ux + ty * uy + tz * uz), 2.0 * inv * (u0 * tx + (ty * uz - tz * uy)),
+                    2.0 * inv * (u0 * ty + (tz * ux - tx * uz)), 2.0 * inv * (u0 * tz + (tx * uy - ty * ux))};
+    double dt[3] = {a[1], a[2], dim == 3 ? a[3] : 0.0};
+    double st = 1e-30, sq = 1e-30;
+    for (int k = 0; k < 3; ++k) st = fmax(st, fabs(dt[k]));
+    for (int k = 0; k < 4; ++k) sq = fmax(sq, fabs(dq[k]));
+    for (int k = 0; k < 3; ++k) t[k] = (T)((double)t[k] + lr_t * dt[k] / st);
+    double qn[4] = {w + lr_q * dq[0] / sq, x + lr_q * dq[1] / sq, y + lr_q * dq[2] / sq, z + lr_q * dq[3] / sq};
+    const double nn = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+    for (int k = 0; k < 4; ++k) q[k] = (T)(nn > 0 ? qn[k] / nn : qn[k]);
+}
+
+template <typename T>
+cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim, double lr_t, double lr_q,
+                               T* hist, int last, cudaStream_t st) {
+    if (P == 0) return cudaSuccess;
+    k_refine_step<T><<<(unsigned)((P + 127) / 128), 128, 0, st>>>(acc, quats, trans, P, dim, lr_t, lr_q, hist, last);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_grad_finalize(const double* acc, const T* quats, int64_t P, int dim, T* score, T* dq, T* dt,
                                  cudaStream_t st) {

@@ -192,5 +192,7 @@ struct GatherArgs {
 template <typename T> cudaError_t launch_gather(const GatherArgs<T>& a, int dim, cudaStream_t st);
 template <typename T> cudaError_t launch_grad_finalize(const double* acc, const T* quats, int64_t P, int dim,
                                                        T* score, T* dq, T* dt, cudaStream_t st);
+template <typename T> cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim,
+                                                     double lr_t, double lr_q, T* hist, int last, cudaStream_t st);
 
 }  // namespace sd

@@ -96,6 +96,9 @@ _SIGS = {
                                   ct.c_void_p]),
     "sd_score_grad": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p,
                                  ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "sd_refine_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p,
+                                   ct.c_void_p, ct.c_int64, ct.c_int, ct.c_double, ct.c_double, ct.c_void_p,
+                                   ct.c_void_p]),
     "sd_host_line_fft": (ct.c_int, [ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_version": (ct.c_char_p, []),
     "sd_launch_count": (ct.c_int64, []),
@@ -353,6 +356,20 @@ class Context:
                                            _ptr(trans), P, _ptr(score), _ptr(dq), _ptr(dt),
                                            _stream(self.device)))
         return score, dq, dt[:, : self.dim]
+
+
+    def refine_poses(self, fixed: Shape, moving: Shape, grid: Grid, q0: torch.Tensor, t0: torch.Tensor,
+                     steps: int = 50, lr_t: float = 0.05, lr_q: float = 0.02):
+        """Gradient ascent on the device (sd_refine_poses): returns (q, t, score history (steps+1, P))."""
+        q = q0.detach().to(device=self.device, dtype=self.real).contiguous().clone()
+        t = self._dev(t0.detach(), cols=3).clone()
+        P = q.shape[0]
+        hist = torch.empty((steps + 1, P), dtype=self.real, device=self.device)
+        g = grid.c()
+        self._check(self.lib.sd_refine_poses(self.handle, fixed.handle, moving.handle, ct.byref(g), _ptr(q), _ptr(t),
+                                             P, int(steps), float(lr_t), float(lr_q), _ptr(hist),
+                                             _stream(self.device)))
+        return q, t[:, : self.dim], hist
 
 
 def launch_count() -> int:

@@ -352,6 +352,37 @@ def test_autograd_function_and_refinement():
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_native_refinement_follows_autograd_path(prec):
+    # sd_refine_poses runs the same ascent rule on the device (update arithmetic
+    # in FP64); its trajectory must follow the autograd loop's
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    g = grid_of(w, 16)
+    real = torch.float64 if prec == "f64" else torch.float32
+    q0 = torch.tensor(rotations.random_uniform(4, 7), device="cuda", dtype=real)
+    t0 = torch.tensor(rotations.random_ball(4, 1.0, 8, 3), device="cuda", dtype=real)
+    steps = 12
+    qa, ta, ha = sd.refine_poses(ctx, fx, mv, g, q0, t0, steps=steps, lr_t=0.02, lr_q=0.01)
+    qn, tn, hn = ctx.refine_poses(fx, mv, g, q0, t0, steps=steps, lr_t=0.02, lr_q=0.01)
+    s0 = ctx.score_grad(fx, mv, g, q0, t0)[0]
+    scale = ha.abs().max().item()
+    tol = 1e-9 if prec == "f64" else 1e-4
+    assert (hn[0] - s0).abs().max().item() <= 1e-12 * scale + (0 if prec == "f64" else 1e-6 * scale)
+    assert hn.shape == (steps + 1, 4)
+    assert (hn - ha).abs().max().item() <= tol * scale
+    assert (qn - qa).abs().max().item() <= (1e-9 if prec == "f64" else 1e-4)
+    assert (tn - ta).abs().max().item() <= (1e-9 if prec == "f64" else 1e-4)
+    assert torch.allclose(qn.norm(dim=1), torch.ones(4, device="cuda", dtype=real), atol=1e-6)
+    assert (hn[-1] >= hn[0]).all()
+    # q0 and t0 are inputs only
+    assert torch.equal(q0, torch.tensor(rotations.random_uniform(4, 7), device="cuda", dtype=real))
+    ctx.close()
+
+
 # ---------------------------------------------------------------------------
 # errors
 # ---------------------------------------------------------------------------
