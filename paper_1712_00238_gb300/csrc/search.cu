@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     __shared__ unsigned short qpair[RS_WARPS][RS_QUEUE][2];  // (fixed slot, moving slot)
     __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
     __shared__ float blo[3], bhi[3];
+    __shared__ float slo[RS_WARPS][3], shi[RS_WARPS][3];  // boxes of the 32-sample slices of a moving tile
     __shared__ double tv[3];
     __shared__ int skip;
     const int pose = blockIdx.y;
@@ -223,6 +224,16 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
         }
         qx1[threadIdx.x] = px; qy1[threadIdx.x] = py; qz1[threadIdx.x] = pz;
         ar1[threadIdx.x] = ar; ai1[threadIdx.x] = ai;
+    }
+    // this warp's box of fixed samples (every lane holds it)
+    float flo[3], fhi[3];
+    for (int d = 0; d < 3; ++d) {
+        flo[d] = lo[d];
+        fhi[d] = hi[d];
+        for (int off = 16; off > 0; off >>= 1) {
+            flo[d] = fminf(flo[d], __shfl_xor_sync(0xffffffffu, flo[d], off));
+            fhi[d] = fmaxf(fhi[d], __shfl_xor_sync(0xffffffffu, fhi[d], off));
+        }
     }
     block_bbox(lo, hi, wlo, whi, blo, bhi);
     // the moved samples lie in a ball of radius sqrt(r2max) around t
@@ -271,15 +282,38 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
         if (g0 * g0 + g1 * g1 + g2 * g2 > cm2) continue;  // same decision in every thread
         const int64_t j = (int64_t)tile * RS_TILE + threadIdx.x;
         __syncthreads();
-        if (j < a.m2) {
-            const double4 y = moved[j];
-            yx[threadIdx.x] = y.x; yy[threadIdx.x] = y.y; yz[threadIdx.x] = y.z;
-            fx[threadIdx.x] = (float)y.x; fy[threadIdx.x] = (float)y.y; fz[threadIdx.x] = (float)y.z;
-            cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
+        {
+            float mlo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+            if (j < a.m2) {
+                const double4 y = moved[j];
+                yx[threadIdx.x] = y.x; yy[threadIdx.x] = y.y; yz[threadIdx.x] = y.z;
+                fx[threadIdx.x] = (float)y.x; fy[threadIdx.x] = (float)y.y; fz[threadIdx.x] = (float)y.z;
+                cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
+                mlo[0] = mhi[0] = fx[threadIdx.x];
+                mlo[1] = mhi[1] = fy[threadIdx.x];
+                mlo[2] = mhi[2] = fz[threadIdx.x];
+            }
+            for (int d = 0; d < 3; ++d)
+                for (int off = 16; off > 0; off >>= 1) {
+                    mlo[d] = fminf(mlo[d], __shfl_down_sync(0xffffffffu, mlo[d], off));
+                    mhi[d] = fmaxf(mhi[d], __shfl_down_sync(0xffffffffu, mhi[d], off));
+                }
+            if (lane == 0)
+                for (int d = 0; d < 3; ++d) { slo[warp][d] = mlo[d]; shi[warp][d] = mhi[d]; }
         }
         __syncthreads();
         const int cnt = (int)min((int64_t)RS_TILE, a.m2 - (int64_t)tile * RS_TILE);
         for (int k = 0; k < cnt; ++k) {
+            if ((k & 31) == 0) {  // skip a slice whose box is beyond the cutoff of this warp's box
+                const int sl = k >> 5;
+                const float h0 = fmaxf(0.f, fmaxf(slo[sl][0] - fhi[0], flo[0] - shi[sl][0]));
+                const float h1 = fmaxf(0.f, fmaxf(slo[sl][1] - fhi[1], flo[1] - shi[sl][1]));
+                const float h2 = (a.dim == 3) ? fmaxf(0.f, fmaxf(slo[sl][2] - fhi[2], flo[2] - shi[sl][2])) : 0.f;
+                if (h0 * h0 + h1 * h1 + h2 * h2 > cm2) {  // same decision in every lane of the warp
+                    k += 31;
+                    continue;
+                }
+            }
             bool pass = false;
             if (live) {
                 const float dxf = fx[k] - pxf, dyf = fy[k] - pyf, dzf = fz[k] - pzf;
