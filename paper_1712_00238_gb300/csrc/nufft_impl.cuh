@@ -425,6 +425,9 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
     // flush: pairs of x-adjacent tile cells (global x even: bins start at multiples of 8)
     constexpr int XP = (PS + 1) / 2;
     constexpr int PAIRS = (D == 3) ? XP * PS2 : XP * PS;
+    bool inner = true;  // the tile does not wrap around the sub-box (no modulo below)
+#pragma unroll
+    for (int d = 0; d < D; ++d) inner &= (org0[d] + PS <= s);
     for (int i = threadIdx.x; i < PAIRS; i += blockDim.x) {
         const int xp = i % XP, row = i / XP;  // row = y + PS z
         const int x = 2 * xp;
@@ -433,9 +436,15 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
         const float2 v1 = (x + 1 < PS) ? make_float2(tre[li + 1], tim[li + 1]) : make_float2(0.f, 0.f);
         if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
         const int y = row % PS, z = row / PS;
+        const int gx = org0[0] + x;
+        if (inner && gx + 1 < s) {
+            int64_t o = (int64_t)(org0[1] + y) * s;
+            if (D == 3) o += (int64_t)(org0[2] + z) * s * s;
+            add_pair(out + o + gx, v0, v1);
+            continue;
+        }
         int64_t o = (int64_t)wrap_index(org0[1] + y, s) * s;
         if (D == 3) o += (int64_t)wrap_index(org0[2] + z, s) * s * s;
-        const int gx = org0[0] + x;
         if (gx + 1 < s) {
             add_pair(out + o + gx, v0, v1);
         } else {
