@@ -394,9 +394,9 @@ def run_ours(args):
 # keyed by (pass, sub-box side, N, rotations per launch); a launch of another
 # shape reports null.
 TRAFFIC_PER_LAUNCH: dict = {
-    ("fused", 108, 128, 34): 553426688 + 531017984,
-    ("fwd_y", 108, 128, 34): 406161920 + 432556032,
-    ("inv_y", 108, 128, 34): 570464768 + 510324480,
+    ("fused", 108, 128, 34): 554947072 + 527249664,
+    ("fwd_y", 108, 128, 34): 406128128 + 432073984,
+    ("inv_y", 108, 128, 34): 570462720 + 506701056,
 }
 
 
