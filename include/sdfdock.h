@@ -223,6 +223,20 @@ int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
                    int32_t* spread_bins);
 
+/* The autotuner's cached plans as JSON text,
+ *   {"sdfdock_plans": 1, "plans": [{"key": K, "batch": B, "spread_bins": S}, ...]}
+ * (K: precision|dim|N|n|sub-box/16|log2 of the moving sample count).  *len
+ * receives the size including the terminating NUL; with buf NULL only the size
+ * is returned; a smaller cap is SD_ERR_ARG. */
+int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
+
+/* Add the plans of a JSON text written by sd_tune_export to this context's
+ * cache (entries with a key already present are replaced), so searches of those
+ * geometries skip the timing trials.  A text that is not such a table, or an
+ * entry with batch outside [1, 64] or spread_bins not 0/1, is SD_ERR_ARG and
+ * leaves the cache unchanged. */
+int sd_tune_import(sd_ctx* ctx, const char* json);
+
 /* Global top-k over per-rotation candidates, ordered by score descending,
  * then rotation ascending, then translation index ascending; optionally each
  * pose is re-scored in FP64 by direct pair sums of the continuous score

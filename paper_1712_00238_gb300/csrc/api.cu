@@ -1363,6 +1363,48 @@ int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, co
     return run_search<float>(ctx, fixed, moving, quats, n_r, g, map_out, 1, st);
 }
 
+int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len) {
+    if (!ctx) return SD_ERR_ARG;
+    std::string js = "{\"sdfdock_plans\": 1, \"plans\": [";
+    bool first = true;
+    for (const auto& kv : ctx->tuned) {
+        char e[256];
+        snprintf(e, sizeof e, "%s{\"key\": \"%s\", \"batch\": %d, \"spread_bins\": %d}", first ? "" : ", ",
+                 kv.first.c_str(), kv.second.B, kv.second.bins);
+        js += e;
+        first = false;
+    }
+    js += "]}";
+    const int64_t need = (int64_t)js.size() + 1;
+    if (len) *len = need;
+    if (!buf) return SD_OK;
+    if (cap < need) return fail(ctx, SD_ERR_ARG, "tune_export: buffer of %lld bytes, %lld needed", (long long)cap,
+                                (long long)need);
+    memcpy(buf, js.c_str(), (size_t)need);
+    return SD_OK;
+}
+
+int sd_tune_import(sd_ctx* ctx, const char* json) {
+    if (!ctx) return SD_ERR_ARG;
+    if (!json || !strstr(json, "\"sdfdock_plans\"")) return fail(ctx, SD_ERR_ARG, "tune_import: not a plan table");
+    std::map<std::string, Plan> got;
+    const char* p = json;
+    while ((p = strstr(p, "{\"key\": \"")) != nullptr) {
+        p += strlen("{\"key\": \"");
+        const char* q = strchr(p, '"');
+        if (!q || q - p > 120) return fail(ctx, SD_ERR_ARG, "tune_import: malformed key");
+        std::string key(p, (size_t)(q - p));
+        int B = 0, bins = -1;
+        if (sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d}", &B, &bins) != 2 || B < 1 || B > 64 ||
+            (bins != 0 && bins != 1))
+            return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
+        got[key] = Plan{B, bins};
+        p = q;
+    }
+    for (auto& kv : got) ctx->tuned[kv.first] = kv.second;
+    return SD_OK;
+}
+
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
                    int32_t* spread_bins) {
     if (!ctx) return SD_ERR_ARG;

@@ -91,6 +91,8 @@ _SIGS = {
                                   ct.c_void_p]),
     "sd_search_plan": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_int64,
                                   ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+    "sd_tune_export": (ct.c_int, [ct.c_void_p, ct.c_char_p, ct.c_int64, ct.POINTER(ct.c_int64)]),
+    "sd_tune_import": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
     "sd_top_k_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_int, ct.c_void_p,
                                   ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.POINTER(sd_pose),
                                   ct.c_void_p]),
@@ -297,6 +299,18 @@ class Context:
         self._check(self.lib.sd_score_maps(self.handle, fixed.handle, moving.handle, _ptr(quats), n_r,
                                            ct.byref(g), _ptr(out), _stream(self.device)))
         return torch.view_as_complex(out)
+
+    def tune_export(self) -> str:
+        """The autotuner's cached plans as JSON text (sd_tune_export)."""
+        n = ct.c_int64()
+        self._check(self.lib.sd_tune_export(self.handle, None, 0, ct.byref(n)))
+        buf = ct.create_string_buffer(n.value)
+        self._check(self.lib.sd_tune_export(self.handle, buf, n.value, ct.byref(n)))
+        return buf.value.decode()
+
+    def tune_import(self, text: str):
+        """Add plans written by tune_export to this context's cache (sd_tune_import)."""
+        self._check(self.lib.sd_tune_import(self.handle, text.encode()))
 
     def search_plan(self, moving: Shape, grid: Grid, n_r: int) -> dict:
         """The plan a search would use now: rotations per batch and binned (1) or direct spreading."""

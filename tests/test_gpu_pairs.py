@@ -107,3 +107,36 @@ def test_score_pairs_rejects_bad_jobs():
         ctx.score_pairs([(fx, mv, _quats(w.quats), sd.Grid(40, w.L))])
     assert e.value.code == sd.SD_ERR_ARG
     ctx.close()
+
+
+def test_tuned_plans_export_and_import():
+    import json
+    import re
+
+    ctx = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
+    fx, mv, q, g, _ = _jobs(ctx)[2]
+    qd = _quats(q)
+    ctx.set_option("autotune", 1)
+    ctx.score_rotations(fx, mv, qd, g)  # times the candidate plans of this geometry once
+    plan = ctx.search_plan(mv, g, qd.shape[0])
+    text = ctx.tune_export()
+    table = json.loads(text)
+    assert table["sdfdock_plans"] == 1 and len(table["plans"]) == 1
+    assert table["plans"][0]["batch"] >= 1 and table["plans"][0]["spread_bins"] in (0, 1)
+
+    ctx2 = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
+    fx2, mv2, _, _, _ = _jobs(ctx2)[2]
+    ctx2.set_option("autotune", 1)
+    before = ctx2.search_plan(mv2, g, qd.shape[0])
+    ctx2.tune_import(text)
+    assert ctx2.search_plan(mv2, g, qd.shape[0]) == plan
+    assert json.loads(ctx2.tune_export()) == table
+    # malformed tables are refused and leave the cache as it was
+    for bad in ("{}", re.sub(r'"batch": \d+', '"batch": 0', text), re.sub(r'"spread_bins": \d+', '"spread_bins": 7', text)):
+        with pytest.raises(sd.SdError) as e:
+            ctx2.tune_import(bad)
+        assert e.value.code == sd.SD_ERR_ARG
+    assert json.loads(ctx2.tune_export()) == table
+    assert isinstance(before["batch"], int)
+    ctx.close()
+    ctx2.close()
