@@ -11,9 +11,12 @@ sdf    Eq. 10A, 11, 12a, 13, 15, 16c, 17t: signed distance, membership and the S
 score  Eq. 1 / Eq. 8: the pair-sum score of Gaussian-represented SDFs, its
        band-limited periodic form on the translation grid of Section 5, the
        per-rotation argmax and global top-k, and pose gradients.
+refine Section 6: force and torque of the virtual energy E ~ -f, and the pose
+       updates that climb the score (gradient ascent, conjugate gradient,
+       damped rigid-body dynamics).
 
 Every function is pinned by tests under tests/ (closed forms, invariances,
 brute force).  Absolute SDF and score values of the synthetic workloads have no
 printed counterpart in the paper: parity unpinned beyond those checks.
 """
-from . import score, sdf  # noqa: F401
+from . import refine, score, sdf  # noqa: F401
