@@ -61,6 +61,8 @@ def parse_args():
                                            "uneven_batch"],
                     default="peg_in_bore_3d")
     ap.add_argument("--pairs", type=int, default=0, help="uneven_batch: use only the first P pairs")
+    ap.add_argument("--refine-method", choices=["autograd", "ascent", "cg", "dynamics"], default="autograd",
+                    help="refine_256: the autograd Function loop, or an on-device rule of sd_refine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -525,7 +527,13 @@ def run_refine(args):
             with torch.cuda.stream(stream):
                 a.record(stream)
                 qi, ti = (hq.to(dev, non_blocking=True), ht.to(dev, non_blocking=True)) if e2e else (dq, dt)
-                _, _, hist = sd.refine_poses(ctx, fx, mv, grid, qi, ti, steps=iters, lr_t=0.2, lr_q=0.01)
+                if args.refine_method == "autograd":
+                    _, _, hist = sd.refine_poses(ctx, fx, mv, grid, qi, ti, steps=iters, lr_t=0.2, lr_q=0.01)
+                else:
+                    method = {"ascent": sd.REFINE_ASCENT, "cg": sd.REFINE_CG,
+                              "dynamics": sd.REFINE_DYNAMICS}[args.refine_method]
+                    _, _, hist = ctx.refine(fx, mv, grid, qi, ti, iters, method=method, lr_t=0.2, lr_q=0.01,
+                                            mass=20.0, inertia=2000.0, damping=0.2, dt=1.0)
                 last = hist[-1].cpu() if e2e else hist
                 b.record(stream)
             b.synchronize()
@@ -553,8 +561,9 @@ def run_refine(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "refine_256: docking pair (2,000 / 500 spheres), 192^3 band-limited field on the "
-                               "n=384 grid; 256 random poses (seed 3), 50 gradient-ascent steps per bench step "
-                               "(type-2 gather score + gradient, autograd Function)",
+                               "n=384 grid; 256 random poses (seed 3), 50 steps per bench step (type-2 gather "
+                               "score + gradient; " + ("autograd Function, gradient ascent" if args.refine_method ==
+                               "autograd" else f"on-device sd_refine, {args.refine_method}") + ")",
                    "poses": poses, "iterations": iters, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * evals / (ms_e2e * 1e-3), "unit": "evals/s",

@@ -278,6 +278,34 @@ int sd_refine_poses(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, 
                     void* quats, void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist,
                     void* stream);
 
+/* Pose-update rules of sd_refine (Section 6: the score as a virtual energy
+ * E ~ -f with force F = d Re f / dt and torque T = sum_j (R p2_j) x g_j, the
+ * derivative for a left rotation R <- exp([omega]x) R). */
+#define SD_REFINE_ASCENT 0    /* t += lr_t F / max|F|; q += lr_q dq / max|dq|, normalised */
+#define SD_REFINE_CG 1        /* Polak-Ribiere (beta clipped at 0) per translation / rotation block;
+                                 t moves lr_t along its direction, R turns lr_q radians */
+#define SD_REFINE_DYNAMICS 2  /* damped rigid body from rest: v <- (1-damping) v + dt F / mass,
+                                 w <- (1-damping) w + dt T / inertia, t += dt v, q <- exp(dt w) q */
+
+typedef struct sd_refine_params {
+    int method;      /* SD_REFINE_* */
+    double lr_t;     /* ascent, CG: largest translation per step */
+    double lr_q;     /* ascent: largest quaternion change per step; CG: rotation per step (radians) */
+    double mass;     /* dynamics: mass (> 0) */
+    double inertia;  /* dynamics: scalar moment of inertia (> 0) */
+    double damping;  /* dynamics: velocity damping factor per step, in [0, 1] */
+    double dt;       /* dynamics: time step (>= 0) */
+} sd_refine_params;
+
+/* Local maximisation of Re f_N from P starting poses on the device with one of
+ * the SD_REFINE_* rules: `steps` updates, each after a type-2 gather of the
+ * score, force and torque (as sd_score_grad).  quats / trans / hist as for
+ * sd_refine_poses; per-pose state (CG directions, velocities) lives in the
+ * context's workspace.  SD_ERR_ARG for an unknown method or out-of-range
+ * parameter.  Asynchronous on `stream`. */
+int sd_refine(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
+              void* trans, int64_t P, int steps, const sd_refine_params* params, void* hist, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------- */
 
 /* Largest candidate count accepted by sd_top_k_static. */

@@ -1555,11 +1555,12 @@ static int score_grad_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
 
 template <typename T>
 static int refine_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
-                    void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist, cudaStream_t st) {
+                    void* trans, int64_t P, int steps, const RefineParams& rp, void* hist, cudaStream_t st) {
     Prep* p = nullptr;
     CKI(prep_fields<T>(ctx, const_cast<sd_shape*>(fixed), g, &p, st));
-    void* acc;
+    void *acc, *state = nullptr;
     CKI(ws_get(ctx, 4, (size_t)P * 8 * sizeof(double) + 256, &acc));
+    if (rp.method != SD_REFINE_ASCENT) CKI(ws_get(ctx, 7, (size_t)P * 12 * sizeof(double) + 256, &state));
     GatherArgs<T> a{};
     a.p2 = (const vec4<T>*)moving->pos;
     a.c2 = (const cplx<T>*)moving->c;
@@ -1576,25 +1577,43 @@ static int refine_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, 
     for (int k = 0; k <= steps; ++k) {
         CK(ctx, launch_gather<T>(a, ctx->p.dim, st));
         T* h = hist ? (T*)hist + (int64_t)k * P : nullptr;
-        CK(ctx, launch_refine_step<T>((const double*)acc, (T*)quats, (T*)trans, P, ctx->p.dim, lr_t, lr_q, h,
-                                      k == steps, st));
+        CK(ctx, launch_refine_step<T>((const double*)acc, (T*)quats, (T*)trans, (double*)state, P, ctx->p.dim, rp,
+                                      k == 0, h, k == steps, st));
     }
     return SD_OK;
 }
 
-int sd_refine_poses(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
-                    void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist, void* stream) {
+int sd_refine(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
+              void* trans, int64_t P, int steps, const sd_refine_params* params, void* hist, void* stream) {
     if (!ctx) return SD_ERR_ARG;
     CKI(check_pair(ctx, fixed, moving));
-    if (P < 0 || steps < 0) return fail(ctx, SD_ERR_ARG, "refine_poses: negative pose or step count");
+    if (!params) return fail(ctx, SD_ERR_ARG, "refine: params is NULL");
+    if (P < 0 || steps < 0) return fail(ctx, SD_ERR_ARG, "refine: negative pose or step count");
     if (P == 0) return SD_OK;
-    if (!quats || !trans) return fail(ctx, SD_ERR_ARG, "refine_poses: NULL pointer");
-    if (!(lr_t >= 0.0) || !(lr_q >= 0.0) || !isfinite(lr_t) || !isfinite(lr_q))
-        return fail(ctx, SD_ERR_ARG, "refine_poses: step sizes must be finite and non-negative");
+    if (!quats || !trans) return fail(ctx, SD_ERR_ARG, "refine: NULL pointer");
+    RefineParams rp{params->method, params->lr_t, params->lr_q, params->mass, params->inertia, params->damping,
+                    params->dt};
+    auto finite_nonneg = [](double x) { return isfinite(x) && x >= 0.0; };
+    if (rp.method == SD_REFINE_ASCENT || rp.method == SD_REFINE_CG) {
+        if (!finite_nonneg(rp.lr_t) || !finite_nonneg(rp.lr_q))
+            return fail(ctx, SD_ERR_ARG, "refine: step sizes must be finite and non-negative");
+    } else if (rp.method == SD_REFINE_DYNAMICS) {
+        if (!(isfinite(rp.mass) && rp.mass > 0.0) || !(isfinite(rp.inertia) && rp.inertia > 0.0) ||
+            !(rp.damping >= 0.0 && rp.damping <= 1.0) || !finite_nonneg(rp.h))
+            return fail(ctx, SD_ERR_ARG, "refine: dynamics needs mass, inertia > 0, damping in [0, 1], dt >= 0");
+    } else {
+        return fail(ctx, SD_ERR_ARG, "refine: unknown method %d", rp.method);
+    }
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (ctx->p.precision == SD_F64) return refine_t<double>(ctx, fixed, moving, g, quats, trans, P, steps, lr_t, lr_q, hist, st);
-    return refine_t<float>(ctx, fixed, moving, g, quats, trans, P, steps, lr_t, lr_q, hist, st);
+    if (ctx->p.precision == SD_F64) return refine_t<double>(ctx, fixed, moving, g, quats, trans, P, steps, rp, hist, st);
+    return refine_t<float>(ctx, fixed, moving, g, quats, trans, P, steps, rp, hist, st);
+}
+
+int sd_refine_poses(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, void* quats,
+                    void* trans, int64_t P, int steps, double lr_t, double lr_q, void* hist, void* stream) {
+    sd_refine_params rp{SD_REFINE_ASCENT, lr_t, lr_q, 1.0, 1.0, 0.0, 0.0};
+    return sd_refine(ctx, fixed, moving, g, quats, trans, P, steps, &rp, hist, stream);
 }
 
 int sd_score_grad(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const sd_grid* g, const void* quats,

@@ -262,42 +262,115 @@ __global__ void k_grad_finalize(const double* acc, const T* quats, int64_t P, in
     dq[4 * p + 3] = (T)(2.0 * sz * inv);
 }
 
-// One step of gradient ascent on P poses from the gather's accumulators: the
-// score goes to hist (if given); unless `last`, the translation moves by
-// lr_t * dt / max|dt| and the quaternion by lr_q * dq / max|dq| and is
-// renormalised (each pose's largest move per step is lr_t, resp. lr_q).
+// q <- exp(theta) (x) q / |.| for a rotation vector theta (left multiplication).
+__device__ __forceinline__ void rotate_left(double q[4], const double th[3]) {
+    const double a = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+    double o[4] = {q[0], q[1], q[2], q[3]};
+    if (a > 0.0) {
+        const double c = cos(0.5 * a), s = sin(0.5 * a) / a;
+        const double ew = c, ex = s * th[0], ey = s * th[1], ez = s * th[2];
+        o[0] = ew * q[0] - ex * q[1] - ey * q[2] - ez * q[3];
+        o[1] = ew * q[1] + ex * q[0] + ey * q[3] - ez * q[2];
+        o[2] = ew * q[2] - ex * q[3] + ey * q[0] + ez * q[1];
+        o[3] = ew * q[3] + ex * q[2] - ey * q[1] + ez * q[0];
+    }
+    const double n = sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + o[3] * o[3]);
+    for (int k = 0; k < 4; ++k) q[k] = n > 0.0 ? o[k] / n : o[k];
+}
+
+// One update of P poses from the gather's accumulators (score, force
+// F = d Re f / dt, torque T = sum (R p2) x g): the score goes to hist (if
+// given); unless `last` the pose moves by
+//   ascent:    t += lr_t F / max|F|, q += lr_q dq / max|dq| (dq = d Re f / dq), q normalised;
+//   CG:        Polak-Ribiere directions (beta clipped at 0) kept per block, t moved
+//              lr_t along the translation direction, R rotated lr_q radians about
+//              the rotation direction;
+//   dynamics:  v <- (1 - gamma) v + h F / m, w <- (1 - gamma) w + h T / I,
+//              t += h v, q <- exp(h w) q.
+// state (P x 12 doubles): CG (gF, gT, dF, dT) of the previous step; dynamics (v, w).
 template <typename T>
-__global__ void k_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim, double lr_t, double lr_q,
-                              T* hist, int last) {
+__global__ void k_refine_step(const double* acc, T* quats, T* trans, double* state, int64_t P, int dim,
+                              RefineParams rp, int first, T* hist, int last) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const double* a = acc + 8 * p;
     if (hist) hist[p] = (T)a[0];
     if (last) return;
-    T* q = quats + 4 * p;
-    T* t = trans + 3 * p;
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    const double nq = sqrt(w * w + x * x + y * y + z * z);
-    const double inv = nq > 0 ? 1.0 / nq : 0.0;
-    const double u0 = w * inv, ux = x * inv, uy = y * inv, uz = z * inv;
-    const double tx = a[4], ty = a[5], tz = a[6];
-    double dq[4] = {2.0 * inv * -(tx * ux + ty * uy + tz * uz), 2.0 * inv * (u0 * tx + (ty * uz - tz * uy)),
-                    2.0 * inv * (u0 * ty + (tz * ux - tx * uz)), 2.0 * inv * (u0 * tz + (tx * uy - ty * ux))};
-    double dt[3] = {a[1], a[2], dim == 3 ? a[3] : 0.0};
-    double st = 1e-30, sq = 1e-30;
-    for (int k = 0; k < 3; ++k) st = fmax(st, fabs(dt[k]));
-    for (int k = 0; k < 4; ++k) sq = fmax(sq, fabs(dq[k]));
-    for (int k = 0; k < 3; ++k) t[k] = (T)((double)t[k] + lr_t * dt[k] / st);
-    double qn[4] = {w + lr_q * dq[0] / sq, x + lr_q * dq[1] / sq, y + lr_q * dq[2] / sq, z + lr_q * dq[3] / sq};
-    const double nn = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
-    for (int k = 0; k < 4; ++k) q[k] = (T)(nn > 0 ? qn[k] / nn : qn[k]);
+    T* qo = quats + 4 * p;
+    T* to = trans + 3 * p;
+    double q[4] = {qo[0], qo[1], qo[2], qo[3]};
+    double t[3] = {to[0], to[1], dim == 3 ? (double)to[2] : 0.0};
+    const double F[3] = {a[1], a[2], dim == 3 ? a[3] : 0.0};
+    const double Tq[3] = {a[4], a[5], a[6]};
+    double* st = state ? state + 12 * p : nullptr;
+    if (rp.method == SD_REFINE_ASCENT) {
+        const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double inv = nq > 0 ? 1.0 / nq : 0.0;
+        const double u0 = q[0] * inv, ux = q[1] * inv, uy = q[2] * inv, uz = q[3] * inv;
+        const double tx = Tq[0], ty = Tq[1], tz = Tq[2];
+        const double dq[4] = {2.0 * inv * -(tx * ux + ty * uy + tz * uz), 2.0 * inv * (u0 * tx + (ty * uz - tz * uy)),
+                              2.0 * inv * (u0 * ty + (tz * ux - tx * uz)), 2.0 * inv * (u0 * tz + (tx * uy - ty * ux))};
+        double sf = 1e-30, sq = 1e-30;
+        for (int k = 0; k < 3; ++k) sf = fmax(sf, fabs(F[k]));
+        for (int k = 0; k < 4; ++k) sq = fmax(sq, fabs(dq[k]));
+        for (int k = 0; k < 3; ++k) t[k] += rp.lr_t * F[k] / sf;
+        double qn[4];
+        for (int k = 0; k < 4; ++k) qn[k] = q[k] + rp.lr_q * dq[k] / sq;
+        const double nn = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        for (int k = 0; k < 4; ++k) q[k] = nn > 0 ? qn[k] / nn : qn[k];
+    } else if (rp.method == SD_REFINE_CG) {
+        const double* g[2] = {F, Tq};
+        double d[2][3];
+        for (int b = 0; b < 2; ++b) {
+            double beta = 0.0;
+            if (!first) {
+                const double* gp = st + 3 * b;
+                double num = 0.0, den = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    num += g[b][k] * (g[b][k] - gp[k]);
+                    den += gp[k] * gp[k];
+                }
+                beta = den > 0.0 ? fmax(0.0, num / den) : 0.0;
+            }
+            for (int k = 0; k < 3; ++k) d[b][k] = g[b][k] + (first ? 0.0 : beta * st[6 + 3 * b + k]);
+        }
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 3; ++k) {
+                st[3 * b + k] = g[b][k];
+                st[6 + 3 * b + k] = d[b][k];
+            }
+        const double nt = sqrt(d[0][0] * d[0][0] + d[0][1] * d[0][1] + d[0][2] * d[0][2]);
+        const double nr = sqrt(d[1][0] * d[1][0] + d[1][1] * d[1][1] + d[1][2] * d[1][2]);
+        if (nt > 0.0)
+            for (int k = 0; k < 3; ++k) t[k] += rp.lr_t * d[0][k] / nt;
+        if (nr > 0.0) {
+            const double th[3] = {rp.lr_q * d[1][0] / nr, rp.lr_q * d[1][1] / nr, rp.lr_q * d[1][2] / nr};
+            rotate_left(q, th);
+        }
+    } else {  // SD_REFINE_DYNAMICS
+        double v[3], w[3];
+        for (int k = 0; k < 3; ++k) {
+            v[k] = (first ? 0.0 : (1.0 - rp.damping) * st[k]) + rp.h * F[k] / rp.mass;
+            w[k] = (first ? 0.0 : (1.0 - rp.damping) * st[3 + k]) + rp.h * Tq[k] / rp.inertia;
+            st[k] = v[k];
+            st[3 + k] = w[k];
+            t[k] += rp.h * v[k];
+        }
+        const double th[3] = {rp.h * w[0], rp.h * w[1], rp.h * w[2]};
+        rotate_left(q, th);
+    }
+    for (int k = 0; k < 4; ++k) qo[k] = (T)q[k];
+    to[0] = (T)t[0];
+    to[1] = (T)t[1];
+    if (dim == 3) to[2] = (T)t[2];
 }
 
 template <typename T>
-cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim, double lr_t, double lr_q,
-                               T* hist, int last, cudaStream_t st) {
+cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, double* state, int64_t P, int dim,
+                               const RefineParams& rp, int first, T* hist, int last, cudaStream_t st) {
     if (P == 0) return cudaSuccess;
-    k_refine_step<T><<<(unsigned)((P + 127) / 128), 128, 0, st>>>(acc, quats, trans, P, dim, lr_t, lr_q, hist, last);
+    k_refine_step<T><<<(unsigned)((P + 127) / 128), 128, 0, st>>>(acc, quats, trans, state, P, dim, rp, first, hist,
+                                                                  last);
     note_launch();
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "../../include/sdfdock.h"
 
 namespace sd {
 
@@ -192,7 +193,13 @@ struct GatherArgs {
 template <typename T> cudaError_t launch_gather(const GatherArgs<T>& a, int dim, cudaStream_t st);
 template <typename T> cudaError_t launch_grad_finalize(const double* acc, const T* quats, int64_t P, int dim,
                                                        T* score, T* dq, T* dt, cudaStream_t st);
-template <typename T> cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, int64_t P, int dim,
-                                                     double lr_t, double lr_q, T* hist, int last, cudaStream_t st);
+// Pose-update rule of the refinement loop (values of sd_refine_params.method).
+struct RefineParams {
+    int method;
+    double lr_t, lr_q, mass, inertia, damping, h;
+};
+template <typename T> cudaError_t launch_refine_step(const double* acc, T* quats, T* trans, double* state, int64_t P,
+                                                     int dim, const RefineParams& rp, int first, T* hist, int last,
+                                                     cudaStream_t st);
 
 }  // namespace sd

@@ -66,6 +66,13 @@ class sd_pair_stat(ct.Structure):
                 ("s", ct.c_int32)]
 
 
+class sd_refine_params(ct.Structure):
+    _fields_ = [("method", ct.c_int), ("lr_t", ct.c_double), ("lr_q", ct.c_double), ("mass", ct.c_double),
+                ("inertia", ct.c_double), ("damping", ct.c_double), ("dt", ct.c_double)]
+
+
+REFINE_ASCENT, REFINE_CG, REFINE_DYNAMICS = 0, 1, 2
+
 CAND_BYTES = 16  # sd_cand: double score, int32 rot, int32 idx
 
 _LIB = None
@@ -101,6 +108,8 @@ _SIGS = {
     "sd_refine_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p,
                                    ct.c_void_p, ct.c_int64, ct.c_int, ct.c_double, ct.c_double, ct.c_void_p,
                                    ct.c_void_p]),
+    "sd_refine": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p, ct.c_void_p,
+                             ct.c_int64, ct.c_int, ct.POINTER(sd_refine_params), ct.c_void_p, ct.c_void_p]),
     "sd_host_line_fft": (ct.c_int, [ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_version": (ct.c_char_p, []),
     "sd_launch_count": (ct.c_int64, []),
@@ -383,6 +392,23 @@ class Context:
         self._check(self.lib.sd_refine_poses(self.handle, fixed.handle, moving.handle, ct.byref(g), _ptr(q), _ptr(t),
                                              P, int(steps), float(lr_t), float(lr_q), _ptr(hist),
                                              _stream(self.device)))
+        return q, t[:, : self.dim], hist
+
+
+    def refine(self, fixed: Shape, moving: Shape, grid: Grid, q0: torch.Tensor, t0: torch.Tensor, steps: int,
+               method: int = REFINE_CG, lr_t: float = 0.05, lr_q: float = 0.02, mass: float = 1.0,
+               inertia: float = 1.0, damping: float = 0.1, dt: float = 0.1):
+        """Maximise the score on the device from P poses with one of the sd_refine rules
+        (REFINE_ASCENT, REFINE_CG, REFINE_DYNAMICS): returns (q, t, score history (steps+1, P))."""
+        q = q0.detach().to(device=self.device, dtype=self.real).contiguous().clone()
+        t = self._dev(t0.detach(), cols=3).clone()
+        P = q.shape[0]
+        hist = torch.empty((steps + 1, P), dtype=self.real, device=self.device)
+        g = grid.c()
+        rp = sd_refine_params(int(method), float(lr_t), float(lr_q), float(mass), float(inertia), float(damping),
+                              float(dt))
+        self._check(self.lib.sd_refine(self.handle, fixed.handle, moving.handle, ct.byref(g), _ptr(q), _ptr(t), P,
+                                       int(steps), ct.byref(rp), _ptr(hist), _stream(self.device)))
         return q, t[:, : self.dim], hist
 
 

@@ -352,6 +352,55 @@ def test_autograd_function_and_refinement():
     ctx.close()
 
 
+@pytest.mark.parametrize("name,method", [("tiny_3d", "cg"), ("tiny_3d", "dynamics"), ("tiny_2d", "cg"),
+                                         ("tiny_2d", "dynamics")])
+def test_refine_rules_match_oracle(name, method):
+    # the device's conjugate-gradient and damped-dynamics updates against the
+    # oracle's rules driven by the oracle's own pair-sum force and torque
+    from oracle import refine as orf
+
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    ctx = make_ctx(w, "f64")
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    N = 16
+    g = grid_of(w, N)
+    P, steps = 2, 4
+    if w.dim == 3:
+        q0 = rotations.random_uniform(P, 9)
+        t0 = rotations.random_ball(P, 0.8, 10, 3)
+    else:
+        q0 = rotations.planar(7)[[1, 4]]
+        t0 = rotations.random_ball(P, 0.8, 10, 2)
+    kw = dict(lr_t=0.03, lr_q=0.02) if method == "cg" else dict(mass=2.0, inertia=3.0, damping=0.2, dt=0.05)
+    code = sd.REFINE_CG if method == "cg" else sd.REFINE_DYNAMICS
+    qd = torch.tensor(q0, device="cuda", dtype=torch.float64)
+    td = torch.tensor(t0, device="cuda", dtype=torch.float64)
+    qg, tg, hg = ctx.refine(fx, mv, g, qd, td, steps, method=code, **kw)
+    qg, tg, hg = qg.cpu().numpy(), tg.cpu().numpy(), hg.cpu().numpy()
+
+    def grad(q, t):
+        return orf.force_torque_fN(p1, c1, p2, c2, q, t[: w.dim], N, w.L, w.sigma_g)
+
+    okw = dict(lr_t=kw.get("lr_t", 0), lr_q=kw.get("lr_q", 0), mass=kw.get("mass", 1), inertia=kw.get("inertia", 1),
+               damping=kw.get("damping", 0), h=kw.get("dt", 0))
+    for i in range(P):
+        qo, to, ho = orf.refine(grad, q0[i], t0[i], steps, orf.CG if method == "cg" else orf.DYNAMICS, **okw)
+        scale = np.abs(ho).max()
+        assert np.abs(hg[:, i] - ho).max() <= 1e-4 * scale, (i, hg[:, i], ho)
+        sign = 1.0 if float(qg[i] @ qo) >= 0 else -1.0  # q and -q are one rotation
+        assert np.abs(qg[i] - sign * qo).max() < 1e-5
+        assert np.abs(tg[i] - to[: w.dim]).max() < 1e-5
+    with pytest.raises(sd.SdError) as e:
+        ctx.refine(fx, mv, g, qd, td, 1, method=7)
+    assert e.value.code == sd.SD_ERR_ARG
+    with pytest.raises(sd.SdError) as e:
+        ctx.refine(fx, mv, g, qd, td, 1, method=sd.REFINE_DYNAMICS, mass=0.0)
+    assert e.value.code == sd.SD_ERR_ARG
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_native_refinement_follows_autograd_path(prec):
     # sd_refine_poses runs the same ascent rule on the device (update arithmetic
