@@ -415,9 +415,9 @@ def run_ours(args):
 # keyed by (pass, sub-box side, N, rotations per launch); a launch of another
 # shape reports null.
 TRAFFIC_PER_LAUNCH: dict = {
-    ("fused", 108, 128, 34): 554947072 + 527249664,
-    ("fwd_y", 108, 128, 34): 406128128 + 432073984,
-    ("inv_y", 108, 128, 34): 570462720 + 506701056,
+    ("fused", 108, 128, 34): 554573824 + 527024896,
+    ("fwd_y", 108, 128, 34): 406127104 + 432105984,
+    ("inv_y", 108, 128, 34): 570511360 + 506710784,
 }
 
 

@@ -58,13 +58,20 @@ __host__ __device__ constexpr int cta_threads() {
 // Resident CTAs per SM that a pass's register allocation is bounded for, 0 for
 // the compiler's own choice.  The 384-point FP32 passes (384 threads) take 3
 // (at most 56 registers a thread; 66-70 otherwise, which allows two); the
-// 512-point FP32 passes take 2 (at most 128; 150-170 otherwise, one CTA).  Every
+// 512-point FP32 passes take 2 (at most 128; 150-170 otherwise, one CTA); the
+// fused 256-point column pass takes 4 (at most 64; it would take 75).  Every
 // other pass keeps the compiler's choice, which already allows four or more
 // CTAs of 256 threads: an explicit minimum there makes it take more registers
 // than it needs.
 template <typename T, int LEN>
 __host__ __device__ constexpr int min_ctas_per_sm() {
     return sizeof(T) != 4 ? 0 : (LEN == 384 ? 3 : (LEN == 512 ? 2 : 0));
+}
+
+// The same for a column pass of MODE (the fused 256-point FP32 pass takes 4).
+template <typename T, int LEN, int MODE>
+__host__ __device__ constexpr int min_ctas_per_sm_cols() {
+    return (sizeof(T) == 4 && LEN == 256 && MODE == COL_FUSED) ? 4 : min_ctas_per_sm<T, LEN>();
 }
 
 // ---------------------------------------------------------------------------
@@ -607,7 +614,7 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a) {
         } else {
             e = pos;
         }
-        return in[(int64_t)e * ncols + gcol];
+        return in[e * ncols + gcol];  // offsets within one rotation's slab: below 2^31
     };
     if constexpr (MODE == COL_FUSED) {
         // forward: keep the N central modes, multiply by W, place them as the
@@ -615,13 +622,13 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a) {
         auto emit_fwd = [&](int line, int o, C v) {
             const int kp = o < hN ? o : (o >= LENF - hN ? o - LENF + N : -1);
             const int gcol = col0 + line;
-            if (kp >= 0 && gcol < ncols) buf[line * LD + pad(kp)] = cmul(v, a.W[(int64_t)kp * ncols + gcol]);
+            if (kp >= 0 && gcol < ncols) buf[line * LD + pad(kp)] = cmul(v, a.W[kp * ncols + gcol]);
         };
         fft_lines_io<C, LENF, false, TC, NT, LAY_COL, false>(buf, LD, twF, load, emit_fwd);
         __syncthreads();
         auto emit_out = [&](int line, int o, C v) {
             const int gcol = col0 + line;
-            if (gcol < ncols) out[(int64_t)o * ncols + gcol] = v;
+            if (gcol < ncols) out[o * ncols + gcol] = v;
         };
         fft_lines_io<C, LENI, true, TC, NT, LAY_COL, true>(buf, LD, twI, load, emit_out);
     } else {
@@ -630,9 +637,9 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a) {
             if (gcol >= ncols) return;
             if constexpr (MODE == COL_FWD) {
                 const int kp = o < hN ? o : (o >= LENF - hN ? o - LENF + N : -1);
-                if (kp >= 0) out[(int64_t)kp * ncols + gcol] = v;
+                if (kp >= 0) out[kp * ncols + gcol] = v;
             } else {
-                out[(int64_t)o * ncols + gcol] = v;
+                out[o * ncols + gcol] = v;
             }
         };
         fft_lines_io<C, LENF, INV1, TC, NT, LAY_COL, false>(buf, LD, twF, load, emit);
@@ -698,7 +705,8 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
     const size_t smem = (size_t)(TC * line_pitch(LENF) + tw_count(LENF) + tw_count(LENI)) * sizeof(C);
     void (*kern)(ColArgs<T>);
-    if constexpr (min_ctas_per_sm<T, LENF>() > 0) kern = k_cols_mb<T, LENF, LENI, MODE, min_ctas_per_sm<T, LENF>()>;
+    if constexpr (min_ctas_per_sm_cols<T, LENF, MODE>() > 0)
+        kern = k_cols_mb<T, LENF, LENI, MODE, min_ctas_per_sm_cols<T, LENF, MODE>()>;
     else kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
