@@ -7,7 +7,8 @@ the product path never does, and it imports nothing from the product package.
 
 Modules
 -------
-sdf    Eq. 10A, 11, 12a, 13, 15, 16c, 17t: signed distance, membership and the SDF sum.
+sdf    Eq. 10A, 11, 12a, 13, 15, 16c, 17t: signed distance, membership and the SDF sum;
+       the other phi-kernels of Section 4 (proximal, radial, skin/core).
 score  Eq. 1 / Eq. 8: the pair-sum score of Gaussian-represented SDFs, its
        band-limited periodic form on the translation grid of Section 5, the
        per-rotation argmax and global top-k, and pose gradients.

@@ -100,6 +100,59 @@ def sdf_rho(p, q, nrm, area, lam1=1.0, lam2=3.0, sigma_t=0.5, eps=1.5, pmc_value
     return rho
 
 
+PHI_SDF, PHI_PROXIMAL, PHI_RADIAL, PHI_SKIN = 0, 1, 2, 3
+
+
+def rho_variant(p, q, nrm, area, phi, radius=1.0, lam1=1.0, lam2=3.0, sigma_t=0.5, pmc_values=None, chunk=512):
+    """rho(p) for the other phi-kernels Section 4 sets beside Eq. 15 (their Section 3 analogues).
+
+    Eq. 13 with a different phi, or the pointwise skin/core form:
+      PHI_PROXIMAL  phi(zeta) = lambda zeta^-2 / sqrt(2 pi), lambda of Eq. 16c (the proximal
+                    factor of Eq. 15 alone: inverse-square, no characteristic size, no
+                    truncation); in 2D the planar angle measure as for Eq. 15;
+      PHI_RADIAL    phi(zeta) = c g(eta / R - 1), c = lam1 outside and i lam2 inside
+                    (skin real, core imaginary), g the normalised Gaussian of width sigma_t:
+                    only eta = Im zeta is used, like the radial-basis double-skin affinity;
+      PHI_SKIN      rho(p) = lam1 g(xi / R - 1) + i lam2 g(xi / R + 1), the swept-volume
+                    skin / core layers of the signed distance (no boundary integral);
+    with R = ``radius``.
+    """
+    p = np.asarray(p, float)
+    q = np.asarray(q, float)
+    nrm = np.asarray(nrm, float)
+    area = np.asarray(area, float)
+    dim = p.shape[1]
+    if pmc_values is None:
+        pmc_values = pmc(p, q, nrm, area)
+
+    def gauss(x):
+        return np.exp(-0.5 * (x / sigma_t) ** 2) / (math.sqrt(2 * math.pi) * sigma_t)
+
+    rho = np.empty(len(p), complex)
+    for s in range(0, len(p), chunk):
+        ps = p[s:s + chunk]
+        diff = ps[:, None, :] - q[None, :, :]
+        eta = np.linalg.norm(diff, axis=2)
+        xi = pmc_values[s:s + chunk] * eta.min(axis=1)
+        if phi == PHI_SKIN:
+            rho[s:s + chunk] = lam1 * gauss(xi / radius - 1.0) + 1j * lam2 * gauss(xi / radius + 1.0)
+            continue
+        cos_t = (diff * nrm[None, :, :]).sum(axis=2) / eta
+        if phi == PHI_PROXIMAL:
+            lam = np.where(xi > 0, lam1, -lam2)
+            zeta = xi[:, None] + 1j * eta
+            f = lam[:, None] / math.sqrt(2 * math.pi) / zeta ** 2
+            if dim == 2:
+                f = f * 2.0 * eta
+        elif phi == PHI_RADIAL:
+            c = np.where(xi > 0, lam1 + 0j, 1j * lam2)
+            f = c[:, None] * gauss(eta / radius - 1.0)
+        else:
+            raise ValueError(phi)
+        rho[s:s + chunk] = (f * cos_t * area[None, :]).sum(axis=1)
+    return rho
+
+
 def sdf_weights(rho, vol):
     """Weights of the sampled representation: c_i = rho_i * v_i."""
     return np.asarray(rho) * np.asarray(vol)

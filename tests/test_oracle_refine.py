@@ -89,3 +89,4 @@ def test_dynamics_under_constant_force_and_torque(gamma):
     s = [sum((1 - gamma) ** j for j in range(i)) for i in range(1, k + 1)]
     assert np.allclose(t, h * h * F0 / m * sum(s), atol=1e-14)
     assert np.allclose(oscore.rotation_matrix(q), _rz(h * h * Tz / inertia * sum(s)), atol=1e-13)
+
