@@ -64,7 +64,26 @@ typedef struct sd_params {
     int w;            /* spreading width in grid cells of the oversampled grid (2..16) */
     int alpha;        /* oversampling factor of the nonequispaced FFT (only 2)         */
     double beta;      /* shape of the exponential-of-semicircle kernel; <= 0: 2.30*w   */
+    int phi;          /* SD_PHI_*: the phi-kernel of Eq. 13 (default SD_PHI_SDF)        */
+    double phi_radius;/* characteristic radius R of SD_PHI_RADIAL / SD_PHI_SKIN (> 0)   */
 } sd_params;
+
+/* phi-kernels (Section 4: Eq. 13 is a platform for several affinities).  g is
+ * the normalised Gaussian of width sigma_t, R = phi_radius, lambda = +lambda1
+ * outside and -lambda2 inside (Eq. 16c).
+ *   SD_PHI_SDF       Eq. 15 with the truncation of Eq. 17t: the skeletal density.
+ *   SD_PHI_PROXIMAL  phi = lambda zeta^-2 / sqrt(2 pi): the proximal factor alone
+ *                    (inverse-square, no characteristic size; eps is ignored).
+ *   SD_PHI_RADIAL    phi = c g(eta / R - 1) with c = lambda1 outside, i lambda2
+ *                    inside: uses eta = Im zeta only, like a radial-basis
+ *                    double-skin affinity (eps is ignored).
+ *   SD_PHI_SKIN      rho = lambda1 g(xi / R - 1) + i lambda2 g(xi / R + 1): the
+ *                    skin / core layers of the signed distance (no boundary sum).
+ * In 2D the inverse-square kernels take the planar angle measure as Eq. 15 does. */
+#define SD_PHI_SDF 0
+#define SD_PHI_PROXIMAL 1
+#define SD_PHI_RADIAL 2
+#define SD_PHI_SKIN 3
 
 /* Translation grid: N points per axis on a periodic box of side L. */
 typedef struct sd_grid {

@@ -1073,6 +1073,8 @@ int sd_default_params(sd_params* p, int dim, int precision) {
     p->w = 6;
     p->alpha = 2;
     p->beta = 0.0;
+    p->phi = SD_PHI_SDF;
+    p->phi_radius = 1.0;
     return SD_OK;
 }
 
@@ -1088,6 +1090,9 @@ int sd_create(sd_ctx** out, int device, const sd_params* p) {
     if (!wok) return fail(nullptr, SD_ERR_ARG, "spreading width w=%d not supported (4-8, 10, 12, 16)", p->w);
     if (!(p->sigma_t > 0) || !(p->sigma_g > 0) || !(p->lambda1 >= 0) || !(p->lambda2 >= 0) || isnan(p->eps))
         return fail(nullptr, SD_ERR_ARG, "sigma_t, sigma_g must be > 0; lambdas >= 0; eps not NaN");
+    if (p->phi < SD_PHI_SDF || p->phi > SD_PHI_SKIN) return fail(nullptr, SD_ERR_ARG, "unknown phi-kernel %d", p->phi);
+    if (!(p->phi_radius > 0) || !isfinite(p->phi_radius))
+        return fail(nullptr, SD_ERR_ARG, "phi_radius must be positive and finite");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -1220,6 +1225,8 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     a.lam2 = (T)ctx->p.lambda2;
     a.sigma = (T)ctx->p.sigma_t;
     a.eps = isinf(ctx->p.eps) ? T(-1) : (T)ctx->p.eps;
+    a.phi = ctx->p.phi;
+    a.radius = (T)ctx->p.phi_radius;
     a.xi_abs = xi;
     a.pmc = pm;
     a.c_out = (cplx<T>*)s->c;

@@ -31,6 +31,8 @@ struct SdfArgs {
     int64_t m;
     const int8_t* pmc_override;  // m or null
     T lam1, lam2, sigma, eps;    // eps < 0 disables truncation
+    int phi;                     // SD_PHI_* (kernel of Eq. 13)
+    T radius;                    // R of the radial and skin / core kernels
     // outputs / intermediates
     T* xi_abs;            // m: nearest distance
     int8_t* pmc;          // m: +1 / -1

@@ -84,7 +84,7 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
     s = t;
 }
 
-template <typename T, int D>
+template <typename T, int D, int PHI>
 __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
     __shared__ vec4<T> sq[SDF_TILE];
     __shared__ vec4<T> sn[SDF_TILE];
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
         p.x = p.y = p.z = p.w = T(0);
     }
     // CTA box and cutoff radius (1 + eps) max|xi| for the tile test
-    const bool cull = a.tile_box != nullptr && a.eps >= T(0);
+    const bool cull = PHI == SD_PHI_SDF && a.tile_box != nullptr && a.eps >= T(0);
     if (cull) {
         float v[7] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f};
         if (live) {
@@ -129,7 +129,12 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
         __syncthreads();
     }
     const T lam = xi > T(0) ? a.lam1 : -a.lam2;
-    const T pref = lam / (T(2.0 * M_PI) * a.sigma);  // lambda/sqrt(2 pi) * 1/(sqrt(2 pi) sigma)
+    // SDF: lambda/sqrt(2 pi) * 1/(sqrt(2 pi) sigma); proximal: lambda/sqrt(2 pi);
+    // radial: 1/(sqrt(2 pi) sigma), times lambda1 (real) outside or lambda2 (imaginary) inside
+    const T pref = PHI == SD_PHI_SDF      ? lam / (T(2.0 * M_PI) * a.sigma)
+                   : PHI == SD_PHI_PROXIMAL ? lam / sqrt(T(2.0 * M_PI))
+                                            : T(1) / (sqrt(T(2.0 * M_PI)) * a.sigma);
+    const T inv_r = recip(a.radius);
     const T inv_xabs = recip(xabs);
     const T inv_2s2 = recip(T(2) * a.sigma * a.sigma);
     const T xi2 = xi * xi;
@@ -155,10 +160,17 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
             const T dx = p.x - q.x, dy = p.y - q.y, dz = (D == 3) ? p.z - q.z : T(0);
             const T d2 = dx * dx + dy * dy + dz * dz;
             const T eta = sqrt(d2);
-            const T rm1 = eta * inv_xabs - T(1);
-            if (a.eps >= T(0) && rm1 > a.eps) continue;
             const vec4<T> nn = sn[k];
-            const T E = exp(-rm1 * rm1 * inv_2s2);
+            if constexpr (PHI == SD_PHI_RADIAL) {
+                const T x = eta * inv_r - T(1);
+                const T f = pref * exp(-x * x * inv_2s2) * (dx * nn.x + dy * nn.y + dz * nn.z) * recip(eta) * nn.w;
+                if (xi > T(0)) kahan_add(sr, cr, a.lam1 * f);
+                else kahan_add(si, ci, a.lam2 * f);
+                continue;
+            }
+            const T rm1 = eta * inv_xabs - T(1);
+            if (PHI == SD_PHI_SDF && a.eps >= T(0) && rm1 > a.eps) continue;
+            const T E = PHI == SD_PHI_SDF ? exp(-rm1 * rm1 * inv_2s2) : T(1);
             const T cos_t = (dx * nn.x + dy * nn.y + dz * nn.z) * recip(eta);
             // zeta^-2 = (xi - i eta)^2 / (xi^2 + eta^2)^2
             const T den = xi2 + d2;
@@ -225,16 +237,54 @@ cudaError_t launch_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const 
     return cudaGetLastError();
 }
 
+// Skin / core layers of the signed distance (no boundary sum):
+// rho = lambda1 g(xi / R - 1) + i lambda2 g(xi / R + 1), g the normalised Gaussian
+// of width sigma.
+template <typename T>
+__global__ void __launch_bounds__(SDF_TILE) k_sdf_skin(SdfArgs<T> a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    const int64_t src = a.perm_q ? (int64_t)a.perm_q[i] : i;
+    const vec4<T> p = a.qry[src];
+    const T xi = a.pmc[i] < 0 ? -a.xi_abs[i] : a.xi_abs[i];
+    const T inv_r = recip(a.radius);
+    const T inv_2s2 = recip(T(2) * a.sigma * a.sigma);
+    const T norm = T(1) / (sqrt(T(2.0 * M_PI)) * a.sigma);
+    const T xo = xi * inv_r - T(1), xc = xi * inv_r + T(1);
+    const T sr = a.lam1 * norm * exp(-xo * xo * inv_2s2);
+    const T si = a.lam2 * norm * exp(-xc * xc * inv_2s2);
+    const T v = a.vol[src];
+    a.c_out[i] = mk(sr * v, si * v);
+    if (a.rho_out) a.rho_out[src] = mk(sr, si);
+    vec4<T> po = p;
+    po.w = T(0);
+    a.pos_out[i] = po;
+}
+
 template <typename T>
 cudaError_t launch_sdf(const SdfArgs<T>& a, int dim, cudaStream_t st) {
     if (a.m == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((a.m + SDF_TILE - 1) / SDF_TILE);
-    if (dim == 2) {
-        k_sdf_nearest<T, 2><<<nb, SDF_TILE, 0, st>>>(a);
-        k_sdf_sum<T, 2><<<nb, SDF_TILE, 0, st>>>(a);
-    } else {
-        k_sdf_nearest<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
-        k_sdf_sum<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
+    if (dim == 2) k_sdf_nearest<T, 2><<<nb, SDF_TILE, 0, st>>>(a);
+    else k_sdf_nearest<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
+    switch (a.phi) {
+        case SD_PHI_SDF:
+            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_SDF><<<nb, SDF_TILE, 0, st>>>(a);
+            else k_sdf_sum<T, 3, SD_PHI_SDF><<<nb, SDF_TILE, 0, st>>>(a);
+            break;
+        case SD_PHI_PROXIMAL:
+            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_PROXIMAL><<<nb, SDF_TILE, 0, st>>>(a);
+            else k_sdf_sum<T, 3, SD_PHI_PROXIMAL><<<nb, SDF_TILE, 0, st>>>(a);
+            break;
+        case SD_PHI_RADIAL:
+            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_RADIAL><<<nb, SDF_TILE, 0, st>>>(a);
+            else k_sdf_sum<T, 3, SD_PHI_RADIAL><<<nb, SDF_TILE, 0, st>>>(a);
+            break;
+        case SD_PHI_SKIN:
+            k_sdf_skin<T><<<nb, SDF_TILE, 0, st>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
     }
     note_launch(2);
     return cudaGetLastError();

@@ -44,7 +44,11 @@ class SdError(RuntimeError):
 class sd_params(ct.Structure):
     _fields_ = [("dim", ct.c_int), ("precision", ct.c_int), ("lambda1", ct.c_double),
                 ("lambda2", ct.c_double), ("sigma_t", ct.c_double), ("eps", ct.c_double),
-                ("sigma_g", ct.c_double), ("w", ct.c_int), ("alpha", ct.c_int), ("beta", ct.c_double)]
+                ("sigma_g", ct.c_double), ("w", ct.c_int), ("alpha", ct.c_int), ("beta", ct.c_double),
+                ("phi", ct.c_int), ("phi_radius", ct.c_double)]
+
+
+PHI_SDF, PHI_PROXIMAL, PHI_RADIAL, PHI_SKIN = 0, 1, 2, 3
 
 
 class sd_grid(ct.Structure):

@@ -73,6 +73,28 @@ def test_sdf_values_match_oracle(name, prec, eps):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,prec", [("tiny_2d", "f64"), ("tiny_3d", "f32"), ("tiny_3d", "f64")])
+@pytest.mark.parametrize("phi", ["proximal", "radial", "skin"])
+def test_other_phi_kernels_match_oracle(name, prec, phi):
+    # the proximal, radial and skin / core kernels of Section 4 through the same build
+    w = getattr(configs, name)()
+    code = {"proximal": sd.PHI_PROXIMAL, "radial": sd.PHI_RADIAL, "skin": sd.PHI_SKIN}[phi]
+    radius = 0.35
+    ctx = make_ctx(w, prec, phi=code, phi_radius=radius)
+    for s in (w.fixed, w.moving):
+        _, rho = gpu_shape(ctx, s, return_rho=True)
+        got = rho.cpu().numpy()
+        got = got[:, 0] + 1j * got[:, 1]
+        b = s.boundary
+        ref = osdf.rho_variant(s.query.pos, b.pos, b.normal, b.area, code, radius, w.lam1, w.lam2, w.sigma_t)
+        assert rel_err(got, ref) < (1e-9 if prec == "f64" else 1e-4), phi
+    ctx.close()
+    with pytest.raises(sd.SdError):
+        make_ctx(w, prec, phi=9)
+    with pytest.raises(sd.SdError):
+        make_ctx(w, prec, phi=code, phi_radius=0.0)
+
+
 def test_sdf_full_size_sampled_points():
     # 3D peg-in-bore shapes at full size (20,000 boundary samples, ~50,000 query
     # points); the oracle evaluates a seeded sample of the query points.
