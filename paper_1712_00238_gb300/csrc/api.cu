@@ -582,8 +582,11 @@ static int prep_fields(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, 
     CK(ctx, pool_alloc((void**)&X, sx * sizeof(C), st));
     if (sy) CK(ctx, pool_alloc((void**)&Y, sy * sizeof(C), st));
     CK(ctx, pool_alloc((void**)&Z, nd * sizeof(C), st));
-    CK(ctx, pool_alloc((void**)&Gf, 4 * nd * sizeof(C), st));
-    CK(ctx, cudaMemsetAsync(Gf, 0, 4 * nd * sizeof(C), st));
+    // type-2 tables on a grid of pitch n + w: the cells past n repeat the periodic field
+    const int pn = n + ctx->p.w;
+    const int64_t pd = (G.dim == 2) ? (int64_t)pn * pn : (int64_t)pn * pn * pn;
+    CK(ctx, pool_alloc((void**)&Gf, 4 * pd * sizeof(C), st));
+    CK(ctx, cudaMemsetAsync(Gf, 0, 4 * pd * sizeof(C), st));
     for (int f = 0; f <= G.dim; ++f) {
         CK(ctx, launch_wtable<T>((const C*)p->B1, D, N, G.dim, G.L, ctx->p.sigma_g, 0, f - 1, F, st));
         RowArgs<T> r{};
@@ -625,7 +628,7 @@ static int prep_fields(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, 
             c.nouter = 1;
             CK(ctx, launch_cols<T>(COL_EXPAND, c, 1, st));
         }
-        CK(ctx, launch_interleave<T>(Z, Gf, nd, f, st));
+        CK(ctx, launch_interleave<T>(Z, Gf, n, pn, G.dim, f, st));
     }
     pool_free(F, st);
     pool_free(X, st);
@@ -1551,6 +1554,7 @@ static int score_grad_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     a.P = P;
     a.G = (const cplx<T>*)p->G;
     a.n = ctx->p.alpha * g->N;
+    a.pn = a.n + ctx->p.w;
     a.inv_h = (T)(a.n / g->L);
     a.beta = (T)ctx->p.beta;
     a.w = ctx->p.w;
@@ -1577,6 +1581,7 @@ static int refine_t(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, 
     a.P = P;
     a.G = (const cplx<T>*)p->G;
     a.n = ctx->p.alpha * g->N;
+    a.pn = a.n + ctx->p.w;
     a.inv_h = (T)(a.n / g->L);
     a.beta = (T)ctx->p.beta;
     a.w = ctx->p.w;

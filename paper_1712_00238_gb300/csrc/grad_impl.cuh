@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
     constexpr bool TABLE = ROUNDS <= 8;  // per-lane tap table in registers (else derived per round)
     constexpr int CHUNK = gather_chunk<T, D, W>();
     constexpr int NWARP = GA_THREADS / 32;
-    constexpr int REC = D * W + 7;  // weights, c (2), R p2 (3), origin cell, packed wrapped origin (-1: no wrap)
+    constexpr int REC = D * W + 7;  // weights, c (2), R p2 (3), origin cell (wrapped into [0, n)), spare
     __shared__ T stage[CHUNK * REC];
     __shared__ T Rm[9], tv[3];
     __shared__ double red[NWARP][7];
@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         tv[2] = (D == 3) ? t[2] : T(0);
     }
     __syncthreads();
-    const int n = a.n;
-    const int64_t cells = (D == 3) ? (int64_t)n * n * n : (int64_t)n * n;
+    const int n = a.n, pn = a.pn;
+    const int64_t cells = (D == 3) ? (int64_t)pn * pn * pn : (int64_t)pn * pn;
     const int64_t j0 = (int64_t)blockIdx.x * CHUNK;
     const int nj = (int)((a.m2 - j0) < (int64_t)CHUNK ? (a.m2 - j0) : (int64_t)CHUNK);
     // stage: one sample per thread
@@ -100,9 +100,7 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         rp[2] = (D == 3) ? Rm[6] * p.x + Rm[7] * p.y + Rm[8] * pz : T(0);
         T* r = stage + threadIdx.x * REC;
         const T half = T(W) * T(0.5), inv_half = T(2) / T(W);
-        bool wraps = false;
-        int64_t base = 0, mul = 1;
-        int packed = 0;
+        int base = 0, mul = 1;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const T g = (rp[d] + tv[d]) * a.inv_h;
@@ -113,27 +111,23 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
                 const T z2 = zz * zz;
                 r[d * W + k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
             }
-            wraps |= (u0 < 0 || u0 + W > n);
-            const int uw = wrap_n(u0, n);
-            base += uw * mul;
-            mul *= n;
-            packed |= uw << (10 * d);
+            base += wrap_n(u0, n) * mul;  // taps reach index n - 1 + W - 1 < pn: no wrapping per tap
+            mul *= pn;
         }
         r[D * W] = c.x;
         r[D * W + 1] = c.y;
         r[D * W + 2] = rp[0];
         r[D * W + 3] = rp[1];
         r[D * W + 4] = rp[2];
-        // cell indices below 2^31 (n <= 512 in 3D) travel as the bits of a T
+        // cell indices below 2^31 (pn <= 528 in 3D) travel as the bits of a T
         int* ri = reinterpret_cast<int*>(r + D * W + 5);
-        ri[0] = (int)base;
-        ri[sizeof(T) / sizeof(int)] = wraps ? packed : -1;
+        ri[0] = base;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this lane's tap in each round: offset in the grid and (kx, ky, kz)
     constexpr int NT = TABLE ? ROUNDS : 1;
-    int toff[NT];  // grid offsets of taps: below n^3 <= 2^27
+    int toff[NT];  // grid offsets of taps: below pn^3 < 2^28
     int tk[NT];
     auto tap_of = [&](int q, int& kx, int& ky, int& kz) {
         const int tap = min(q * 32 + lane, TAPS - 1);
@@ -146,22 +140,20 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
         for (int q = 0; q < ROUNDS; ++q) {
             int kx, ky, kz;
             tap_of(q, kx, ky, kz);
-            toff[q] = kx + n * (ky + n * kz);
+            toff[q] = kx + pn * (ky + pn * kz);
             tk[q] = kx | (ky << 8) | (kz << 16);
         }
     }
     T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int jj = warp; jj < nj; jj += NWARP) {
         const T* r = stage + jj * REC;
-        const int* ri = reinterpret_cast<const int*>(r + D * W + 5);
-        const int64_t base = ri[0];
-        const int packed = ri[sizeof(T) / sizeof(int)];
+        const int base = reinterpret_cast<const int*>(r + D * W + 5)[0];
         C f0 = mk(T(0), T(0)), f1 = f0, f2 = f0, f3 = f0;
 #pragma unroll(TABLE ? ROUNDS : 1)
         for (int q = 0; q < ROUNDS; ++q) {
             if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
                 int kx, ky, kz;
-                int64_t off;
+                int off;
                 if constexpr (TABLE) {
                     kx = tk[q] & 255;
                     ky = (tk[q] >> 8) & 255;
@@ -169,17 +161,11 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(GatherArgs<T> a) {
                     off = toff[q];
                 } else {
                     tap_of(q, kx, ky, kz);
-                    off = kx + (int64_t)n * (ky + (int64_t)n * kz);
+                    off = kx + pn * (ky + pn * kz);
                 }
                 T wgt = r[kx] * r[W + ky];
                 if (D == 3) wgt *= r[2 * W + kz];
-                int64_t cell;
-                if (packed < 0) {  // uniform over the warp
-                    cell = base + off;
-                } else {
-                    cell = wrap_n((packed & 1023) + kx, n) + (int64_t)n * wrap_n(((packed >> 10) & 1023) + ky, n);
-                    if (D == 3) cell += (int64_t)n * n * wrap_n(((packed >> 20) & 1023) + kz, n);
-                }
+                const int cell = base + off;
                 C f[4];
                 load_cell(a.G, cells, cell, f);
                 f0 = cadd(f0, cscale(f[0], wgt));

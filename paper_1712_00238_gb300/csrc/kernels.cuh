@@ -148,9 +148,9 @@ cudaError_t launch_wtable(const cplx<T>* B1, const double* D, int N, int dim, do
 cudaError_t launch_reduce_argmax(const double* part_score, const int* part_idx, int nparts, int batch,
                                  int64_t rot0, void* cand, cudaStream_t st);
 
-// copy field f of 4 into an interleaved [cell][4] array
+// field f of 4 into its plane of the halo-padded type-2 tables
 template <typename T>
-cudaError_t launch_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f, cudaStream_t st);
+cudaError_t launch_interleave(const cplx<T>* src, cplx<T>* dst, int n, int pn, int dim, int f, cudaStream_t st);
 
 // ---- search -----------------------------------------------------------------
 cudaError_t launch_topk(const void* cand, int64_t n, int k, void* out_cand, unsigned* flags,
@@ -186,8 +186,9 @@ struct GatherArgs {
     const T* quats;           // P x 4
     const T* trans;           // P x 3
     int64_t P;
-    const cplx<T>* G;         // two planes of n^d cells: (Phi, dPhi/dx), (dPhi/dy, dPhi/dz)
-    int n;
+    const cplx<T>* G;         // two planes of pn^d cells: (Phi, dPhi/dx), (dPhi/dy, dPhi/dz)
+    int n;                    // periodic grid size per axis
+    int pn;                   // pitch of the planes: n plus a halo of w cells repeating the field
     T inv_h, beta;
     int w;
     double* acc;              // P x 8

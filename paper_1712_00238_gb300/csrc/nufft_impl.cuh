@@ -872,11 +872,18 @@ __global__ void k_wtable(const cplx<T>* B1, const double* D, int N, int dim, dou
 }
 
 // Field f (0: Phi, 1-3: its gradient) of the type-2 tables into its plane:
-// plane f / 2 holds fields (2k, 2k + 1) of every cell side by side.
+// plane f / 2 holds fields (2k, 2k + 1) of every cell side by side, on a grid of
+// pitch pn >= n per axis whose cells past n repeat the periodic field (a halo,
+// so that a tap box starting inside [0, n) never needs wrapping).
 template <typename T>
-__global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f) {
+__global__ void k_interleave(const cplx<T>* src, cplx<T>* dst, int n, int pn, int dim, int f) {
+    const int64_t cells = (dim == 3) ? (int64_t)pn * pn * pn : (int64_t)pn * pn;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cells) dst[(f >> 1) * 2 * cells + 2 * i + (f & 1)] = src[i];
+    if (i >= cells) return;
+    const int x = (int)(i % pn), y = (int)((i / pn) % pn), z = (dim == 3) ? (int)(i / ((int64_t)pn * pn)) : 0;
+    const int sx = x < n ? x : x - n, sy = y < n ? y : y - n, sz = z < n ? z : z - n;
+    const int64_t si = (dim == 3) ? ((int64_t)sz * n + sy) * n + sx : (int64_t)sy * n + sx;
+    dst[(f >> 1) * 2 * cells + 2 * i + (f & 1)] = src[si];
 }
 
 template <typename T>
@@ -896,8 +903,9 @@ cudaError_t launch_wtable_t(const cplx<T>* B1, const double* D, int N, int dim, 
 }
 
 template <typename T>
-cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int64_t cells, int f, cudaStream_t st) {
-    k_interleave<T><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(src, dst, cells, f);
+cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn, int dim, int f, cudaStream_t st) {
+    const int64_t cells = (dim == 3) ? (int64_t)pn * pn * pn : (int64_t)pn * pn;
+    k_interleave<T><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(src, dst, n, pn, dim, f);
     note_launch();
     return cudaGetLastError();
 }
@@ -926,7 +934,8 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int64_t cells,
                                              double sg, int shift, int deriv, cplx<T>* W, cudaStream_t st) { \
         return launch_wtable_t<T>(B1, D, N, dim, L, sg, shift, deriv, W, st);                           \
     }                                                                                                   \
-    template <> cudaError_t launch_interleave<T>(const cplx<T>* s, cplx<T>* d, int64_t c, int f, cudaStream_t st) { \
-        return launch_interleave_t<T>(s, d, c, f, st);                                                  \
+    template <> cudaError_t launch_interleave<T>(const cplx<T>* s, cplx<T>* d, int n, int pn, int dim, int f,       \
+                                                 cudaStream_t st) {                                                 \
+        return launch_interleave_t<T>(s, d, n, pn, dim, f, st);                                         \
     }                                                                                                   \
     }
