@@ -68,7 +68,7 @@ typedef struct sd_params {
     double phi_radius;/* characteristic radius R of SD_PHI_RADIAL / SD_PHI_SKIN (> 0)   */
 } sd_params;
 
-/* phi-kernels (Section 4: Eq. 13 is a platform for several affinities).  g is
+/* phi-kernels (Section 4: Eq. 13 holds for any phi, each giving an affinity).  g is
  * the normalised Gaussian of width sigma_t, R = phi_radius, lambda = +lambda1
  * outside and -lambda2 inside (Eq. 16c).
  *   SD_PHI_SDF       Eq. 15 with the truncation of Eq. 17t: the skeletal density.
