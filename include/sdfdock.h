@@ -42,7 +42,7 @@ extern "C" {
 #define SD_ERR_OOM (-2)           /* device allocation failed                       */
 #define SD_ERR_CUDA (-3)          /* a CUDA runtime call or kernel launch failed    */
 #define SD_ERR_TIMEOUT (-4)       /* reserved: a bounded device wait gave up        */
-#define SD_ERR_UNIMPLEMENTED (-5) /* a valid request this build does not support    */
+#define SD_ERR_UNIMPLEMENTED (-5) /* a valid request this library does not support  */
 #define SD_ERR_NONFINITE (-6)     /* a result was NaN or infinite                   */
 
 #define SD_F32 0
