@@ -518,6 +518,39 @@ def test_maps_docking_grids(N, L, n1, n2):
     ctx.close()
 
 
+def test_maps_largest_grid_sampled_translations():
+    # N = 256 (512-point lines, the two-CTA register bound): the map at sampled
+    # translations, the GPU argmax among them, against the oracle's direct pair sums
+    fx_in, mv_in = configs.docking_pair(200, 60, 5)
+    rng = np.random.default_rng(256)
+    n1, n2 = 700, 300
+    p1 = fx_in.query.pos[np.sort(rng.choice(fx_in.query.m, n1, replace=False))]
+    p2 = mv_in.query.pos[np.sort(rng.choice(mv_in.query.m, n2, replace=False))]
+    c1 = synthetic_weights(n1, 7)
+    c2 = synthetic_weights(n2, 8)
+    N, L, sg = 256, 204.8, 0.6
+    ctx = sd.Context(3, "f32", 0, sigma_g=sg)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    quat = rotations.super_fibonacci(40)[[11]]
+    maps = ctx.score_maps(fx, mv, quats_dev(quat), sd.Grid(N, L)).cpu().numpy()[0]
+    cand = sd.decode_cands(ctx.score_rotations(fx, mv, quats_dev(quat), sd.Grid(N, L)))
+    top = int(cand[2][0].item())
+    assert top == int(np.argmax(maps.real))
+    # the top and translations within three cells of it (where the map is far from zero)
+    tz, ty, tx = top // (N * N), (top // N) % N, top % N
+    near = [((tz + dz) % N) * N * N + ((ty + dy) % N) * N + (tx + dx) % N
+            for dz, dy, dx in rng.integers(-3, 4, (8, 3))]
+    idx = np.concatenate([[top], near])
+    h = L / N
+    scale = np.abs(maps.real).max()
+    for i in idx:
+        t = np.array([i % N - N // 2, (i // N) % N - N // 2, i // (N * N) - N // 2], float) * h
+        ref = oscore.pair_score_fN(p1, c1, p2, c2, quat[0], t, N, L, sg)
+        assert abs(maps[i] - ref) < 1e-4 * scale, i
+    ctx.close()
+
+
 def test_sdf_docking_pair_sampled_points():
     fx_in, mv_in = configs.docking_pair(200, 60, 5)
     ctx = sd.Context(3, "f32", 0, sigma_g=0.6)
