@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
 // lie in the tile (not possible when the counting pass and this one agree, as
 // they evaluate the same function) is added with global atomics instead.
 template <int D, int W>
-__global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
+__global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
     constexpr int PS = SPREAD_BIN + W - 1;
     constexpr int PS2 = PS * PS;
     constexpr int CELLS = (D == 3) ? PS2 * PS : PS2;
@@ -331,21 +331,51 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
     constexpr int ROUNDS = (TAPS + 31) / 32;
     constexpr int REC = D * W + 4;  // D*W weights, c.x, c.y, tile offset (-1: outside), packed origin
     constexpr int NWARP = 8;
-    __shared__ float tre[CELLS];
-    __shared__ float tim[CELLS];
+    __shared__ int tre[CELLS];  // fixed point: value * scale
+    __shared__ int tim[CELLS];
     __shared__ float stage[NWARP * 32 * REC];
     __shared__ float Rm[9];
+    __shared__ float bsum[NWARP][2];
     const int b = blockIdx.y;
     const int t = blockIdx.x;
     const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
     const int lo = off[t], hi = off[t + 1];
     if (lo == hi) return;  // empty bin (uniform over the block)
     for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
-        tre[i] = 0.f;
-        tim[i] = 0.f;
+        tre[i] = 0;
+        tim[i] = 0;
     }
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
+    const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
+    // No tile cell exceeds sum_j |Re c_j| (resp. |Im c_j|) over the bin's samples,
+    // the kernel weights being at most 1: accumulate in fixed point with the
+    // power of two that keeps that bound below 2^30 (native integer atomics;
+    // each tap rounds by at most half a unit, and the sums are exact and
+    // independent of the order of the adds).
+    {
+        float sx = 0.f, sy = 0.f;
+        for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+            const float2 c = a.c[sorted[p]];
+            sx += fabsf(c.x);
+            sy += fabsf(c.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            bsum[threadIdx.x >> 5][0] = sx;
+            bsum[threadIdx.x >> 5][1] = sy;
+        }
+    }
     __syncthreads();
+    float bound = 0.f;
+    for (int w = 0; w < NWARP; ++w) bound = fmaxf(bound, fmaxf(bsum[w][0], bsum[w][1]));
+    // bound < 2^e2 with e2 from the exponent bits; scale = 2^(30 - e2), kept a normal float
+    const int e2 = ((__float_as_int(bound) >> 23) & 255) - 126;
+    const int se = bound > 0.f ? min(max(127 + 30 - e2, 1), 254) : 127;
+    const float scale = __int_as_float(se << 23);
+    const float inv_scale = 1.f / scale;  // a power of two: exact
     const int nb = bn.nb, s = a.s;
     const int org0[3] = {(t % nb) * SPREAD_BIN, ((t / nb) % nb) * SPREAD_BIN,
                          (D == 3) ? (t / (nb * nb)) * SPREAD_BIN : 0};
@@ -359,7 +389,6 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
         tap_of[q] = (kx + PS * ky + PS2 * kz) | (kx << 12) | (ky << 16) | (kz << 20);
     }
     float2* out = a.out + (int64_t)b * a.out_rot_stride;
-    const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
     constexpr int CHUNK = NWARP * 32;
     for (int p0 = lo; p0 < hi; p0 += CHUNK) {
         // every thread stages one sample of the chunk ...
@@ -396,6 +425,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
             const float cx = r[D * W], cy = r[D * W + 1];
             const int base = __float_as_int(r[D * W + 2]);
             if (base >= 0) {  // uniform over the warp
+                const float cxs = cx * scale, cys = cy * scale;
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
                     if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
@@ -403,17 +433,17 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
                         float w = r[(tp >> 12) & 15] * r[W + ((tp >> 16) & 15)];
                         if (D == 3) w *= r[2 * W + ((tp >> 20) & 15)];
                         const int cell = base + (tp & 4095);
-                        atomicAdd(tre + cell, cx * w);
-                        atomicAdd(tim + cell, cy * w);
+                        atomicAdd(tre + cell, __float2int_rn(cxs * w));
+                        atomicAdd(tim + cell, __float2int_rn(cys * w));
                     }
                 }
             } else {  // safety net (a tap box outside the tile): global atomics on the sub-box
                 const int packed = __float_as_int(r[D * W + 3]);
 #pragma unroll 1
                 for (int q = 0; q < ROUNDS; ++q) {
-                    if (q * 32 + lane < TAPS) {
-                        const int tp = tap_of[q];
-                        const int kx = (tp >> 12) & 15, ky = (tp >> 16) & 15, kz = (tp >> 20) & 15;
+                    const int tap = q * 32 + lane;
+                    if (tap < TAPS) {
+                        const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
                         float w = r[kx] * r[W + ky];
                         int64_t o = (int64_t)wrap_index(((packed >> 10) & 1023) + ky, s) * s +
                                     wrap_index((packed & 1023) + kx, s);
@@ -439,8 +469,9 @@ __global__ void __launch_bounds__(256) k_spread_tiles(SpreadArgs<float> a, BinAr
         const int xp = i % XP, row = i / XP;  // row = y + PS z
         const int x = 2 * xp;
         const int li = row * PS + x;
-        const float2 v0 = make_float2(tre[li], tim[li]);
-        const float2 v1 = (x + 1 < PS) ? make_float2(tre[li + 1], tim[li + 1]) : make_float2(0.f, 0.f);
+        const float2 v0 = make_float2((float)tre[li] * inv_scale, (float)tim[li] * inv_scale);
+        const float2 v1 = (x + 1 < PS) ? make_float2((float)tre[li + 1] * inv_scale, (float)tim[li + 1] * inv_scale)
+                                       : make_float2(0.f, 0.f);
         if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
         const int y = row % PS, z = row / PS;
         const int gx = org0[0] + x;
