@@ -125,7 +125,10 @@ int sd_destroy(sd_ctx* ctx);
  * sd_create. */
 const char* sd_last_error(const sd_ctx* ctx);
 
-/* Set a tuning option: "batch" (rotations per batch, 0 = automatic),
+/* A context serves one host thread at a time: calls on one context from
+ * several threads must be serialised by the caller.
+ *
+ * Set a tuning option: "batch" (rotations per batch, 0 = automatic),
  * "graph" (1: replay the batched launch sequence from a captured CUDA graph;
  * needs a non-NULL stream; the first call with given arguments runs eagerly,
  * later ones capture once and replay), "plain" (1: one rotation per batch, no

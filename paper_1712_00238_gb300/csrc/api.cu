@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <deque>
 #include <atomic>
 #include <map>
 #include <memory>
@@ -75,6 +76,7 @@ struct sd_ctx {
     double* gl_w = nullptr;
     int nq = 0;
     std::map<std::string, GraphEntry> graphs;
+    std::deque<std::string> graph_order;  // keys of `graphs`, oldest first
     std::map<std::string, int> seen;
 };
 
@@ -201,8 +203,29 @@ static void drop_graphs(sd_ctx* ctx) {
         cudaGraphExecDestroy(kv.second.exec);
         for (auto e : kv.second.events) cudaEventDestroy(e);
     }
+    ctx->graph_order.clear();
     ctx->graphs.clear();
     ctx->seen.clear();
+}
+
+// Keeps a newly captured graph; the cache holds at most 64, the oldest going
+// first (an executable graph or event still in flight is released when it
+// completes).  The first-call markers are bounded too.
+static std::map<std::string, GraphEntry>::iterator keep_graph(sd_ctx* ctx, const std::string& k,
+                                                             const GraphEntry& ge) {
+    constexpr size_t kMaxGraphs = 64;
+    while (ctx->graphs.size() >= kMaxGraphs && !ctx->graph_order.empty()) {
+        auto old = ctx->graphs.find(ctx->graph_order.front());
+        if (old != ctx->graphs.end()) {
+            cudaGraphExecDestroy(old->second.exec);
+            for (auto e : old->second.events) cudaEventDestroy(e);
+            ctx->graphs.erase(old);
+        }
+        ctx->graph_order.pop_front();
+    }
+    if (ctx->seen.size() > 4096) ctx->seen.clear();
+    ctx->graph_order.push_back(k);
+    return ctx->graphs.emplace(k, ge).first;
 }
 
 static int ws_get(sd_ctx* ctx, int slot, size_t bytes, void** out) {
@@ -942,7 +965,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
             ec = cudaGraphInstantiate(&ge.exec, graph, 0);
             cudaGraphDestroy(graph);
             CK(ctx, ec);
-            it = ctx->graphs.emplace(k, ge).first;
+            it = keep_graph(ctx, k, ge);
         }
         {
             PassTimer pt(ctx, SD_PASS_GRAPH, st, true);
@@ -1022,7 +1045,7 @@ static int run_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pa
             g_launches.fetch_sub(ge.kernels);  // counted when the graph runs
             if (rc == SD_OK) {
                 ge.events = evs;
-                it = ctx->graphs.emplace(k, ge).first;
+                it = keep_graph(ctx, k, ge);
             }
         }
         if (rc != SD_OK) {
