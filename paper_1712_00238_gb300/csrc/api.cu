@@ -447,6 +447,10 @@ static cudaError_t pass_last(int mode, const Geo& G, const Tw<T>& tw, const cplx
     c.twF = tw.n;
     c.twI = tw.N;
     c.W = W;
+    // W larger than a quarter of the 129 MB L2 would be evicted between rotations
+    // by the streaming data: let the batch's rotations share each block of it
+    const int64_t w_bytes = (int64_t)c.ncols * G.N * (int64_t)sizeof(cplx<T>);
+    c.rot_fastest = (mode == COL_FUSED && w_bytes > ((int64_t)32 << 20)) ? 1 : 0;
     return launch_cols<T>(mode, c, batch, st);
 }
 

@@ -125,6 +125,7 @@ struct ColArgs {
     const cplx<T>* twF;                 // twiddles of n (forward / expand)
     const cplx<T>* twI;                 // twiddles of N (inverse)
     const cplx<T>* W;                   // COL_FUSED: N x ncols table
+    int rot_fastest;                    // COL_FUSED: grid (batch, column blocks), W reused from L2
 };
 template <typename T> cudaError_t launch_cols(int mode, const ColArgs<T>& a, int batch, cudaStream_t st);
 

@@ -618,9 +618,14 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a) {
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* twF = buf + TC * LD;
     C* twI = twF + NTWF;
-    const int b = blockIdx.z;
-    const int outer = blockIdx.y;
-    const int col0 = blockIdx.x * TC;
+    // a fused pass whose W is too large to stay in L2 runs rotations fastest (grid
+    // (batch, column blocks)), so the CTAs that read one block of W for every
+    // rotation of a batch run together and W comes from L2; every other pass runs
+    // column blocks fastest (grid (blocks, outer, batch))
+    const bool rf = MODE == COL_FUSED && a.rot_fastest;
+    const int b = rf ? (int)blockIdx.x : (int)blockIdx.z;
+    const int outer = rf ? 0 : (int)blockIdx.y;
+    const int col0 = (rf ? (int)blockIdx.y : (int)blockIdx.x) * TC;
     for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
     if constexpr (MODE == COL_FUSED)
         for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
@@ -741,7 +746,10 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     else kern = k_cols<T, LENF, LENI, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LENF>(), smem, st>>>(a);
+    const bool rf = MODE == COL_FUSED && a.rot_fastest;
+    const dim3 grid = rf ? dim3(batch, nb, 1) : dim3(nb, a.nouter, batch);
+    if (rf && (a.nouter != 1 || nb > 65535)) return cudaErrorInvalidValue;
+    kern<<<grid, cta_threads<T, LENF>(), smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
