@@ -402,7 +402,7 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("peg_in_bore_3d",
                                                                                   "peg_in_hole_2d"):
-        result["cpu_baseline"] = cpu_baseline(w, 2 if w.dim == 3 else w.n_rot)
+        result["cpu_baseline"] = cpu_baseline(w, 4 if w.dim == 3 else w.n_rot)
     if rank == 0:
         print(json.dumps(result), flush=True)
     ctx.close()
