@@ -334,3 +334,25 @@ def test_rotation_sets():
     assert len(g) == 576
     ang = 2 * np.arccos(np.clip(np.abs(g @ g.T), 0, 1)) + 4 * np.eye(len(g))
     assert ang.min() > np.deg2rad(10)        # distinct rotations, none repeated
+
+
+def test_optimum_score_trends_of_section_6():
+    # Section 6's parameter study, as loose behaviour checks on the 2D peg-in-hole pair at
+    # the inserted pose: the optimal score scales roughly like 1 / sigma_t, and at a fixed
+    # product lambda1 lambda2 it hardly depends on the penalty factor lambda2 / lambda1 >= 3
+    w = configs.peg_in_hole_2d()
+
+    def f_opt(lam1, lam2, st):
+        cs = []
+        for s in (w.fixed, w.moving):
+            b = s.boundary
+            cs.append(sdf.sdf_rho(s.query.pos, b.pos, b.normal, b.area, lam1, lam2, st, 1.5) * s.query.vol)
+        return score.pair_score_fc(w.fixed.query.pos, cs[0], w.moving.query.pos, cs[1],
+                                    np.array([1.0, 0, 0, 0]), np.zeros(2), w.sigma_g).real
+
+    f = {st: f_opt(1.0, 3.0, st) for st in (0.25, 0.5, 1.0)}
+    assert 1.5 < f[0.25] / f[0.5] < 2.5 and 1.5 < f[0.5] / f[1.0] < 2.5
+    base = f[0.5]
+    for pen in (6.0, 12.0):
+        g = f_opt(np.sqrt(3.0 / pen), np.sqrt(3.0 * pen), 0.5)
+        assert abs(g - base) <= 0.01 * abs(base)
