@@ -225,8 +225,9 @@ typedef struct sd_pair_stat {
  * problems).  Each job runs with its own plan (autotuned when the "autotune"
  * option is on); the workspace is sized once for the largest job.  The first
  * call with a given job list runs eagerly; later calls with the same list
- * replay one captured CUDA graph holding every job.  Results equal
- * sd_score_rotations on each job.
+ * replay one captured CUDA graph holding every job.  Each job's candidates
+ * are those of sd_score_rotations on it, up to the FP32 rounding of the
+ * spreading's atomic order (its plan may differ).
  *   jobs   host, n_jobs sd_pair_job; pointers inside stay valid while the
  *          context may replay the graph (until sd_shape_free or sd_destroy)
  *   stats  host, n_jobs sd_pair_stat, or NULL.  When given, the call
