@@ -6,7 +6,11 @@ stream, and turns error codes into exceptions.  There is no CPU fallback: if the
 library cannot be loaded, the calls raise.
 
 Names follow the C ABI of include/sdfdock.h: sdf_build, score_rotations,
-score_maps, top_k_poses, score_grad.
+score_maps, top_k_poses, score_grad, score_pairs, refine, search_plan,
+tune_export / tune_import.  Pose refinement comes three ways: Context.refine
+(sd_refine: ascent, conjugate gradient or damped dynamics, all on the device),
+Context.refine_poses (its ascent rule) and the module-level refine_poses, the
+same ascent written as a PyTorch loop over the SdfScore autograd Function.
 """
 
 from __future__ import annotations
