@@ -78,3 +78,23 @@ def test_rotation_sharding_covers_all():
             spans = [sdfdock.shard_range(n, world, r) for r in range(world)]
             assert spans[0][0] == 0 and spans[-1][1] == n
             assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 with every type it declares
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text('#include "sdfdock.h"\n'
+                   "int main(void) { sd_params p; sd_grid g; sd_cand c; sd_pose o; sd_pair_job j;\n"
+                   "  sd_pair_stat s; sd_refine_params r;\n"
+                   "  (void)p; (void)g; (void)c; (void)o; (void)j; (void)s; (void)r;\n"
+                   "  return SD_OK + SD_F32 + SD_PHI_SDF + SD_REFINE_ASCENT; }\n")
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", include,
+                        "-fsyntax-only", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
