@@ -458,6 +458,27 @@ def test_native_refinement_follows_autograd_path(prec):
 # errors
 # ---------------------------------------------------------------------------
 
+def test_degenerate_inputs():
+    # an empty rotation list writes nothing; a one-sample moving shape still matches the oracle
+    w = configs.tiny_3d()
+    rng = np.random.default_rng(91)
+    p1 = w.fixed.query.pos
+    c1 = rng.standard_normal(len(p1)) + 1j * rng.standard_normal(len(p1))
+    p2 = np.array([[0.3, -0.2, 0.1]])
+    c2 = np.array([0.7 - 0.4j])
+    ctx = make_ctx(w)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    empty = torch.empty((0, 4), dtype=torch.float64, device="cuda")
+    assert ctx.score_rotations(fx, mv, empty, grid_of(w, 16)).shape[0] == 0
+    quats = rotations.super_fibonacci(40)[[0, 9]]
+    maps = ctx.score_maps(fx, mv, quats_dev(quats), grid_of(w, 16)).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, quats, 16, w.L, w.sigma_g)
+    for r in range(2):
+        assert rel_err(maps[r], ref[r]) < 1e-4
+    ctx.close()
+
+
 def test_argument_errors_are_reported():
     w = configs.tiny_3d()
     p1, c1, p2, c2 = oracle_weights("tiny_3d")
