@@ -15,9 +15,11 @@ score  Eq. 1 / Eq. 8: the pair-sum score of Gaussian-represented SDFs, its
 refine Section 6: force and torque of the virtual energy E ~ -f, and the pose
        updates that climb the score (gradient ascent, conjugate gradient,
        damped rigid-body dynamics).
+octree Section 5: adaptive tree sampling of the SDF, subdivided deepest where the
+       skeletal density (the weight of a cell) is high.
 
 Every function is pinned by tests under tests/ (closed forms, invariances,
 brute force).  Absolute SDF and score values of the synthetic workloads have no
 printed counterpart in the paper: parity unpinned beyond those checks.
 """
-from . import refine, score, sdf  # noqa: F401
+from . import octree, refine, score, sdf  # noqa: F401
