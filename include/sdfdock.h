@@ -178,6 +178,56 @@ int sd_shape_info(const sd_shape* s, int64_t* m, double* radius);
 /* Free a shape and its cached spectra; NULL is accepted. */
 int sd_shape_free(sd_shape* s);
 
+/* ---- adaptive sampling of the SDF (Section 5, octree) ------------------ */
+
+/* Section 5 proposes sampling the SDF on a tree subdivided deepest where the
+ * skeletal density is high, instead of a uniform grid, and scoring the
+ * nonequispaced samples with a nonequispaced FFT (which the search above is).
+ * sd_octree builds such a tree (a quadtree in 2D) on the HOST, one level at a
+ * time, from SDF values the caller evaluates -- normally with sd_sdf_build's
+ * rho_out at the centres sd_octree_pending lists.  Needs no GPU.
+ *
+ * Rule: the root is the cube [lo, lo + size]^dim, cut uniformly into
+ * 2^depth_min cells per axis.  A cell of side h = size / 2^D at depth
+ * D < depth_max, centre c, is split into its 2^dim children when the boundary
+ * sample nearest c lies closer than half the cell's diagonal (0.5 h sqrt(dim)),
+ * or else when |rho(c)| h^dim >= tau.  Cells not split are leaves (position c,
+ * volume h^dim), except that a leaf whose centre lies closer than `clearance`
+ * to a boundary sample is dropped.  Leaves are listed by depth, then by the
+ * linear index k_x + 2^D (k_y + 2^D k_z) of their integer coordinates
+ * k = (c - lo) / h - 1/2.  tau = 0 gives the uniform grid at depth_max.
+ *
+ *   bnd        host, n_b x 4 double: boundary sample positions (x, y, z, pad);
+ *              n_b = 0 (bnd may be NULL) means no boundary; copied
+ *   lo         host, dim doubles: the root's lowest corner
+ *   depth_min <= depth_max <= 20
+ * Errors: SD_ERR_ARG for bad arguments, SD_ERR_NONFINITE for a non-finite
+ * boundary position, SD_ERR_OOM when a level would exceed 2^27 cells or memory
+ * runs out; *out is NULL then.  Not thread-safe per tree. */
+typedef struct sd_octree sd_octree;
+int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, double size, int depth_min,
+                     int depth_max, double tau, double clearance, sd_octree** out);
+
+/* The cells of the current level that need rho: *n of them (0 once the tree
+ * is complete).  centres (host, n x 4 double, or NULL) receives their centres
+ * (x, y, z, 0), vol (host, n double, or NULL) their volumes h^dim. */
+int sd_octree_pending(const sd_octree* t, int64_t* n, double* centres, double* vol);
+
+/* Feed rho at the pending centres (host, n x 2 double: re, im, in the order
+ * sd_octree_pending listed them) and resolve levels until rho is needed again
+ * or the tree is complete.  n must equal the pending count (SD_ERR_ARG);
+ * a non-finite value returns SD_ERR_NONFINITE and leaves the tree unchanged;
+ * SD_ERR_OOM (level too large) leaves the tree unusable. */
+int sd_octree_feed(sd_octree* t, const double* rho, int64_t n);
+
+/* The leaves of a complete tree (SD_ERR_ARG before): *m of them; centres
+ * (host, m x 4 double), vol (host, m double) and coords (host, m x 4 int32:
+ * k_x, k_y, k_z, depth) may each be NULL. */
+int sd_octree_leaves(const sd_octree* t, int64_t* m, double* centres, double* vol, int32_t* coords);
+
+/* Free a tree; NULL is accepted. */
+int sd_octree_free(sd_octree* t);
+
 /* ---- search over rotations x translations (Section 5) ------------------ */
 
 /* For each rotation r, the best translation of Re f_N(R_r, t) over the grid.

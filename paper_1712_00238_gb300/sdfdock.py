@@ -7,7 +7,8 @@ library cannot be loaded, the calls raise.
 
 Names follow the C ABI of include/sdfdock.h: sdf_build, score_rotations,
 score_maps, top_k_poses, score_grad, score_pairs, refine, search_plan,
-tune_export / tune_import.  Pose refinement comes three ways: Context.refine
+tune_export / tune_import, and the host-side adaptive sampling tree (Octree,
+Context.sdf_build_octree).  Pose refinement comes three ways: Context.refine
 (sd_refine: ascent, conjugate gradient or damped dynamics, all on the device),
 Context.refine_poses (its ascent rule) and the module-level refine_poses, the
 same ascent written as a PyTorch loop over the SdfScore autograd Function.
@@ -20,6 +21,7 @@ import math
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -118,6 +120,12 @@ _SIGS = {
                                    ct.c_void_p]),
     "sd_refine": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p, ct.c_void_p,
                              ct.c_int64, ct.c_int, ct.POINTER(sd_refine_params), ct.c_void_p, ct.c_void_p]),
+    "sd_octree_create": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_double, ct.c_int, ct.c_int,
+                                    ct.c_double, ct.c_double, ct.POINTER(ct.c_void_p)]),
+    "sd_octree_pending": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p, ct.c_void_p]),
+    "sd_octree_feed": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64]),
+    "sd_octree_leaves": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "sd_octree_free": (ct.c_int, [ct.c_void_p]),
     "sd_host_line_fft": (ct.c_int, [ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_version": (ct.c_char_p, []),
     "sd_launch_count": (ct.c_int64, []),
@@ -284,6 +292,34 @@ class Context:
         self.shapes.append(s)
         return (s, rho) if return_rho else s
 
+    def sdf_build_octree(self, bnd, nrm, area, lo, size: float, depth_min: int, depth_max: int, tau: float,
+                         clearance: float, return_leaves: bool = False):
+        """Sampled SDF on an adaptive tree (Section 5): sd_octree levels, rho by sd_sdf_build.
+
+        Each level's pending centres are evaluated on the device and their rho
+        fed back to the host tree; the leaves then become the shape's samples.
+        With ``return_leaves`` also returns (centres, volumes, coords, rho) of
+        the leaves (host arrays; rho as a device tensor)."""
+        # the tree measures distances to the boundary samples as given, in FP64
+        tree = Octree(self.dim, torch.as_tensor(bnd).double().cpu().numpy(), lo, size, depth_min, depth_max, tau,
+                      clearance)
+        bnd = self._dev(bnd, cols=4)
+        nrm = self._dev(nrm, cols=4)
+        area = self._dev(area)
+        try:
+            while True:
+                cen, vol = tree.pending()
+                if len(cen) == 0:
+                    break
+                part, rho = self.sdf_build(bnd, nrm, area, cen, vol, return_rho=True)
+                part.free()
+                tree.feed(rho.double().cpu().numpy())
+            cen, vol, crd = tree.leaves()
+        finally:
+            tree.close()
+        shape, rho = self.sdf_build(bnd, nrm, area, cen, vol, return_rho=True)
+        return (shape, (cen, vol, crd, rho)) if return_leaves else shape
+
     def shape_from_samples(self, pos, c) -> Shape:
         pos = self._dev(pos, cols=4)
         c = self._dev(c, cols=2)
@@ -418,6 +454,76 @@ class Context:
         self._check(self.lib.sd_refine(self.handle, fixed.handle, moving.handle, ct.byref(g), _ptr(q), _ptr(t), P,
                                        int(steps), ct.byref(rp), _ptr(hist), _stream(self.device)))
         return q, t[:, : self.dim], hist
+
+
+class Octree:
+    """Host-side adaptive tree of SDF sample cells (sd_octree_*); needs no GPU."""
+
+    def __init__(self, dim: int, bnd, lo, size: float, depth_min: int, depth_max: int, tau: float,
+                 clearance: float):
+        self.lib = load()
+        b = np.asarray(bnd, dtype=np.float64)
+        if b.ndim != 2:
+            raise ValueError("bnd: expected an (n_b, dim..4) array")
+        if b.shape[1] < 4:
+            b = np.concatenate([b, np.zeros((b.shape[0], 4 - b.shape[1]))], 1)
+        b = np.ascontiguousarray(b[:, :4])
+        lo = np.ascontiguousarray(np.asarray(lo, dtype=np.float64).reshape(-1))
+        if lo.shape[0] < dim:
+            raise ValueError("lo: expected dim values")
+        self.dim = dim
+        self.handle = ct.c_void_p()
+        rc = self.lib.sd_octree_create(dim, b.ctypes.data if len(b) else None, b.shape[0], lo.ctypes.data,
+                                       float(size), depth_min, depth_max, float(tau), float(clearance),
+                                       ct.byref(self.handle))
+        if rc != SD_OK:
+            raise SdError(rc, "octree_create failed")
+
+    def _check(self, rc, what):
+        if rc != SD_OK:
+            raise SdError(rc, f"octree_{what} failed")
+
+    def pending(self):
+        """Centres (n, 4) and volumes (n,) of the cells that need rho."""
+        n = ct.c_int64()
+        self._check(self.lib.sd_octree_pending(self.handle, ct.byref(n), None, None), "pending")
+        cen = np.zeros((n.value, 4))
+        vol = np.zeros(n.value)
+        if n.value:
+            self._check(self.lib.sd_octree_pending(self.handle, ct.byref(n), cen.ctypes.data, vol.ctypes.data),
+                        "pending")
+        return cen, vol
+
+    def feed(self, rho):
+        """rho at the pending centres: (n, 2) real pairs, (n,) complex or (n,) real."""
+        r = np.asarray(rho)
+        if np.iscomplexobj(r) or r.ndim == 1:
+            r = np.stack([r.real, np.imag(r)], -1)
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 2)
+        self._check(self.lib.sd_octree_feed(self.handle, r.ctypes.data if len(r) else None, r.shape[0]), "feed")
+
+    def leaves(self):
+        """Centres (m, 4), volumes (m,) and int32 coords (m, 4: k_x, k_y, k_z, depth) of the leaves."""
+        m = ct.c_int64()
+        self._check(self.lib.sd_octree_leaves(self.handle, ct.byref(m), None, None, None), "leaves")
+        cen = np.zeros((m.value, 4))
+        vol = np.zeros(m.value)
+        crd = np.zeros((m.value, 4), np.int32)
+        if m.value:
+            self._check(self.lib.sd_octree_leaves(self.handle, ct.byref(m), cen.ctypes.data, vol.ctypes.data,
+                                                  crd.ctypes.data), "leaves")
+        return cen, vol, crd
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sd_octree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:
