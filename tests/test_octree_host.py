@@ -40,10 +40,11 @@ def _drive(tree, rho_fn, dim):
     return asked
 
 
-@pytest.mark.parametrize("case", [("tiny_2d", "moving", 2, 7, 2e-3), ("tiny_2d", "fixed", 2, 7, 2e-2),
-                                  ("tiny_3d", "moving", 1, 4, 2e-2)])
+@pytest.mark.parametrize("case", [("tiny_2d", "moving", 2, 7, 2e-3, 0.2), ("tiny_2d", "fixed", 2, 7, 2e-2, 0.2),
+                                  ("tiny_3d", "moving", 1, 4, 2e-2, 0.2),
+                                  ("tiny_2d", "moving", 0, 8, 2e-3, 3.0)])   # root far larger than the shape
 def test_tree_equals_oracle_tree(lib, case):
-    name, which, d_min, d_max, tau = case
+    name, which, d_min, d_max, tau, pad = case
     w = getattr(configs, name)()
     s = getattr(w, which)
     b = s.boundary
@@ -55,7 +56,7 @@ def test_tree_equals_oracle_tree(lib, case):
     def xi_fn(p):
         return osdf.nearest_distance(p, b.pos)
 
-    lo, size = _box(s)
+    lo, size = _box(s, pad)
     c, v, k, d, asked = ooct.octree_leaves(rho_fn, xi_fn, lo, size, w.dim, d_min, d_max, tau, b.spacing)
     tree = sd.Octree(w.dim, b.pos, lo, size, d_min, d_max, tau, b.spacing)
     got_asked = _drive(tree, rho_fn, w.dim)
@@ -87,12 +88,11 @@ def test_argument_errors(lib):
     lo = np.zeros(3)
     b = np.zeros((4, 4))
     b[:, 0] = np.arange(4)
-    ok = dict(dim=3, depth_min=1, depth_max=3)
 
     def create(dim=3, bp=b.ctypes.data, n=4, size=1.0, dmin=1, dmax=3, tau=0.1, clear=0.0):
         return lib.sd_octree_create(dim, bp, n, lo.ctypes.data, size, dmin, dmax, tau, clear, ct.byref(h))
 
-    assert ok and create() == sd.SD_OK
+    assert create() == sd.SD_OK
     lib.sd_octree_free(h)
     for bad in (dict(dim=4), dict(n=-1), dict(bp=None), dict(size=0.0), dict(size=float("inf")), dict(dmin=4),
                 dict(dmax=21), dict(tau=float("nan")), dict(tau=-1.0), dict(clear=-0.1)):
