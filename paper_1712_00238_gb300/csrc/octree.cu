@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -248,7 +249,7 @@ int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, 
         for (int a = 0; a < dim; ++a)
             if (!std::isfinite(bnd[4 * i + a])) return SD_ERR_NONFINITE;
     try {
-        sd_octree* t = new sd_octree();
+        std::unique_ptr<sd_octree> t(new sd_octree());
         t->dim = dim;
         t->d_min = depth_min;
         t->d_max = depth_max;
@@ -262,11 +263,8 @@ int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, 
         t->keys.resize((size_t)n0);
         for (int64_t i = 0; i < n0; ++i) t->keys[(size_t)i] = i;  // the uniform level is already in key order
         const int rc = t->settle();
-        if (rc != SD_OK) {
-            delete t;
-            return rc;
-        }
-        *out = t;
+        if (rc != SD_OK) return rc;
+        *out = t.release();
         return SD_OK;
     } catch (const std::bad_alloc&) {
         return SD_ERR_OOM;
