@@ -313,6 +313,7 @@ class Context:
                     break
                 part, rho = self.sdf_build(bnd, nrm, area, cen, vol, return_rho=True)
                 part.free()
+                self.shapes.remove(part)
                 tree.feed(rho.double().cpu().numpy())
             cen, vol, crd = tree.leaves()
         finally:
