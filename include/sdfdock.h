@@ -182,7 +182,7 @@ int sd_shape_free(sd_shape* s);
 
 /* Section 5 proposes sampling the SDF on a tree subdivided deepest where the
  * skeletal density is high, instead of a uniform grid, and scoring the
- * nonequispaced samples with a nonequispaced FFT (which the search above is).
+ * nonequispaced samples with a nonequispaced FFT (what sd_score_rotations runs).
  * sd_octree builds such a tree (a quadtree in 2D) on the HOST, one level at a
  * time, from SDF values the caller evaluates -- normally with sd_sdf_build's
  * rho_out at the centres sd_octree_pending lists.  Needs no GPU.
