@@ -22,6 +22,11 @@ reading restated here:
   except that a leaf whose centre lies closer than ``clearance`` to a boundary
   sample is dropped (the same rule that keeps uniform query points off the
   boundary's single-sample singularity);
+* optionally the samples are kept to a band around the boundary, like the
+  uniform query sets: a leaf whose centre lies farther than ``band`` from the
+  boundary is dropped, and a cell whose centre lies farther than ``band`` plus
+  half its diagonal (so that all of it lies beyond the band, the distance to
+  the boundary being 1-Lipschitz) is dropped without being split or evaluated;
 * leaves are listed by depth, then by the linear index
   k_x + 2^D (k_y + 2^D k_z) of their coordinates.
 
@@ -44,7 +49,7 @@ def _sorted_level(k, D):
     return k[np.argsort(lin, kind="stable")]
 
 
-def octree_leaves(rho_fn, xi_fn, lo, size, dim, d_min, d_max, tau, clearance):
+def octree_leaves(rho_fn, xi_fn, lo, size, dim, d_min, d_max, tau, clearance, band=np.inf):
     """Leaves of the adaptive tree, level by level.
 
     ``rho_fn(points) -> complex rho`` and ``xi_fn(points) -> |xi|`` (distance to
@@ -64,14 +69,16 @@ def octree_leaves(rho_fn, xi_fn, lo, size, dim, d_min, d_max, tau, clearance):
         h = size / (1 << D)
         c = lo + (k + 0.5) * h
         xi = xi_fn(c)
+        half_diag = 0.5 * h * math.sqrt(dim)
+        beyond = xi - half_diag > band
         split = np.zeros(len(k), bool)
         if D < d_max:
-            split = xi < 0.5 * h * math.sqrt(dim)
-            ask = ~split
+            split = xi < half_diag
+            ask = ~split & ~beyond
             asked.append(c[ask])
             if ask.any():
                 split[ask] = np.abs(rho_fn(c[ask])) * h ** dim >= tau
-        leaf = ~split & (xi >= clearance)
+        leaf = ~split & ~beyond & (xi >= clearance) & (xi <= band)
         cen.append(c[leaf])
         vol.append(np.full(int(leaf.sum()), h ** dim))
         crd.append(k[leaf])

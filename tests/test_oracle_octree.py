@@ -100,3 +100,28 @@ def test_midpoint_rule_is_exact_for_affine_density():
     # where the density is large the cube is sampled deeper
     w = np.abs(rho_fn(c))
     assert np.mean(d[w > np.median(w)]) > np.mean(d[w < np.median(w)])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_band_keeps_exactly_the_leaves_within_it(dim):
+    # a cell dropped as lying wholly beyond the band has only descendants beyond it,
+    # so the banded tree is the full tree's leaves filtered by centre distance
+    rng = np.random.default_rng(21 + dim)
+    q = rng.normal(size=(80, dim))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    lo, size, band = np.full(dim, -2.3), 4.7, 0.35
+
+    def xi_fn(p):
+        return np.linalg.norm(p[:, None, :] - q[None], axis=2).min(1)
+
+    def rho_fn(p):
+        return 1.0 / (0.05 + np.abs(np.linalg.norm(p, axis=1) - 1.0)) + 0j
+
+    args = (rho_fn, xi_fn, lo, size, dim, 1, 6 if dim == 2 else 4, 4e-3, 0.05)
+    c0, v0, k0, d0, a0 = ooct.octree_leaves(*args)
+    c1, v1, k1, d1, a1 = ooct.octree_leaves(*args, band=band)
+    keep = xi_fn(c0) <= band
+    assert 0 < keep.sum() < len(keep)
+    assert np.array_equal(c1, c0[keep]) and np.array_equal(d1, d0[keep]) and np.array_equal(k1, k0[keep])
+    assert np.all(xi_fn(c1) <= band) and np.all(xi_fn(c1) >= 0.05)
+    assert sum(len(a) for a in a1) < sum(len(a) for a in a0)
