@@ -193,7 +193,10 @@ int sd_shape_free(sd_shape* s);
  * sample nearest c lies closer than half the cell's diagonal (0.5 h sqrt(dim)),
  * or else when |rho(c)| h^dim >= tau.  Cells not split are leaves (position c,
  * volume h^dim), except that a leaf whose centre lies closer than `clearance`
- * to a boundary sample is dropped.  Leaves are listed by depth, then by the
+ * to a boundary sample is dropped, and so is a leaf whose centre lies farther
+ * than `band` from it; a cell whose centre lies farther than band + 0.5 h sqrt(dim)
+ * lies wholly beyond the band and is dropped without being split or evaluated
+ * (band = INFINITY keeps everything).  Leaves are listed by depth, then by the
  * linear index k_x + 2^D (k_y + 2^D k_z) of their integer coordinates
  * k = (c - lo) / h - 1/2.  tau = 0 gives the uniform grid at depth_max.
  *
@@ -206,7 +209,7 @@ int sd_shape_free(sd_shape* s);
  * runs out; *out is NULL then.  Not thread-safe per tree. */
 typedef struct sd_octree sd_octree;
 int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, double size, int depth_min,
-                     int depth_max, double tau, double clearance, sd_octree** out);
+                     int depth_max, double tau, double clearance, double band, sd_octree** out);
 
 /* The cells of the current level that need rho: *n of them (0 once the tree
  * is complete).  centres (host, n x 4 double, or NULL) receives their centres

@@ -6,7 +6,8 @@
 // host, one level at a time: cells whose centre lies within half a diagonal of
 // the nearest boundary sample are split outright; the others ask the caller for
 // rho at their centres (evaluated on the device by sd_sdf_build) and are split
-// when their weight |rho| h^d reaches tau.  Leaves become the SDF samples.
+// when their weight |rho| h^d reaches tau.  Leaves become the SDF samples;
+// optionally only those within a band around the boundary.
 //
 // Nearest boundary distances come from a uniform bucket grid over the boundary
 // samples searched in growing Chebyshev shells, exact below the radius a level
@@ -129,12 +130,13 @@ struct BucketGrid {
 struct sd_octree {
     int dim = 3, d_min = 0, d_max = 0, D = 0;
     double lo[3] = {0, 0, 0};
-    double size = 1.0, tau = 0.0, clear = 0.0;
+    double size = 1.0, tau = 0.0, clear = 0.0, band = INFINITY;
     bool done = false, failed = false;
     BucketGrid grid;
     std::vector<int64_t> keys;   // cells of level D, sorted
     std::vector<double> xi;      // nearest boundary distance per cell
     std::vector<uint8_t> split;  // split decision per cell
+    std::vector<uint8_t> beyond; // cell lies wholly beyond the band
     std::vector<int64_t> ask;    // cells of level D that need rho
     std::vector<double> leaf_c, leaf_v;
     std::vector<int32_t> leaf_k;
@@ -155,22 +157,28 @@ struct sd_octree {
         for (int a = 0; a < 3; ++a) c[a] = a < dim ? lo[a] + ((double)k[a] + 0.5) * h : 0.0;
     }
 
-    // distances and outright splits of the current level; records which cells need rho
+    // distances, outright splits and cells beyond the band of the current level;
+    // records which cells need rho.  The distance to the boundary is 1-Lipschitz,
+    // so a cell whose centre lies farther than band + r holds no point within the band.
     void examine() {
         const double h = side();
         const double r = 0.5 * h * std::sqrt((double)dim);
-        const double cap = std::max(r, clear) * (1.0 + 1e-12) + 1e-300;
+        double cap = std::max(r, clear);
+        if (std::isfinite(band)) cap = std::max(cap, band + r);
+        cap = cap * (1.0 + 1e-12) + 1e-300;
         xi.assign(keys.size(), 0.0);
         split.assign(keys.size(), 0);
+        beyond.assign(keys.size(), 0);
         ask.clear();
         for (size_t i = 0; i < keys.size(); ++i) {
             double c[3];
             centre(keys[i], c);
             xi[i] = grid.nearest(c, cap);
+            beyond[i] = xi[i] - r > band ? 1 : 0;
             if (D < d_max) {
                 if (xi[i] < r)
                     split[i] = 1;
-                else
+                else if (!beyond[i])
                     ask.push_back((int64_t)i);
             }
         }
@@ -186,7 +194,7 @@ struct sd_octree {
                 ++n_split;
                 continue;
             }
-            if (!(xi[i] >= clear)) continue;
+            if (beyond[i] || !(xi[i] >= clear) || !(xi[i] <= band)) continue;
             double c[3];
             centre(keys[i], c);
             int64_t k[3];
@@ -235,11 +243,12 @@ struct sd_octree {
 extern "C" {
 
 int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, double size, int depth_min,
-                     int depth_max, double tau, double clearance, sd_octree** out) {
+                     int depth_max, double tau, double clearance, double band, sd_octree** out) {
     if (!out) return SD_ERR_ARG;
     *out = nullptr;
     if ((dim != 2 && dim != 3) || n_b < 0 || (n_b > 0 && !bnd) || !lo) return SD_ERR_ARG;
-    if (!(size > 0.0) || !std::isfinite(size) || !(tau >= 0.0) || !(clearance >= 0.0) || !std::isfinite(clearance))
+    if (!(size > 0.0) || !std::isfinite(size) || !(tau >= 0.0) || !(clearance >= 0.0) || !std::isfinite(clearance) ||
+        !(band >= 0.0))
         return SD_ERR_ARG;
     if (depth_min < 0 || depth_max < depth_min || depth_max > kMaxDepth) return SD_ERR_ARG;
     if ((int64_t)depth_min * dim > kMaxCellsLog2) return SD_ERR_OOM;
@@ -258,6 +267,7 @@ int sd_octree_create(int dim, const double* bnd, int64_t n_b, const double* lo, 
         t->size = size;
         t->tau = tau;
         t->clear = clearance;
+        t->band = band;
         t->grid.build(bnd, n_b, dim);
         const int64_t n0 = int64_t(1) << (depth_min * dim);
         t->keys.resize((size_t)n0);

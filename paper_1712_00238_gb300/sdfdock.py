@@ -121,7 +121,7 @@ _SIGS = {
     "sd_refine": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_void_p, ct.c_void_p,
                              ct.c_int64, ct.c_int, ct.POINTER(sd_refine_params), ct.c_void_p, ct.c_void_p]),
     "sd_octree_create": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_double, ct.c_int, ct.c_int,
-                                    ct.c_double, ct.c_double, ct.POINTER(ct.c_void_p)]),
+                                    ct.c_double, ct.c_double, ct.c_double, ct.POINTER(ct.c_void_p)]),
     "sd_octree_pending": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p, ct.c_void_p]),
     "sd_octree_feed": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64]),
     "sd_octree_leaves": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -293,7 +293,7 @@ class Context:
         return (s, rho) if return_rho else s
 
     def sdf_build_octree(self, bnd, nrm, area, lo, size: float, depth_min: int, depth_max: int, tau: float,
-                         clearance: float, return_leaves: bool = False):
+                         clearance: float, return_leaves: bool = False, band: float = math.inf):
         """Sampled SDF on an adaptive tree (Section 5): sd_octree levels, rho by sd_sdf_build.
 
         Each level's pending centres are evaluated on the device and their rho
@@ -302,7 +302,7 @@ class Context:
         the leaves (host arrays; rho as a device tensor)."""
         # the tree measures distances to the boundary samples as given, in FP64
         tree = Octree(self.dim, torch.as_tensor(bnd).double().cpu().numpy(), lo, size, depth_min, depth_max, tau,
-                      clearance)
+                      clearance, band)
         bnd = self._dev(bnd, cols=4)
         nrm = self._dev(nrm, cols=4)
         area = self._dev(area)
@@ -461,7 +461,7 @@ class Octree:
     """Host-side adaptive tree of SDF sample cells (sd_octree_*); needs no GPU."""
 
     def __init__(self, dim: int, bnd, lo, size: float, depth_min: int, depth_max: int, tau: float,
-                 clearance: float):
+                 clearance: float, band: float = math.inf):
         self.lib = load()
         b = np.asarray(bnd, dtype=np.float64)
         if b.ndim != 2:
@@ -476,7 +476,7 @@ class Octree:
         self.handle = ct.c_void_p()
         rc = self.lib.sd_octree_create(dim, b.ctypes.data if len(b) else None, b.shape[0], lo.ctypes.data,
                                        float(size), depth_min, depth_max, float(tau), float(clearance),
-                                       ct.byref(self.handle))
+                                       float(band), ct.byref(self.handle))
         if rc != SD_OK:
             raise SdError(rc, "octree_create failed")
 

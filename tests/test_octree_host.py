@@ -40,11 +40,16 @@ def _drive(tree, rho_fn, dim):
     return asked
 
 
-@pytest.mark.parametrize("case", [("tiny_2d", "moving", 2, 7, 2e-3, 0.2), ("tiny_2d", "fixed", 2, 7, 2e-2, 0.2),
-                                  ("tiny_3d", "moving", 1, 4, 2e-2, 0.2),
-                                  ("tiny_2d", "moving", 0, 8, 2e-3, 3.0)])   # root far larger than the shape
+INF = float("inf")
+
+
+@pytest.mark.parametrize("case", [("tiny_2d", "moving", 2, 7, 2e-3, 0.2, INF), ("tiny_2d", "fixed", 2, 7, 2e-2, 0.2, INF),
+                                  ("tiny_3d", "moving", 1, 4, 2e-2, 0.2, INF),
+                                  ("tiny_2d", "moving", 0, 8, 2e-3, 3.0, INF),   # root far larger than the shape
+                                  ("tiny_2d", "fixed", 1, 7, 2e-2, 1.0, 0.5),     # samples kept to a band
+                                  ("tiny_3d", "moving", 1, 5, 5e-3, 0.5, 0.3)])
 def test_tree_equals_oracle_tree(lib, case):
-    name, which, d_min, d_max, tau, pad = case
+    name, which, d_min, d_max, tau, pad, band = case
     w = getattr(configs, name)()
     s = getattr(w, which)
     b = s.boundary
@@ -57,8 +62,8 @@ def test_tree_equals_oracle_tree(lib, case):
         return osdf.nearest_distance(p, b.pos)
 
     lo, size = _box(s, pad)
-    c, v, k, d, asked = ooct.octree_leaves(rho_fn, xi_fn, lo, size, w.dim, d_min, d_max, tau, b.spacing)
-    tree = sd.Octree(w.dim, b.pos, lo, size, d_min, d_max, tau, b.spacing)
+    c, v, k, d, asked = ooct.octree_leaves(rho_fn, xi_fn, lo, size, w.dim, d_min, d_max, tau, b.spacing, band)
+    tree = sd.Octree(w.dim, b.pos, lo, size, d_min, d_max, tau, b.spacing, band)
     got_asked = _drive(tree, rho_fn, w.dim)
     cen, vol, crd = tree.leaves()
     tree.close()
@@ -89,19 +94,20 @@ def test_argument_errors(lib):
     b = np.zeros((4, 4))
     b[:, 0] = np.arange(4)
 
-    def create(dim=3, bp=b.ctypes.data, n=4, size=1.0, dmin=1, dmax=3, tau=0.1, clear=0.0):
-        return lib.sd_octree_create(dim, bp, n, lo.ctypes.data, size, dmin, dmax, tau, clear, ct.byref(h))
+    def create(dim=3, bp=b.ctypes.data, n=4, size=1.0, dmin=1, dmax=3, tau=0.1, clear=0.0, band=INF):
+        return lib.sd_octree_create(dim, bp, n, lo.ctypes.data, size, dmin, dmax, tau, clear, band, ct.byref(h))
 
     assert create() == sd.SD_OK
     lib.sd_octree_free(h)
     for bad in (dict(dim=4), dict(n=-1), dict(bp=None), dict(size=0.0), dict(size=float("inf")), dict(dmin=4),
-                dict(dmax=21), dict(tau=float("nan")), dict(tau=-1.0), dict(clear=-0.1)):
+                dict(dmax=21), dict(tau=float("nan")), dict(tau=-1.0), dict(clear=-0.1), dict(band=-1.0),
+                dict(band=float("nan"))):
         assert create(**bad) == sd.SD_ERR_ARG, bad
         assert not h.value
     assert create(dmin=10, dmax=12) == sd.SD_ERR_OOM
     b2 = b.copy()
     b2[2, 1] = np.nan
-    assert lib.sd_octree_create(3, b2.ctypes.data, 4, lo.ctypes.data, 1.0, 1, 3, 0.1, 0.0, ct.byref(h)) \
+    assert lib.sd_octree_create(3, b2.ctypes.data, 4, lo.ctypes.data, 1.0, 1, 3, 0.1, 0.0, INF, ct.byref(h)) \
         == sd.SD_ERR_NONFINITE
     # a tree waiting for rho: wrong count, non-finite values and early leaves are refused
     tree = sd.Octree(3, np.zeros((0, 4)), lo, 1.0, 1, 3, 1e-3, 0.0)
