@@ -399,9 +399,16 @@ int sd_refine(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const 
  * Scratch: a 128 KiB bitset in a fixed device array that every GPU which loads
  * the library keeps until the process exits; each call clears the bits it uses.
  * The first call on a device looks up the array's device address (set-up):
- * make that first call before any stream capture.  All calls share the one
- * array, so calls whose kernels can overlap on the GPU (other streams, other
- * host threads) race; serialise them.  Larger inputs return SD_ERR_ARG.
+ * make that first call before any stream capture.  The address stays cached for
+ * the process, so a cudaDeviceReset (or anything else that destroys the
+ * device's primary context) invalidates it together with every context and
+ * shape on that device: do not call this entry on a device after such a reset.
+ * All calls share the one array, so calls whose kernels can overlap on the GPU
+ * (other streams, other host threads) race; serialise them.  Larger inputs
+ * return SD_ERR_ARG.
+ * Cost: one CTA makes k passes over the candidates, O(k n_cand) reads (the same
+ * selection as sd_top_k_poses); at k = 4096 and n_cand = 2^20 that is 64 GiB of
+ * reads by one SM.
  * Asynchronous on `stream`. */
 int sd_top_k_static(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, sd_cand* out, void* stream);
 

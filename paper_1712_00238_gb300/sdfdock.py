@@ -604,7 +604,11 @@ def shard_range(n: int, world: int, rank: int) -> tuple[int, int]:
 
 
 def merge_top_k(parts, k: int):
-    """Merge per-rank lists of (score, rot, idx) into the global top-k (score desc, rot asc, idx asc)."""
-    allc = [c for p in parts for c in p]
+    """Merge per-rank lists of (score, rot, idx) into the global top-k (score desc, rot asc, idx asc).
+
+    Entries with rot < 0 are the padding a rank returns when it has fewer than k
+    candidates; they are dropped, so they never rank ahead of a real candidate
+    whose score is -inf or NaN (NaN ranks with -inf, last)."""
+    allc = [c for p in parts for c in p if c[1] >= 0]
     allc.sort(key=lambda c: (-c[0] if c[0] == c[0] else math.inf, c[1], c[2]))
     return allc[:k]

@@ -423,6 +423,50 @@ def test_refine_rules_match_oracle(name, method):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,prec", [("tiny_3d", "f64"), ("tiny_3d", "f32"), ("tiny_2d", "f64"), ("tiny_2d", "f32")])
+def test_device_ascent_matches_oracle(name, prec):
+    # the device's gradient-ascent rule (sd_refine with SD_REFINE_ASCENT, which
+    # sd_refine_poses runs) against the oracle's ascent driven by the oracle's
+    # own pair-sum force and dq
+    from oracle import refine as orf
+
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    N = 16
+    g = grid_of(w, N)
+    P, steps, lr_t, lr_q = 3, 5, 0.03, 0.02
+    if w.dim == 3:
+        q0 = rotations.random_uniform(P, 19)
+        t0 = rotations.random_ball(P, 0.8, 20, 3)
+    else:
+        q0 = rotations.planar(9)[[1, 4, 7]]
+        t0 = rotations.random_ball(P, 0.8, 20, 2)
+    real = torch.float64 if prec == "f64" else torch.float32
+    qd = torch.tensor(q0, device="cuda", dtype=real)
+    td = torch.tensor(t0, device="cuda", dtype=real)
+    qg, tg, hg = ctx.refine(fx, mv, g, qd, td, steps, method=sd.REFINE_ASCENT, lr_t=lr_t, lr_q=lr_q)
+    qn, tn, hn = ctx.refine_poses(fx, mv, g, qd, td, steps=steps, lr_t=lr_t, lr_q=lr_q)
+    qg, tg, hg = qg.cpu().double().numpy(), tg.cpu().double().numpy(), hg.cpu().double().numpy()
+
+    def grad(q, t):
+        return orf.force_torque_fN(p1, c1, p2, c2, q, t[: w.dim], N, w.L, w.sigma_g)
+
+    tol, ptol = (2e-5, 1e-5) if prec == "f64" else (1e-4, 1e-4)
+    for i in range(P):
+        qo, to, ho = orf.refine(grad, q0[i], t0[i], steps, orf.ASCENT, lr_t=lr_t, lr_q=lr_q)
+        scale = np.abs(ho).max()
+        assert np.abs(hg[:, i] - ho).max() <= tol * scale, (i, hg[:, i], ho)
+        sign = 1.0 if float(qg[i] @ qo) >= 0 else -1.0
+        assert np.abs(qg[i] - sign * qo).max() < ptol, (i, qg[i], qo)
+        assert np.abs(tg[i] - to[: w.dim]).max() < ptol, (i, tg[i], to)
+    # sd_refine_poses is the same rule
+    assert np.abs(hn.cpu().double().numpy() - hg).max() <= 1e-12 * np.abs(hg).max() + (0 if prec == "f64" else 1e-6)
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_native_refinement_follows_autograd_path(prec):
     # sd_refine_poses runs the same ascent rule on the device (update arithmetic

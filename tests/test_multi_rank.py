@@ -78,3 +78,13 @@ def test_sharded_top_k_equals_single_process(world):
 def test_merge_order_and_nan():
     parts = [[(1.0, 3, 7), (0.5, 1, 2)], [(1.0, 2, 9), (float("nan"), 0, 0), (2.0, 5, 1)]]
     assert merge_top_k(parts, 4) == [(2.0, 5, 1), (1.0, 2, 9), (1.0, 3, 7), (0.5, 1, 2)]
+
+
+def test_merge_drops_rank_padding():
+    # a rank with fewer than k candidates pads its list with rot = idx = -1, score -inf;
+    # the padding must not displace real candidates scoring -inf or NaN
+    inf = float("inf")
+    parts = [[(0.5, 4, 1), (-inf, -1, -1), (-inf, -1, -1)], [(-inf, 2, 8), (float("nan"), 0, 3), (1.5, 7, 0)]]
+    merged = merge_top_k(parts, 4)
+    assert [(r, i) for _, r, i in merged] == [(7, 0), (4, 1), (0, 3), (2, 8)]
+    assert len(merge_top_k(parts, 10)) == 4
