@@ -1,14 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the SDF complementarity search on one or more GPUs.
 
-One step runs the whole hot path on the 3D peg-in-bore workload (cylinder
-r = 1, length 3, into a 6x6x4 block with a blind bore r = 1.02, depth 2.5;
-20,000 boundary samples and ~50,000 SDF samples per shape; 128^3 translations;
-576 Hopf-grid rotations):
+One step runs the whole hot path on the docking-shaped pair (unions of 2,000
+and 500 spheres, ~80,000 and ~20,000 SDF samples; 192^3 translations at 0.8 A;
+all 54,000 super-Fibonacci rotations):
 
   SDF build of both shapes -> per-rotation search (rotate, spread, forward FFT,
-  product, inverse FFT, argmax) -> global top-10 with FP64 re-score ->
-  gradient refinement of the 10 poses (type-2 score+gradient, 20 steps).
+  product, inverse FFT, argmax) -> global top-100 with FP64 re-score ->
+  gradient refinement of the best 10 poses (type-2 score+gradient, 20 steps).
+
+`--workload peg_in_bore_3d` runs the same step on the 3D peg-in-bore pair
+(cylinder r = 1, length 3, into a 6x6x4 block with a blind bore r = 1.02,
+depth 2.5; ~50,000 SDF samples per shape; 128^3 translations; 576 Hopf
+rotations; top-10).
 
 metric: poses scored per second = rotations x translations / step time.
 `value` uses device-resident inputs; `e2e` copies the step's inputs from pinned
@@ -41,6 +45,11 @@ L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
 TOP_K = 10
 REFINE_STEPS = 20
+E2E_STEPS = 5
+# rotations of the oracle's CPU baseline per workload (about 10-30 s of host time)
+CPU_BASELINE_ROTATIONS = {"peg_in_hole_2d": 64, "peg_in_bore_3d": 4, "docking_2000_500": 2}
+# rotations on which the plain per-rotation path is timed against the batched plan
+PLAIN_ROTATIONS = {"peg_in_hole_2d": 64, "peg_in_bore_3d": 576, "docking_2000_500": 1000}
 
 
 def parse_args():
@@ -59,11 +68,14 @@ def parse_args():
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--workload", choices=["peg_in_bore_3d", "peg_in_hole_2d", "docking_2000_500", "refine_256",
                                            "uneven_batch", "multistart_2d"],
-                    default="peg_in_bore_3d")
+                    default="docking_2000_500")
     ap.add_argument("--pairs", type=int, default=0, help="uneven_batch: use only the first P pairs")
     ap.add_argument("--refine-method", choices=["autograd", "ascent", "cg", "dynamics"], default="autograd",
                     help="refine_256: the autograd Function loop, or an on-device rule of sd_refine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-rotations", type=int, default=-1,
+                    help="rotations on which the plain per-rotation path is timed against the batched plan "
+                         "(-1: automatic, 0: skip)")
     return ap.parse_args()
 
 
@@ -143,8 +155,6 @@ def load_workload(n_rot: int = 0, name: str = "peg_in_bore_3d"):
 
     from synth import configs
     w = getattr(configs, name)()
-    if name == "docking_2000_500" and not n_rot:
-        n_rot = w.extra["rot_per_launch"]  # one launch batch of 3,000 rotations per step
     if n_rot and n_rot < w.n_rot:
         w = copy.copy(w)
         w.quats = w.quats[:n_rot]
@@ -160,8 +170,8 @@ WORKLOAD_TEXT = {
                       "re-score; 20-step on-device gradient refinement of the top 10",
     "docking_2000_500": "docking_2000_500: sphere unions of 2,000 and 500 spheres (radii U[1.2,2.0], confined "
                         "self-avoiding walks), 2 samples/A^2, ~80k/20k SDF samples; 192^3 translations at 0.8 A, "
-                        "n=384; 3,000 super-Fibonacci rotations (one launch batch of the 54,000); top-100 + FP64 "
-                        "re-score; 20-step gradient refinement of the top-10",
+                        "n=384; 54,000 super-Fibonacci rotations; top-100 + FP64 re-score; 20-step gradient "
+                        "refinement of the top-10",
 }
 
 
@@ -321,10 +331,14 @@ def run_ours(args):
     ctx.set_option("timing", 0)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    e2e_times, _ = timed_steps(args.steps, True)
+    # end to end: the same steps with inputs copied from pinned host memory (at most
+    # E2E_STEPS of them: a docking step takes seconds)
+    e2e_steps = max(1, min(args.steps, E2E_STEPS))
+    e2e_times, _ = timed_steps(e2e_steps, True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    plain = plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand) if rank == 0 else None
 
     ms = statistics.mean(times)
     ms_e2e = statistics.mean(e2e_times)
@@ -388,7 +402,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": ms_e2e},
+                "ms_per_step": ms_e2e, "steps": e2e_steps},
         "gpu_launches": int(launches // max(args.steps, 1)),
         "gpu_launches_total": int(launches),
         "roofline": roofline,
@@ -398,16 +412,60 @@ def run_ours(args):
         "search_ms_per_step": search_ms,
         "phase_ms_per_step": phases,
         "top1": {"score": merged[0][0], "rot": merged[0][1], "idx": merged[0][2]},
+        "plain_speedup": plain,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("peg_in_bore_3d",
-                                                                                  "peg_in_hole_2d"):
-        result["cpu_baseline"] = cpu_baseline(w, 4 if w.dim == 3 else w.n_rot)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, CPU_BASELINE_ROTATIONS.get(args.workload, 4))
     if rank == 0:
         print(json.dumps(result), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
+    """Search time of the plain per-rotation path (one rotation per launch sequence,
+    no graph, direct spreading) against the plan the step ran, on the same rotations.
+
+    Both searches run the same kernels on the same inputs, so they compute the same
+    per-rotation maxima up to the FP32 rounding of the spreading's atomic order."""
+    n = args.plain_rotations if args.plain_rotations >= 0 else PLAIN_ROTATIONS.get(args.workload, 0)
+    n = min(n, w.n_rot)
+    if n <= 0 or args.plain:
+        return None
+    fx = ctx.sdf_build(devin["f_bnd"], devin["f_nrm"], devin["f_area"], devin["f_qry"], devin["f_vol"])
+    mv = ctx.sdf_build(devin["m_bnd"], devin["m_nrm"], devin["m_area"], devin["m_qry"], devin["m_vol"])
+    quats = devin["quats"][:n]
+    out = cand[:n]
+
+    def timed(reps=2):
+        best = math.inf
+        for _ in range(reps + 1):  # the first run is a warm-up
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                ctx.score_rotations(fx, mv, quats, grid, out=out)
+                b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b)) if _ else best
+        return best
+
+    batched = timed()
+    ctx.set_option("plain", 1)
+    ctx.set_option("graph", 0)
+    plain = timed()
+    ctx.set_option("plain", 0)
+    ctx.set_option("graph", args.graph)
+    ctx.shapes.remove(fx)
+    ctx.shapes.remove(mv)
+    fx.free()
+    mv.free()
+    return {"rotations": n, "plain_ms": round(plain, 3), "batched_ms": round(batched, 3),
+            "speedup": round(plain / batched, 3),
+            "note": "search only (rotate, spread, FFTs, product, argmax), best of 2 after a warm-up; plain = one "
+                    "rotation per launch sequence, direct spreading, no graph"}
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -455,10 +513,12 @@ def cpu_baseline(w, n_rot=2):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the same workload, one rotation per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w = load_workload()
+    name = args.workload if args.workload in WORKLOAD_TEXT else "docking_2000_500"
+    w = load_workload(0, name)
     st = oracle_setup(w)
     for r in range(max(args.warmup, 0)):
         oracle_rotation(w, st, r % w.n_rot)
@@ -468,15 +528,16 @@ def run_reference(args):
         oracle_rotation(w, st, k % w.n_rot)
         times.append(time.perf_counter() - t0)
     ms = statistics.mean(times) * 1e3
-    value = w.N ** 3 / (ms * 1e-3)
-    sample = ("each step: one rotation of the 128^3 map by the FP64 oracle (direct NUDFT of the moving "
-              "samples, spectral product, numpy inverse FFT, argmax) on the 3D peg-in-bore workload")
+    value = w.N ** w.dim / (ms * 1e-3)
+    sample = (f"each step: one rotation of the {w.N}^{w.dim} map by the FP64 oracle (direct NUDFT of the moving "
+              f"samples, spectral product, numpy inverse FFT, argmax) on the {name} workload (the fixed shape's "
+              f"transform is computed once, before the steps)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "peg_in_bore_3d (one rotation per step)", "rotations": 1,
-                   "translations": w.N ** 3},
+        "config": {"workload": WORKLOAD_TEXT[name] + " [oracle: one rotation per step]", "rotations": 1,
+                   "translations": w.N ** w.dim},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
