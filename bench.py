@@ -398,7 +398,8 @@ def run_ours(args):
                    "rotations": n_rot, "translations": w.N ** w.dim, "sub_box": s,
                    "batch": plan_used.get("batch"), "autotune": bool(args.autotune),
                    "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": "binned shared-memory tiles" if plan_used.get("spread_bins") else "global vector atomics",
+                   "spread": (f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
+                              if plan_used.get("spread_bins") else "global vector atomics"),
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -724,7 +725,7 @@ def run_pairs(args):
     pair_ms = [x["ms"] for st in per_pair for x in st]
     plans = {}
     for x in per_pair[-1]:
-        key = f"n={x['n']} B={x['batch']} {'bins' if x['spread_bins'] else 'direct'}"
+        key = f"n={x['n']} B={x['batch']} {('bins' + str(x['spread_bins'])) if x['spread_bins'] else 'direct'}"
         plans[key] = plans.get(key, 0) + 1
     grids = {}
     for w in mine:

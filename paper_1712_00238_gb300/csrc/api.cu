@@ -35,6 +35,9 @@ struct Prep {  // fixed-shape tables for one grid
     void* B1 = nullptr;  // N^d: spread + forward FFT of the fixed samples (deconvolution pending)
     void* W = nullptr;   // N^d: the product table of the search
     void* G = nullptr;   // n^d x 4: Phi and its gradient on the oversampled grid
+    // W times the phase of an unshifted sub-box of half-side s_h (the pruned
+    // passes), one per s_h met: (s_h, table)
+    std::vector<std::pair<int, void*>> Wsh;
 };
 
 struct GraphEntry {
@@ -45,7 +48,7 @@ struct GraphEntry {
 
 struct Plan {      // launch plan of one scoring job
     int B = 1;     // rotations per launch sequence
-    int bins = 0;  // 1: bin-sorted spreading, 0: direct
+    int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct
 };
 
 struct TimerRec {
@@ -66,6 +69,7 @@ struct sd_ctx {
     int opt_graph = 0;
     int opt_plain = 0;
     int opt_spread_direct = 1;  // 0: spread by bins
+    int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
     int opt_autotune = 0;       // 1: time candidate plans per job geometry
     std::map<std::string, Plan> tuned;
@@ -388,7 +392,7 @@ static int get_tw(sd_ctx* ctx, const Geo& G, Tw<T>* tw, cudaStream_t st) {
 // x pass: rows of the box
 template <typename T>
 static cudaError_t pass_x_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
-                              int64_t out_rs, int batch, cudaStream_t st) {
+                              int64_t out_rs, int batch, cudaStream_t st, int mode = ROW_FWD) {
     RowArgs<T> r{};
     r.in = in;
     r.out = out;
@@ -402,13 +406,13 @@ static cudaError_t pass_x_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
     r.N = G.N;
     r.n = G.n;
     r.tw = tw.n;
-    return launch_rows<T>(ROW_FWD, r, batch, nullptr, st);
+    return launch_rows<T>(mode, r, batch, nullptr, st);
 }
 
 // y pass (3D): (s,s,N) -> (s,N,N)
 template <typename T>
 static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
-                              int64_t out_rs, int batch, cudaStream_t st) {
+                              int64_t out_rs, int batch, cudaStream_t st, int mode = COL_FWD) {
     ColArgs<T> c{};
     c.in = in;
     c.out = out;
@@ -424,7 +428,7 @@ static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
     c.n = G.n;
     c.twF = tw.n;
     c.twI = tw.N;
-    return launch_cols<T>(COL_FWD, c, batch, st);
+    return launch_cols<T>(mode, c, batch, st);
 }
 
 // last axis (z in 3D, y in 2D): FWD (modes) or FUSED (product with W, inverse)
@@ -450,7 +454,7 @@ static cudaError_t pass_last(int mode, const Geo& G, const Tw<T>& tw, const cplx
     // W larger than a quarter of the 129 MB L2 would be evicted between rotations
     // by the streaming data: let the batch's rotations share each block of it
     const int64_t w_bytes = (int64_t)c.ncols * G.N * (int64_t)sizeof(cplx<T>);
-    c.rot_fastest = (mode == COL_FUSED && w_bytes > ((int64_t)32 << 20)) ? 1 : 0;
+    c.rot_fastest = ((mode == COL_FUSED || mode == COL_FUSED_P) && w_bytes > ((int64_t)32 << 20)) ? 1 : 0;
     return launch_cols<T>(mode, c, batch, st);
 }
 
@@ -475,18 +479,20 @@ static cudaError_t pass_y_inv(const Geo& G, const Tw<T>& tw, cplx<T>* buf, int64
     return launch_cols<T>(COL_INV, c, batch, st);
 }
 
-// Bin workspace of one spread batch (slot 6): its size and its layout.
-static size_t bins_bytes(int s, int dim, int64_t m, int batch) {
-    const int nb = (s + 7) / 8;
+// Bin workspace of one spread batch (slot 6) with bins of tb^d cells: its size
+// and its layout.
+static size_t bins_bytes(int s, int dim, int64_t m, int batch, int tb) {
+    const int nb = (s + tb - 1) / tb;
     const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
     const size_t ints = (size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m;
-    return ints * sizeof(int) + 1024;
+    return ints * sizeof(int);
 }
 
-static void bins_layout(void* p, int s, int dim, int64_t m, int batch, BinArgs* bn) {
-    const int nb = (s + 7) / 8;
+static void bins_layout(void* p, int s, int dim, int64_t m, int batch, int tb, BinArgs* bn) {
+    const int nb = (s + tb - 1) / tb;
     const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
     int* q = (int*)p;
+    bn->tb = tb;
     bn->nb = nb;
     bn->nbins = nbins;
     bn->count = q;
@@ -500,14 +506,17 @@ static void bins_layout(void* p, int s, int dim, int64_t m, int batch, BinArgs* 
     bn->sorted = q;
 }
 
-static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, BinArgs* bn) {
+static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, int tb, BinArgs* bn) {
     void* p = nullptr;
-    CKI(ws_get(ctx, 6, bins_bytes(s, dim, m, batch), &p));
-    bins_layout(p, s, dim, m, batch, bn);
+    CKI(ws_get(ctx, 6, bins_bytes(s, dim, m, batch, tb), &p));
+    bins_layout(p, s, dim, m, batch, tb, bn);
     return SD_OK;
 }
 
-// Binned spreading exists for FP32 and kernel widths 4-7 (tiles of 8 + w - 1 cells).
+// Bin side of binned spreading when it is asked for without the autotuner.
+constexpr int DEFAULT_BIN = 16;
+
+// Binned spreading exists for FP32 and kernel widths 4-7 (tiles of tb + w - 1 cells).
 static bool bins_supported(const sd_ctx* ctx) { return ctx->p.precision == SD_F32 && ctx->p.w >= 4 && ctx->p.w <= 7; }
 
 // ---------------------------------------------------------------------------
@@ -558,7 +567,7 @@ static int prep_fixed(sd_ctx* ctx, sd_shape* fx, const sd_grid* g, Prep** out, c
         CK(ctx, launch_spread<T>(sa, G.dim, 1, st));
     } else {
         BinArgs bn;
-        CKI(bins_for(ctx, G.s, G.dim, fx->m, 1, &bn));
+        CKI(bins_for(ctx, G.s, G.dim, fx->m, 1, DEFAULT_BIN, &bn));
         CK(ctx, launch_spread_bins<T>(sa, bn, G.dim, 1, st));
     }
     CK(ctx, pass_x_fwd<T>(G, tw, b0, 0, b1, 0, 1, st));
@@ -708,6 +717,7 @@ struct Search {
     void* out = nullptr;
     int maps = 0;
     Plan plan{};
+    bool pruned = false;  // pruned forward passes with the shifted table W'
     int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
     cplx<T>* b0 = nullptr;
     cplx<T>* b1 = nullptr;
@@ -732,10 +742,23 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     S->out = out;
     S->maps = maps;
     S->plan.B = choose_batch<T>(ctx, S->G, n_r);
-    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? 1 : 0;
+    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
     per_rot_elems<T>(S->G, &S->e0, &S->e1);
     S->rows_last = (S->G.dim == 2) ? S->G.N : (int64_t)S->G.N * S->G.N;
     S->Nd = (S->G.dim == 2) ? (int64_t)S->G.N * S->G.N : (int64_t)S->G.N * S->G.N * S->G.N;
+    // pruned forward passes: the sub-box must fit in the low half of a line
+    S->pruned = ctx->opt_pruned && pruned_len_ok(S->G.n) && S->G.s <= S->G.N;
+    if (S->pruned) {
+        void* ws = nullptr;
+        for (auto& w : prep->Wsh)
+            if (w.first == S->G.s_h) ws = w.second;
+        if (!ws) {
+            CK(ctx, pool_alloc(&ws, (size_t)S->Nd * sizeof(cplx<T>), st));
+            CK(ctx, launch_wshift<T>((const cplx<T>*)prep->W, S->G.N, S->G.dim, S->G.n, S->G.s_h, (cplx<T>*)ws, st));
+            prep->Wsh.emplace_back(S->G.s_h, ws);
+        }
+        S->W = (const cplx<T>*)ws;
+    }
     return SD_OK;
 }
 
@@ -747,7 +770,7 @@ static void search_need(const Search<T>& S, size_t need[8]) {
     need[1] = std::max(need[1], B * S.e1 * sizeof(cplx<T>));
     need[2] = std::max(need[2], B * S.rows_last * sizeof(double));  // at most one partial per row
     need[3] = std::max(need[3], B * S.rows_last * sizeof(int));
-    if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B));
+    if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
 }
 
 static int ws_reserve(sd_ctx* ctx, const size_t need[8]) {
@@ -764,7 +787,7 @@ static void search_bind(sd_ctx* ctx, Search<T>* S) {
     S->b1 = (cplx<T>*)ctx->ws[1].p;
     S->ps = (double*)ctx->ws[2].p;
     S->pi = (int*)ctx->ws[3].p;
-    if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, &S->bn);
+    if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, S->plan.bins, &S->bn);
 }
 
 // Launch sequence of rotations [r_lo, r_hi), plan.B rotations at a time.
@@ -800,20 +823,23 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
             else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
         }
+        const int mx = S.pruned ? ROW_FWD_P : ROW_FWD;
+        const int my = S.pruned ? COL_FWD_P : COL_FWD;
+        const int mf = S.pruned ? COL_FUSED_P : COL_FUSED;
         {
             PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
-            CK(ctx, pass_x_fwd<T>(G, S.tw, S.b0, S.e0, S.b1, S.e1, b, s));
+            CK(ctx, pass_x_fwd<T>(G, S.tw, S.b0, S.e0, S.b1, S.e1, b, s, mx));
         }
         C* fin;
         int64_t fin_rs;
         if (G.dim == 3) {
             {
                 PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
-                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s));
+                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s, my));
             }
             {
                 PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                CK(ctx, pass_last<T>(COL_FUSED, G, S.tw, S.b0, S.e0, S.b1, S.e1, S.W, b, s));
+                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, S.W, b, s));
             }
             {
                 PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
@@ -823,7 +849,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             fin_rs = S.e1;
         } else {
             PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-            CK(ctx, pass_last<T>(COL_FUSED, G, S.tw, S.b1, S.e1, S.b0, S.e0, S.W, b, s));
+            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, S.W, b, s));
             fin = S.b0;
             fin_rs = S.e0;
         }
@@ -888,7 +914,8 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     std::vector<Plan> cand;
     for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
         if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
-        for (int bins = 0; bins <= (bins_supported(ctx) ? 1 : 0); ++bins) {
+        for (int bins : {0, 8, 12, 16}) {
+            if (bins && !bins_supported(ctx)) continue;
             bool dup = false;
             for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
             if (!dup) cand.push_back(Plan{B, bins});
@@ -1174,6 +1201,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "plain")) ctx->opt_plain = (int)value;
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
+    else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
     else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
     else if (!strcmp(key, "autotune")) ctx->opt_autotune = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
@@ -1360,6 +1388,7 @@ int sd_shape_free(sd_shape* s) {
         pool_free(p.B1, nullptr);
         pool_free(p.W, nullptr);
         pool_free(p.G, nullptr);
+        for (auto& w : p.Wsh) pool_free(w.second, nullptr);
     }
     delete s;
     return SD_OK;
@@ -1433,7 +1462,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         std::string key(p, (size_t)(q - p));
         int B = 0, bins = -1;
         if (sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d}", &B, &bins) != 2 || B < 1 || B > 64 ||
-            (bins != 0 && bins != 1))
+            (bins != 0 && bins != 8 && bins != 12 && bins != 16))
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
         got[key] = Plan{B, bins};
         p = q;
@@ -1454,7 +1483,7 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
         S.moving = moving;
         S.n_r = n_r;
         S.plan.B = choose_batch<T>(ctx, S.G, n_r);
-        S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? 1 : 0;
+        S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
         if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) {
             auto it = ctx->tuned.find(plan_key(ctx, S));
             if (it != ctx->tuned.end()) {

@@ -75,9 +75,10 @@ struct SpreadArgs {
 };
 template <typename T> cudaError_t launch_spread(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);
 
-// Bins of the spread sub-box (8^d cells each) and the per-rotation sample order.
+// Bins of the spread sub-box (tb^d cells each) and the per-rotation sample order.
 struct BinArgs {
-    int nb;               // bins per axis = ceil(s / 8)
+    int tb;               // cells per bin along an axis: 8, 12 or 16
+    int nb;               // bins per axis = ceil(s / tb)
     int nbins;            // nb^d
     int* count;           // batch x nbins
     int* offset;          // batch x (nbins + 1)
@@ -86,13 +87,25 @@ struct BinArgs {
     int32_t* sorted;      // batch x m: sample indices in bin order
 };
 // Spread by bins; accumulates into the batch's sub-boxes, which must be cleared first.
-// Supports w = 4..7 (shared tile of (8 + w - 1)^d cells).
+// Supports w = 4..7 and tb = 8, 12, 16 (shared tile of (tb + w - 1)^d cells).
 template <typename T>
 cudaError_t launch_spread_bins(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st);
 
 // ---- line passes ------------------------------------------------------------
-enum RowMode { ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3 };
-enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FUSED = 2, COL_EXPAND = 3 };
+// *_P modes are the pruned forward passes of the search: the sub-box is read
+// unshifted (cell a at position a, a < s <= n/2; the shift is a phase folded
+// into W, see launch_wshift), and only the N = n/2 central modes are computed.
+enum RowMode { ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3, ROW_FWD_P = 4 };
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FUSED = 2, COL_EXPAND = 3, COL_FWD_P = 4, COL_FUSED_P = 5 };
+
+// Whether the pruned passes serve an oversampled length n (a host-side copy of
+// prunable_len for the lengths the library builds).
+inline bool pruned_len_ok(int n) {
+    switch (n) {
+        case 16: case 32: case 64: case 96: case 128: case 192: case 256: case 384: case 512: return true;
+        default: return false;
+    }
+}
 
 template <typename T>
 struct RowArgs {
@@ -144,6 +157,11 @@ cudaError_t launch_deconv(double* D, int N, int n, int w, double beta, const dou
 template <typename T>
 cudaError_t launch_wtable(const cplx<T>* B1, const double* D, int N, int dim, double L, double sigma_g,
                           int shift, int deriv, cplx<T>* W, cudaStream_t st);
+
+// W' = W exp(2 pi i s_h sum_d kappa_d / n): the product table of a search whose
+// forward passes read the sub-box unshifted (the *_P modes).
+template <typename T>
+cudaError_t launch_wshift(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out, cudaStream_t st);
 
 // argmax partials -> one candidate per rotation
 cudaError_t launch_reduce_argmax(const double* part_score, const int* part_idx, int nparts, int batch,

@@ -24,6 +24,7 @@
 #include <tuple>
 
 #include "fft.cuh"
+#include "fftp.cuh"
 #include "kernels.cuh"
 
 namespace sd {
@@ -202,17 +203,15 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// spreading by bins (no global atomics, no clearing pass)
+// spreading by bins
 // ---------------------------------------------------------------------------
 //
-// The sub-box is cut into bins of SPREAD_BIN^d cells.  A sample belongs to the
-// bin that holds the first cell of its tap box.  Since W - 1 < SPREAD_BIN, the
-// taps of a sample only reach its own bin and the next one along each axis, so
-// the tile of bin t receives taps only from samples of bins t - {0,1}^d.  One CTA
-// per tile gathers those samples, accumulates the taps that fall in its tile in
-// shared memory and stores the whole tile (zeros included) once.
-
-constexpr int SPREAD_BIN = 8;
+// The sub-box is cut into bins of TB^d cells (TB = 8, 12 or 16, at least W - 1).
+// A sample belongs to the bin that holds the first cell of its tap box, so its
+// taps fall in that bin grown by W - 1 cells along each axis: a tile of
+// (TB + W - 1)^d cells that one CTA accumulates in shared memory before adding
+// it to the sub-box with 16-byte pair atomics (the block-local accumulation
+// before the global atomics).
 
 // Tap-box origin (sub-box coordinates, wrapped when the sub-box is the whole
 // periodic grid) and kernel weights of sample j under rotation Rm.
@@ -241,7 +240,20 @@ __device__ __forceinline__ void sample_taps(const SpreadArgs<T>& a, const T* Rm,
     }
 }
 
+// The tap-box origin alone (the same arithmetic as sample_taps).
 template <typename T, int D, int W>
+__device__ __forceinline__ void sample_origin(const SpreadArgs<T>& a, const T* Rm, int64_t j, int org[D]) {
+    const vec4<T> p = a.pos[j];
+    T y[3];
+    y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
+    y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
+    y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
+    const T half = T(W) * T(0.5);
+#pragma unroll
+    for (int d = 0; d < D; ++d) org[d] = wrap_index((int)ceil(y[d] * a.inv_h - half) + a.s_h, a.s);
+}
+
+template <typename T, int D, int W, int TB>
 __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) {
     __shared__ T Rm[9];
     const int b = blockIdx.y;
@@ -250,12 +262,10 @@ __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) 
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.m) return;
     int org[D];
-    T wt[D][W];
-    cplx<T> c;
-    sample_taps<T, D, W>(a, Rm, j, org, wt, c);
+    sample_origin<T, D, W>(a, Rm, j, org);
     int bin = 0;
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / SPREAD_BIN;
+    for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / TB;
     const int64_t o = (int64_t)b * a.m + j;
     bn.bin_of[o] = bin;
     bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
@@ -308,34 +318,50 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
     bn.sorted[(int64_t)b * m + pos] = (int32_t)j;
 }
 
-// One CTA per (bin, rotation): the taps of the bin's samples all fall in the
-// bin grown by W - 1 cells, a PS^d tile (PS = 8 + W - 1) accumulated in shared
-// memory, then added to the sub-box with one 16-byte atomic per pair of
-// x-adjacent tile cells that is not zero.
-//
-// Accumulation is warp-cooperative: the CTA stages up to 256 of the bin's
-// samples (kernel weights, weight value, tap-box offset in the tile; one per
-// thread) in shared memory, then its warps take the staged samples round-robin
-// and add each with the lanes on consecutive taps, so the shared atomics of one
-// instruction hit distinct cells (for the 13-cell pitch of W = 6, at most two
-// lanes share a bank) and a bin of a few dozen samples still keeps every warp
-// busy.  A sample whose tap box does not
-// lie in the tile (not possible when the counting pass and this one agree, as
-// they evaluate the same function) is added with global atomics instead.
-template <int D, int W>
-__global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
-    constexpr int PS = SPREAD_BIN + W - 1;
-    constexpr int PS2 = PS * PS;
-    constexpr int CELLS = (D == 3) ? PS2 * PS : PS2;
-    constexpr int TAPS = (D == 3) ? W * W * W : W * W;
+// Shared-memory layout of the tile kernel: two fixed-point planes of the tile
+// (real, imaginary), then the staged sample records.
+template <int D, int W, int TB>
+struct TileShape {
+    static constexpr int PS = TB + W - 1;                         // tile side
+    static constexpr int CELLS = (D == 3) ? PS * PS * PS : PS * PS;
+    static constexpr int ROWS = (D == 3) ? W * W : W;             // (ky, kz) rows of a tap box
+    static constexpr int TAPS = ROWS * W;
+    static constexpr int CHUNK = 64;                              // samples staged at a time
+    // record: wx[W] wy[W] wz[W] | c.x c.y | base | origin | c * wy * wz per row (pairs)
+    static constexpr int O_C = 3 * W, O_BASE = 3 * W + 2, O_ORG = 3 * W + 3, O_ROW = (3 * W + 4 + 1) & ~1;
+    static constexpr int REC = (O_ROW + 2 * ROWS + 1) & ~1;
+    static constexpr size_t smem = (size_t)2 * CELLS * sizeof(int) + (size_t)CHUNK * REC * sizeof(float);
+};
+
+// One CTA per (bin, rotation).  The CTA stages CHUNK of the bin's samples at a
+// time: one thread per sample evaluates its kernel weights and tile offset, then
+// all threads form the products c * scale * wy[ky] * wz[kz] of every row of
+// every staged tap box.  The warps then take the staged samples round-robin with
+// the lanes on consecutive taps (x fastest), so one shared atomic instruction
+// hits up to 32 distinct cells; a tap costs one FFMA per component that both
+// multiplies by wx and rounds to the fixed point (the addend 1.5 * 2^23 leaves
+// round(v) in the low mantissa bits for |v| < 2^22), an integer subtract and the
+// atomic.  The scale is the power of two that keeps every tap below 2^21 and
+// every cell (at most the bin's sum of |c|, the weights being <= 1) below 2^30,
+// so the integer sums are exact and independent of the order of the adds.
+// A sample whose tap box does not lie in the tile (not possible when the
+// counting pass and this one agree, as they evaluate the same function) is
+// added with global atomics instead.
+template <int D, int W, int TB>
+__global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
+    using TS = TileShape<D, W, TB>;
+    constexpr int PS = TS::PS, PS2 = PS * PS, CELLS = TS::CELLS, ROWS = TS::ROWS, TAPS = TS::TAPS;
     constexpr int ROUNDS = (TAPS + 31) / 32;
-    constexpr int REC = D * W + 4;  // D*W weights, c.x, c.y, tile offset (-1: outside), packed origin
+    constexpr int CHUNK = TS::CHUNK, REC = TS::REC;
     constexpr int NWARP = 8;
-    __shared__ int tre[CELLS];  // fixed point: value * scale
-    __shared__ int tim[CELLS];
-    __shared__ float stage[NWARP * 32 * REC];
+    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+    constexpr int MAGIC_BITS = 0x4B400000;
+    extern __shared__ __align__(16) int tsm[];
+    int* tre = tsm;
+    int* tim = tsm + CELLS;
+    float* stage = reinterpret_cast<float*>(tsm + 2 * CELLS);
     __shared__ float Rm[9];
-    __shared__ float bsum[NWARP][2];
+    __shared__ float wred[NWARP][2];
     const int b = blockIdx.y;
     const int t = blockIdx.x;
     const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
@@ -347,52 +373,56 @@ __global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, Bi
     }
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
     const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
-    // No tile cell exceeds sum_j |Re c_j| (resp. |Im c_j|) over the bin's samples,
-    // the kernel weights being at most 1: accumulate in fixed point with the
-    // power of two that keeps that bound below 2^30 (native integer atomics;
-    // each tap rounds by at most half a unit, and the sums are exact and
-    // independent of the order of the adds).
+    // largest |component| of one sample and the bin's sum of them
     {
-        float sx = 0.f, sy = 0.f;
+        float mx = 0.f, sm = 0.f;
         for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
             const float2 c = a.c[sorted[p]];
-            sx += fabsf(c.x);
-            sy += fabsf(c.y);
+            const float v = fmaxf(fabsf(c.x), fabsf(c.y));
+            mx = fmaxf(mx, v);
+            sm += v;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_down_sync(0xffffffffu, sx, o);
-            sy += __shfl_down_sync(0xffffffffu, sy, o);
+            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            sm += __shfl_down_sync(0xffffffffu, sm, o);
         }
         if ((threadIdx.x & 31) == 0) {
-            bsum[threadIdx.x >> 5][0] = sx;
-            bsum[threadIdx.x >> 5][1] = sy;
+            wred[threadIdx.x >> 5][0] = mx;
+            wred[threadIdx.x >> 5][1] = sm;
         }
     }
     __syncthreads();
-    float bound = 0.f;
-    for (int w = 0; w < NWARP; ++w) bound = fmaxf(bound, fmaxf(bsum[w][0], bsum[w][1]));
-    // bound < 2^e2 with e2 from the exponent bits; scale = 2^(30 - e2), kept a normal float
-    const int e2 = ((__float_as_int(bound) >> 23) & 255) - 126;
-    const int se = bound > 0.f ? min(max(127 + 30 - e2, 1), 254) : 127;
+    float mx = 0.f, sm = 0.f;
+    for (int w = 0; w < NWARP; ++w) {
+        mx = fmaxf(mx, wred[w][0]);
+        sm += wred[w][1];
+    }
+    // x < 2^(biased exponent - 126) for a positive normal x; scale = 2^e with
+    // mx * scale < 2^21 and sm * scale < 2^30
+    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
+    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
+    const int e = min(21 - emx, 30 - esm);
+    const int se = sm > 0.f ? min(max(127 + e, 1), 254) : 127;
     const float scale = __int_as_float(se << 23);
     const float inv_scale = 1.f / scale;  // a power of two: exact
     const int nb = bn.nb, s = a.s;
-    const int org0[3] = {(t % nb) * SPREAD_BIN, ((t / nb) % nb) * SPREAD_BIN,
-                         (D == 3) ? (t / (nb * nb)) * SPREAD_BIN : 0};
+    const int org0[3] = {(t % nb) * TB, ((t / nb) % nb) * TB, (D == 3) ? (t / (nb * nb)) * TB : 0};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this lane's tap in each round: tile offset (10 bits) and kx, ky, kz (4 bits each)
-    int tap_of[ROUNDS];
+    // this lane's tap in each round: x weight, row of c * wy * wz, tile offset
+    int kx_of[ROUNDS], row_of[ROUNDS], cell_of[ROUNDS];
 #pragma unroll
     for (int q = 0; q < ROUNDS; ++q) {
         const int tap = min(q * 32 + lane, TAPS - 1);
-        const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
-        tap_of[q] = (kx + PS * ky + PS2 * kz) | (kx << 12) | (ky << 16) | (kz << 20);
+        const int kx = tap % W, row = tap / W;
+        const int ky = row % W, kz = (D == 3) ? row / W : 0;
+        kx_of[q] = kx;
+        row_of[q] = TS::O_ROW + 2 * row;
+        cell_of[q] = kx + PS * ky + PS2 * kz;
     }
     float2* out = a.out + (int64_t)b * a.out_rot_stride;
-    constexpr int CHUNK = NWARP * 32;
     for (int p0 = lo; p0 < hi; p0 += CHUNK) {
-        // every thread stages one sample of the chunk ...
         const int nj = min(CHUNK, hi - p0);
+        // (1) one thread per sample: weights, weight value, tile offset
         if ((int)threadIdx.x < nj) {
             int org[D];
             float wt[D][W];
@@ -403,7 +433,7 @@ __global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, Bi
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const int l = org[d] - org0[d];
-                inside &= (l >= 0 && l < SPREAD_BIN);
+                inside &= (l >= 0 && l < TB);
                 base += l * mul;
                 mul *= PS;
                 packed |= org[d] << (10 * d);
@@ -413,32 +443,42 @@ __global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, Bi
             for (int d = 0; d < D; ++d)
 #pragma unroll
                 for (int k = 0; k < W; ++k) r[d * W + k] = wt[d][k];
-            r[D * W] = c.x;
-            r[D * W + 1] = c.y;
-            r[D * W + 2] = __int_as_float(inside ? base : -1);
-            r[D * W + 3] = __int_as_float(packed);
+            if (D == 2)
+#pragma unroll
+                for (int k = 0; k < W; ++k) r[2 * W + k] = 1.f;
+            r[TS::O_C] = c.x * scale;
+            r[TS::O_C + 1] = c.y * scale;
+            r[TS::O_BASE] = __int_as_float(inside ? base : -1);
+            r[TS::O_ORG] = __int_as_float(packed);
         }
         __syncthreads();
-        // ... and the warps add the staged samples round-robin, one at a time
+        // (2) c * scale * wy * wz for every row of every staged sample
+        for (int i = threadIdx.x; i < nj * ROWS; i += blockDim.x) {
+            const int j = i / ROWS, row = i - j * ROWS;
+            float* r = stage + j * REC;
+            const float wyz = r[W + row % W] * r[2 * W + row / W];
+            r[TS::O_ROW + 2 * row] = r[TS::O_C] * wyz;
+            r[TS::O_ROW + 2 * row + 1] = r[TS::O_C + 1] * wyz;
+        }
+        __syncthreads();
+        // (3) the warps add the staged samples round-robin, one at a time
         for (int j = warp; j < nj; j += NWARP) {
             const float* r = stage + j * REC;
-            const float cx = r[D * W], cy = r[D * W + 1];
-            const int base = __float_as_int(r[D * W + 2]);
+            const int base = __float_as_int(r[TS::O_BASE]);
             if (base >= 0) {  // uniform over the warp
-                const float cxs = cx * scale, cys = cy * scale;
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
                     if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
-                        const int tp = tap_of[q];
-                        float w = r[(tp >> 12) & 15] * r[W + ((tp >> 16) & 15)];
-                        if (D == 3) w *= r[2 * W + ((tp >> 20) & 15)];
-                        const int cell = base + (tp & 4095);
-                        atomicAdd(tre + cell, __float2int_rn(cxs * w));
-                        atomicAdd(tim + cell, __float2int_rn(cys * w));
+                        const float wx = r[kx_of[q]];
+                        const float2 cw = *reinterpret_cast<const float2*>(r + row_of[q]);
+                        const int cell = base + cell_of[q];
+                        atomicAdd(tre + cell, __float_as_int(fmaf(cw.x, wx, MAGIC)) - MAGIC_BITS);
+                        atomicAdd(tim + cell, __float_as_int(fmaf(cw.y, wx, MAGIC)) - MAGIC_BITS);
                     }
                 }
             } else {  // safety net (a tap box outside the tile): global atomics on the sub-box
-                const int packed = __float_as_int(r[D * W + 3]);
+                const int packed = __float_as_int(r[TS::O_ORG]);
+                const float cx = r[TS::O_C] * inv_scale, cy = r[TS::O_C + 1] * inv_scale;
 #pragma unroll 1
                 for (int q = 0; q < ROUNDS; ++q) {
                     const int tap = q * 32 + lane;
@@ -458,8 +498,7 @@ __global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, Bi
         }
         __syncthreads();  // the stage is refilled by the next chunk
     }
-    __syncthreads();
-    // flush: pairs of x-adjacent tile cells (global x even: bins start at multiples of 8)
+    // flush: pairs of x-adjacent tile cells (global x even: bins start at even cells)
     constexpr int XP = (PS + 1) / 2;
     constexpr int PAIRS = (D == 3) ? XP * PS2 : XP * PS;
     bool inner = true;  // the tile does not wrap around the sub-box (no modulo below)
@@ -469,10 +508,11 @@ __global__ void __launch_bounds__(256, 5) k_spread_tiles(SpreadArgs<float> a, Bi
         const int xp = i % XP, row = i / XP;  // row = y + PS z
         const int x = 2 * xp;
         const int li = row * PS + x;
-        const float2 v0 = make_float2((float)tre[li] * inv_scale, (float)tim[li] * inv_scale);
-        const float2 v1 = (x + 1 < PS) ? make_float2((float)tre[li + 1] * inv_scale, (float)tim[li + 1] * inv_scale)
-                                       : make_float2(0.f, 0.f);
-        if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
+        const int r0 = tre[li], i0 = tim[li];
+        const int r1 = (x + 1 < PS) ? tre[li + 1] : 0, i1 = (x + 1 < PS) ? tim[li + 1] : 0;
+        if ((r0 | i0 | r1 | i1) == 0) continue;
+        const float2 v0 = make_float2((float)r0 * inv_scale, (float)i0 * inv_scale);
+        const float2 v1 = make_float2((float)r1 * inv_scale, (float)i1 * inv_scale);
         const int y = row % PS, z = row / PS;
         const int gx = org0[0] + x;
         if (inner && gx + 1 < s) {
@@ -693,6 +733,173 @@ __global__ void __launch_bounds__(cta_threads<T, LENF>(), MB) k_cols_mb(ColArgs<
 }
 
 // ---------------------------------------------------------------------------
+// pruned search passes: the sub-box is loaded unshifted (cell a at position a,
+// a < s <= n/2) and the forward passes keep only the N = n/2 central modes,
+// both decided at compile time (fftp.cuh); the shift of the sub-box to the
+// centred grid, exp(2 pi i kappa s_h / n) per axis, is folded into the product
+// table of the fused pass (k_wshift)
+// ---------------------------------------------------------------------------
+
+// Pitch of an unpadded column line in shared memory (odd: lanes on consecutive
+// lines hit distinct banks).
+__host__ __device__ constexpr int col_pitch(int len) { return len + 1; }
+
+// x pass: rows of the sub-box -> N modes per row (row stride N = LEN/2).
+template <typename T, int LEN>
+__device__ __forceinline__ void rows_fwd_p_body(const RowArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int NH = LEN / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TR * LD;
+    const int row0 = blockIdx.x * TR;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
+    __syncthreads();
+    const int rs = a.in_row_stride;
+    const C* in = a.in + (int64_t)blockIdx.y * a.in_rot_stride + (int64_t)row0 * rs;
+    C* out = a.out + (int64_t)blockIdx.y * a.out_rot_stride + (int64_t)row0 * NH;
+    const int nrows = a.nrows - row0;
+    const int s = a.len_in;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C {
+        const int pos = i + r * NB1;
+        return (line < nrows && pos < s) ? in[line * rs + pos] : zero;
+    };
+    auto emit = [&](int line, int i, int r, C v) {
+        if (kept_out<LEN>(r) && line < nrows) out[line * NH + i + kept_slot<LEN>(r)] = v;
+    };
+    fftp_lines<C, LEN, false, TR, cta_threads<T, LEN>(), LAY_ROW, true, false, true>(buf, LD, tw, load, emit);
+}
+
+template <typename T, int LEN, int MB>
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), MB) k_rows_fwd_p(RowArgs<T> a) {
+    rows_fwd_p_body<T, LEN>(a);
+}
+
+// y pass (3D): columns (one per kept x mode) of each z plane -> N modes.
+template <typename T, int LEN>
+__device__ __forceinline__ void cols_fwd_p_body(const ColArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LEN>();
+    constexpr int NT = cta_threads<T, LEN>();
+    constexpr int LD = col_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TC * LD;
+    const int col0 = blockIdx.x * TC;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.twF[j];
+    __syncthreads();
+    const int ncols = a.ncols;
+    const int ncl = ncols - col0;
+    const C* in = a.in + (int64_t)blockIdx.z * a.in_rot_stride + (int64_t)blockIdx.y * a.in_outer_stride + col0;
+    C* out = a.out + (int64_t)blockIdx.z * a.out_rot_stride + (int64_t)blockIdx.y * a.out_outer_stride + col0;
+    const int s = a.len_in;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C {
+        const int pos = i + r * NB1;
+        return (line < ncl && pos < s) ? in[pos * ncols + line] : zero;
+    };
+    auto emit = [&](int line, int i, int r, C v) {
+        if (kept_out<LEN>(r) && line < ncl) out[(i + kept_slot<LEN>(r)) * ncols + line] = v;
+    };
+    fftp_lines<C, LEN, false, TC, NT, LAY_COL, false, false, true>(buf, LD, tw, load, emit);
+}
+
+template <typename T, int LEN, int MB>
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), MB) k_cols_fwd_p(ColArgs<T> a) {
+    cols_fwd_p_body<T, LEN>(a);
+}
+
+// Last axis: pruned forward FFT of length LENF, times the shifted product table
+// W' (N x ncols), inverse FFT of length LENF/2 in the same block.
+template <typename T, int LENF>
+__device__ __forceinline__ void cols_fused_p_body(const ColArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int LENI = LENF / 2;
+    constexpr int TC = lines_per_cta<T, LENF>();
+    constexpr int NT = cta_threads<T, LENF>();
+    constexpr int LD = col_pitch(LENF);
+    constexpr int NTWF = tw_count(LENF);
+    constexpr int NTWI = tw_count(LENI);
+    constexpr int NB1 = LENF / plan_radix(LENF, 0);
+    constexpr int PI = LENI / plan_last_radix(LENI);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* twF = buf + TC * LD;
+    C* twI = twF + NTWF;
+    const bool rf = a.rot_fastest;
+    const int b = rf ? (int)blockIdx.x : (int)blockIdx.z;
+    const int col0 = (rf ? (int)blockIdx.y : (int)blockIdx.x) * TC;
+    for (int j = threadIdx.x; j < NTWF; j += blockDim.x) twF[j] = a.twF[j];
+    for (int j = threadIdx.x; j < NTWI; j += blockDim.x) twI[j] = a.twI[j];
+    __syncthreads();
+    const int ncols = a.ncols;
+    const int ncl = ncols - col0;
+    const C* in = a.in + (int64_t)b * a.in_rot_stride + col0;
+    C* out = a.out + (int64_t)b * a.out_rot_stride + col0;
+    const C* Wc = a.W + col0;
+    const int s = a.len_in;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C {
+        const int pos = i + r * NB1;
+        return (line < ncl && pos < s) ? in[pos * ncols + line] : zero;
+    };
+    auto emit_fwd = [&](int line, int i, int r, C v) {
+        if (kept_out<LENF>(r) && line < ncl) {
+            const int kp = i + kept_slot<LENF>(r);
+            buf[line * LD + kp] = cmul(v, Wc[kp * ncols + line]);
+        }
+    };
+    fftp_lines<C, LENF, false, TC, NT, LAY_COL, false, false, true>(buf, LD, twF, load, emit_fwd);
+    __syncthreads();
+    auto emit_out = [&](int line, int i, int r, C v) {
+        if (line < ncl) out[(i + r * PI) * ncols + line] = v;
+    };
+    fftp_lines<C, LENI, true, TC, NT, LAY_COL, false, true, false>(buf, LD, twI, load, emit_out);
+}
+
+template <typename T, int LENF, int MB>
+__global__ void __launch_bounds__(cta_threads<T, LENF>(), MB) k_cols_fused_p(ColArgs<T> a) {
+    cols_fused_p_body<T, LENF>(a);
+}
+
+// Resident CTAs per SM the pruned passes are compiled for (0: the compiler's choice).
+// 512-point FP32 lines (256 threads, two butterflies each) take 2 (at most 128
+// registers; 146 otherwise); 384-point ones 3 (384 threads: at most 56).
+template <typename T, int LEN, int KIND>
+__host__ __device__ constexpr int pruned_min_ctas() {
+    return sizeof(T) != 4 ? 0 : (LEN == 512 ? 2 : (LEN == 384 ? 3 : 0));
+}
+
+// W' = W exp(2 pi i s_h (kx + ky [+ kz]) / n) with kappa signed (modes at kappa mod N).
+template <typename T>
+__global__ void k_wshift(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out) {
+    const int64_t tot = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tot) return;
+    int64_t r = i;
+    int64_t ksum = 0;
+    for (int d = 0; d < dim; ++d) {
+        const int kp = (int)(r % N);
+        r /= N;
+        ksum += kp < N / 2 ? kp : kp - N;
+    }
+    // exp(2 pi i ksum s_h / n): reduce the integer ksum * s_h mod n first (exact)
+    int64_t e = (ksum * s_h) % n;
+    if (e < 0) e += n;
+    double sn, cs;
+    sincospi(2.0 * (double)e / (double)n, &sn, &cs);
+    const double wr = (double)W[i].x, wi = (double)W[i].y;
+    out[i] = mk(T(wr * cs - wi * sn), T(wr * sn + wi * cs));
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 
@@ -754,8 +961,73 @@ static cudaError_t cols_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Lengths the pruned passes are built for (prunable_len).
+#define SD_FOR_EACH_PLEN(X) X(16) X(32) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+template <typename T, int LEN>
+static cudaError_t rows_fwd_p_impl(const RowArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    static_assert(prunable_len(LEN), "length not prunable");
+    constexpr int TR = lines_per_cta<T, LEN>();
+    const int nb = (a.nrows + TR - 1) / TR;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
+    auto kern = k_rows_fwd_p<T, LEN, pruned_min_ctas<T, LEN, 0>()>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, batch), cta_threads<T, LEN>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int LEN>
+static cudaError_t cols_fwd_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    static_assert(prunable_len(LEN), "length not prunable");
+    constexpr int TC = lines_per_cta<T, LEN>();
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
+    const size_t smem = (size_t)(TC * col_pitch(LEN) + tw_count(LEN)) * sizeof(C);
+    auto kern = k_cols_fwd_p<T, LEN, pruned_min_ctas<T, LEN, 1>()>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LEN>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int LENF>
+static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    static_assert(prunable_len(LENF), "length not prunable");
+    constexpr int TC = lines_per_cta<T, LENF>();
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    if (a.nouter != 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(TC * col_pitch(LENF) + tw_count(LENF) + tw_count(LENF / 2)) * sizeof(C);
+    auto kern = k_cols_fused_p<T, LENF, pruned_min_ctas<T, LENF, 2>()>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const bool rf = a.rot_fastest;
+    if (rf && nb > 65535) return cudaErrorInvalidValue;
+    const dim3 grid = rf ? dim3(batch, nb, 1) : dim3(nb, 1, batch);
+    kern<<<grid, cta_threads<T, LENF>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_rows_t(int mode, const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    if (mode == ROW_FWD_P) {
+        if (nparts) *nparts = 0;
+        switch (a.n) {
+#define SD_ROWP_CASE(L) \
+    case L: return rows_fwd_p_impl<T, L>(a, batch, st);
+            SD_FOR_EACH_PLEN(SD_ROWP_CASE)
+#undef SD_ROWP_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
     const int len = (mode == ROW_FWD || mode == ROW_EXPAND) ? a.n : a.N;
 #define SD_ROW_CASE(L)                                                          \
     case L:                                                                     \
@@ -774,6 +1046,16 @@ cudaError_t launch_rows_t(int mode, const RowArgs<T>& a, int batch, int* nparts,
 // n = 2N pairs for the fused pass
 template <typename T>
 cudaError_t launch_cols_t(int mode, const ColArgs<T>& a, int batch, cudaStream_t st) {
+    if (mode == COL_FWD_P || mode == COL_FUSED_P) {
+        switch (a.n) {
+#define SD_COLP_CASE(L)                                                                       \
+    case L:                                                                                   \
+        return mode == COL_FWD_P ? cols_fwd_p_impl<T, L>(a, batch, st) : cols_fused_p_impl<T, L>(a, batch, st);
+            SD_FOR_EACH_PLEN(SD_COLP_CASE)
+#undef SD_COLP_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
     if (mode == COL_FUSED) {
         switch (a.N) {
 #define SD_FUSED_CASE(NN) \
@@ -817,37 +1099,43 @@ cudaError_t launch_spread_t(const SpreadArgs<T>& a, int dim, int batch, cudaStre
     return cudaErrorInvalidValue;
 }
 
+template <int D, int W, int TB>
+static cudaError_t spread_bins_impl(const SpreadArgs<float>& a, const BinArgs& bn, int batch, cudaStream_t st) {
+    const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
+    if (a.m > 0) {
+        k_bin_count<float, D, W, TB><<<gpts, 256, 0, st>>>(a, bn);
+        k_bin_scan<<<batch, 1024, 0, st>>>(bn);
+        k_bin_scatter<float><<<gpts, 256, 0, st>>>(a.m, bn);
+        note_launch(3);
+    } else {
+        k_bin_scan<<<batch, 1024, 0, st>>>(bn);
+        note_launch();
+    }
+    auto kern = k_spread_tiles<D, W, TB>;
+    const size_t smem = TileShape<D, W, TB>::smem;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)bn.nbins, batch), 256, smem, st>>>(a, bn);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     if constexpr (sizeof(T) != 4) {
         return launch_spread_t<T>(a, dim, batch, st);  // binned spreading is FP32 only
     } else {
-    cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
-    if (e != cudaSuccess) return e;
-    const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
-    const dim3 gtiles((unsigned)bn.nbins, batch);
-#define SD_BIN_CASE(WW)                                                           \
-    case WW:                                                                      \
-        if (a.m > 0) {                                                            \
-            if (dim == 2) k_bin_count<T, 2, WW><<<gpts, 256, 0, st>>>(a, bn);      \
-            else k_bin_count<T, 3, WW><<<gpts, 256, 0, st>>>(a, bn);               \
-            k_bin_scan<<<batch, 1024, 0, st>>>(bn);                                \
-            k_bin_scatter<T><<<gpts, 256, 0, st>>>(a.m, bn);                        \
-            note_launch(3);                                                       \
-        } else {                                                                  \
-            k_bin_scan<<<batch, 1024, 0, st>>>(bn);                                \
-            note_launch();                                                        \
-        }                                                                         \
-        if (dim == 2) k_spread_tiles<2, WW><<<gtiles, 256, 0, st>>>(a, bn);        \
-        else k_spread_tiles<3, WW><<<gtiles, 256, 0, st>>>(a, bn);                 \
-        note_launch();                                                            \
-        return cudaGetLastError();
-    switch (a.w) {
-        SD_BIN_CASE(4) SD_BIN_CASE(5) SD_BIN_CASE(6) SD_BIN_CASE(7)
-    }
-#undef SD_BIN_CASE
-    return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
+        if (e != cudaSuccess) return e;
+#define SD_BIN_TB(WW, TBB)                                                                       \
+    if (a.w == WW && bn.tb == TBB)                                                               \
+        return dim == 2 ? spread_bins_impl<2, WW, TBB>(a, bn, batch, st) : spread_bins_impl<3, WW, TBB>(a, bn, batch, st);
+#define SD_BIN_W(WW) SD_BIN_TB(WW, 8) SD_BIN_TB(WW, 12) SD_BIN_TB(WW, 16)
+        SD_BIN_W(4) SD_BIN_W(5) SD_BIN_W(6) SD_BIN_W(7)
+#undef SD_BIN_W
+#undef SD_BIN_TB
+        return cudaErrorInvalidValue;
     }
 }
 
@@ -942,6 +1230,14 @@ cudaError_t launch_wtable_t(const cplx<T>* B1, const double* D, int N, int dim, 
 }
 
 template <typename T>
+cudaError_t launch_wshift_t(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out, cudaStream_t st) {
+    const int64_t tot = (dim == 2) ? (int64_t)N * N : (int64_t)N * N * N;
+    k_wshift<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, N, dim, n, s_h, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn, int dim, int f, cudaStream_t st) {
     const int64_t cells = (dim == 3) ? (int64_t)pn * pn * pn : (int64_t)pn * pn;
     k_interleave<T><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(src, dst, n, pn, dim, f);
@@ -972,6 +1268,10 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn,
     template <> cudaError_t launch_wtable<T>(const cplx<T>* B1, const double* D, int N, int dim, double L, \
                                              double sg, int shift, int deriv, cplx<T>* W, cudaStream_t st) { \
         return launch_wtable_t<T>(B1, D, N, dim, L, sg, shift, deriv, W, st);                           \
+    }                                                                                                   \
+    template <> cudaError_t launch_wshift<T>(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out,      \
+                                             cudaStream_t st) {                                                \
+        return launch_wshift_t<T>(W, N, dim, n, s_h, out, st);                                          \
     }                                                                                                   \
     template <> cudaError_t launch_interleave<T>(const cplx<T>* s, cplx<T>* d, int n, int pn, int dim, int f,       \
                                                  cudaStream_t st) {                                                 \

@@ -174,6 +174,41 @@ def test_binned_spreading_matches_oracle(name, N, swap):
     ctx.close()
 
 
+def _sub_box(radius, N, L, w):
+    # side of the moving shape's sub-box on the oversampled grid n = 2N
+    n = 2 * N
+    s_h = int(math.floor(radius * n / L + 0.5 * w)) + 2
+    return n if 2 * s_h >= n else 2 * s_h
+
+
+@pytest.mark.parametrize("name,prec,N", [("tiny_3d", "f32", 48), ("tiny_3d", "f64", 64), ("tiny_2d", "f64", 32),
+                                         ("tiny_2d", "f32", 64), ("tiny_3d", "f32", 64)])
+def test_pruned_and_full_forward_passes_agree(name, prec, N):
+    # The pruned forward passes read the sub-box unshifted and compute only the
+    # kept modes, applying the shift as a phase in the product table; the full
+    # passes read the shifted sub-box and compute every mode.  Same maps, and
+    # both equal the oracle's.  (tiny_3d at N = 48 has s = N exactly, the largest
+    # sub-box the pruned path takes; n = 96 ends with radix 12, n = 64 / 128 with 8.)
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    s = _sub_box(float(np.linalg.norm(p2, axis=1).max()), N, w.L, w.w)
+    assert s <= N, "the pruned path needs the sub-box in the low half of a line"
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    got = {}
+    for pruned in (1, 0):
+        ctx.set_option("pruned", pruned)
+        got[pruned] = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    for r in range(w.n_rot):
+        assert rel_err(got[1][r], got[0][r]) < (1e-12 if prec == "f64" else 2e-6), r
+        assert rel_err(got[1][r], ref[r]) < TOL[prec], r
+    ctx.close()
+
+
 def test_maps_full_size_peg_in_bore():
     # 128^3 translations, n = 256 oversampled grid, ~50,000 samples per shape;
     # weights are seeded synthetic values shared by both sides.
