@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
     ap.add_argument("--spread-direct", type=int, default=1,
                     help="with --autotune 0: 1 global vector atomics, 0 spread by bins")
+    ap.add_argument("--spread-fused", type=int, default=0,
+                    help="with --autotune 0: 1 spreads straight into rows held in shared memory and runs the "
+                         "forward x transform there (3D FP32)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library times candidate plans (batch, spreading) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
@@ -210,6 +213,8 @@ def algorithmic_bytes_per_rotation(s: int, N: int, m_moving: int, dim: int = 3, 
         "clear": s ** 3 * c,
         "spread": m_moving * 24 + s ** 3 * c,
         "fwd_x": (s ** 3 + s * s * N) * c,
+        # spreading fused with the forward x transform: samples in, x modes out
+        "spread_x": m_moving * 24 + s * s * N * c,
         "fwd_y": (s * s * N + s * N * N) * c,
         "fused": (s * N * N + 2 * N ** 3) * c,
         "inv_y": 2 * N ** 3 * c,
@@ -248,6 +253,7 @@ def run_ours(args):
     ctx.set_option("plain", args.plain)
     ctx.set_option("graph", 0 if args.plain else args.graph)
     ctx.set_option("spread_direct", args.spread_direct)
+    ctx.set_option("spread_fused", args.spread_fused)
     ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
     plan_used = {}
@@ -374,7 +380,7 @@ def run_ours(args):
             pass_report[k] = {"launches": n, "ms_total": round(t, 4),
                               "gbs": round(tot_bytes / (t * 1e-3) / 1e9, 1) if t > 0 else None}
     if passes and not l2_resident:
-        dom = max((k for k in passes if per_rot.get(k, 0) > 0 and k not in ("spread", "clear")),
+        dom = max((k for k in passes if per_rot.get(k, 0) > 0 and k not in ("spread", "clear", "spread_x")),
                   key=lambda k: passes[k][1])
         n, t = passes[dom]
         per_launch = per_rot[dom] * n_rot * args.steps / n
@@ -398,7 +404,9 @@ def run_ours(args):
                    "rotations": n_rot, "translations": w.N ** w.dim, "sub_box": s,
                    "batch": plan_used.get("batch"), "autotune": bool(args.autotune),
                    "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": (f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
+                   "spread": ("fused with the forward x transform (8x6 row bins, shared fixed-point tile)"
+                              if plan_used.get("spread_bins") == 1 else
+                              f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
                               if plan_used.get("spread_bins") else "global vector atomics"),
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -725,7 +733,8 @@ def run_pairs(args):
     pair_ms = [x["ms"] for st in per_pair for x in st]
     plans = {}
     for x in per_pair[-1]:
-        key = f"n={x['n']} B={x['batch']} {('bins' + str(x['spread_bins'])) if x['spread_bins'] else 'direct'}"
+        sp = {0: "direct", 1: "spread_x"}.get(x["spread_bins"], f"bins{x['spread_bins']}")
+        key = f"n={x['n']} B={x['batch']} {sp}"
         plans[key] = plans.get(key, 0) + 1
     grids = {}
     for w in mine:

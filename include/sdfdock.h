@@ -138,12 +138,17 @@ const char* sd_last_error(const sd_ctx* ctx);
  * shared memory first), "pruned" (1, the default: the forward FFT passes of the
  * search read the spread sub-box unshifted and compute only the kept modes, with
  * the shift applied as a phase in the product table; 0: the shifted sub-box and
- * every mode; results are the same up to FP rounding), "sdf_cull" (1, the
+ * every mode; results are the same up to FP rounding), "spread_fused" (1: in
+ * pruned 3D FP32 searches with w = 6, spread each rotation's samples straight
+ * into whole rows held in shared memory and run the forward x transform there,
+ * with no sub-box in device memory; default 0), "sdf_cull" (1, the
  * default: the SDF sums skip boundary
  * tiles that lie beyond the truncation radius of every query of a block; 0: sum
  * over every tile; results are the same), "autotune" (1: before a scoring job
  * runs, time its candidate plans -- rotations per batch from a quarter to
- * twice the automatic choice, direct spreading or bins of 8, 12 or 16 cells -- on its first
+ * twice the automatic choice, direct spreading, bins of 8, 12 or 16 cells, or
+ * (pruned 3D FP32 searches with w = 6) spreading fused with the forward x
+ * transform -- on its first
  * rotations and keep the fastest; the choice is cached per precision, grid,
  * sub-box size and sample-count octave; ignored when "batch" or "plain" is
  * set; results do not depend on the plan beyond FP32 rounding). */
@@ -272,7 +277,8 @@ typedef struct sd_pair_job {
 typedef struct sd_pair_stat {
     double ms;            /* device time of the job within the call */
     int32_t batch;        /* rotations per batch of its plan */
-    int32_t spread_bins;  /* bin side of its plan's binned spreading, 0: direct */
+    int32_t spread_bins;  /* bin side of its plan's binned spreading, 0: direct,
+                             1: spreading fused with the forward x transform */
     int32_t n;            /* oversampled grid size per axis */
     int32_t s;            /* sub-box side of its moving shape */
 } sd_pair_stat;
@@ -297,7 +303,8 @@ int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair
                    void* stream);
 
 /* The plan a search of n_r rotations of `moving` on grid g would run with now:
- * rotations per batch and the bin side of binned spreading (0: direct).  With the
+ * rotations per batch and the bin side of binned spreading (0: direct; 1:
+ * spreading fused with the forward x transform).  With the
  * "autotune" option it is the cached choice for this geometry if there is one
  * (the first search of a geometry makes it), else the default.  No device work. */
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
@@ -313,7 +320,7 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
 /* Add the plans of a JSON text written by sd_tune_export to this context's
  * cache (entries with a key already present are replaced), so searches of those
  * geometries skip the timing trials.  A text that is not such a table, or an
- * entry with batch outside [1, 64] or spread_bins not 0, 8, 12 or 16, is SD_ERR_ARG and
+ * entry with batch outside [1, 64] or spread_bins not 0, 1, 8, 12 or 16, is SD_ERR_ARG and
  * leaves the cache unchanged. */
 int sd_tune_import(sd_ctx* ctx, const char* json);
 
@@ -441,7 +448,8 @@ int64_t sd_launch_count(void);
 #define SD_PASS_INV_X 6   /* inverse FFT along x with argmax (or the map)     */
 #define SD_PASS_REDUCE 7  /* per-rotation argmax reduction                    */
 #define SD_PASS_GRAPH 8   /* one replay of a captured search graph            */
-#define SD_PASS_COUNT 9
+#define SD_PASS_SPREAD_X 9  /* rotate + spread fused with the forward x FFT   */
+#define SD_PASS_COUNT 10
 
 /* With the context option "timing" = 1, every pass launch of the search is
  * bracketed by CUDA events on its stream.  Returns the number of timed

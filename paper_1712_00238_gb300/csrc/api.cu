@@ -48,7 +48,8 @@ struct GraphEntry {
 
 struct Plan {      // launch plan of one scoring job
     int B = 1;     // rotations per launch sequence
-    int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct
+    int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct,
+                   // 1: spreading fused with the forward x transform (SPREAD_X)
 };
 
 struct TimerRec {
@@ -70,6 +71,7 @@ struct sd_ctx {
     int opt_plain = 0;
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
+    int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
     int opt_autotune = 0;       // 1: time candidate plans per job geometry
     std::map<std::string, Plan> tuned;
@@ -515,6 +517,37 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, int tb, B
 
 // Bin side of binned spreading when it is asked for without the autotuner.
 constexpr int DEFAULT_BIN = 16;
+// Plan.bins value of spreading fused with the forward x transform.
+constexpr int SPREAD_X = 1;
+
+// Bin workspace of the fused spreading (bins over (y, z)).
+static int spread_x_bins(int s, int* nby, int* nbz) {
+    *nby = (s + SPREADX_TY - 1) / SPREADX_TY;
+    *nbz = (s + SPREADX_TZ - 1) / SPREADX_TZ;
+    return *nby * *nbz;
+}
+static size_t bins_bytes_x(int s, int64_t m, int batch) {
+    int nby, nbz;
+    const int nbins = spread_x_bins(s, &nby, &nbz);
+    return ((size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m) * sizeof(int);
+}
+static void bins_layout_x(void* p, int s, int64_t m, int batch, BinArgs* bn, int* nbz) {
+    int nby;
+    const int nbins = spread_x_bins(s, &nby, nbz);
+    int* q = (int*)p;
+    bn->tb = SPREADX_TY;
+    bn->nb = nby;
+    bn->nbins = nbins;
+    bn->count = q;
+    q += (size_t)batch * nbins;
+    bn->offset = q;
+    q += (size_t)batch * (nbins + 1);
+    bn->bin_of = q;
+    q += (size_t)batch * m;
+    bn->rank = q;
+    q += (size_t)batch * m;
+    bn->sorted = q;
+}
 
 // Binned spreading exists for FP32 and kernel widths 4-7 (tiles of tb + w - 1 cells).
 static bool bins_supported(const sd_ctx* ctx) { return ctx->p.precision == SD_F32 && ctx->p.w >= 4 && ctx->p.w <= 7; }
@@ -724,7 +757,14 @@ struct Search {
     double* ps = nullptr;
     int* pi = nullptr;
     BinArgs bn{};
+    int nbz = 0;  // SPREAD_X: bins along z
 };
+
+// Spreading fused with the x transform: pruned 3D FP32 searches with w = 6.
+template <typename T>
+static bool spread_x_ok(const sd_ctx* ctx, const Search<T>& S) {
+    return sizeof(T) == 4 && S.G.dim == 3 && ctx->p.w == 6 && S.pruned;
+}
 
 // Fixed-shape tables, geometry, twiddles and the default plan of a job (may
 // synchronise the stream the first time a fixed shape meets a grid).
@@ -759,6 +799,7 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
         }
         S->W = (const cplx<T>*)ws;
     }
+    if (ctx->opt_spread_fused && spread_x_ok(ctx, *S)) S->plan.bins = SPREAD_X;
     return SD_OK;
 }
 
@@ -770,7 +811,8 @@ static void search_need(const Search<T>& S, size_t need[8]) {
     need[1] = std::max(need[1], B * S.e1 * sizeof(cplx<T>));
     need[2] = std::max(need[2], B * S.rows_last * sizeof(double));  // at most one partial per row
     need[3] = std::max(need[3], B * S.rows_last * sizeof(int));
-    if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
+    if (S.plan.bins == SPREAD_X) need[6] = std::max(need[6], bins_bytes_x(S.G.s, S.moving->m, S.plan.B));
+    else if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
 }
 
 static int ws_reserve(sd_ctx* ctx, const size_t need[8]) {
@@ -787,7 +829,8 @@ static void search_bind(sd_ctx* ctx, Search<T>* S) {
     S->b1 = (cplx<T>*)ctx->ws[1].p;
     S->ps = (double*)ctx->ws[2].p;
     S->pi = (int*)ctx->ws[3].p;
-    if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, S->plan.bins, &S->bn);
+    if (S->plan.bins == SPREAD_X) bins_layout_x(ctx->ws[6].p, S->G.s, S->moving->m, S->plan.B, &S->bn, &S->nbz);
+    else if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, S->plan.bins, &S->bn);
 }
 
 // Launch sequence of rotations [r_lo, r_hi), plan.B rotations at a time.
@@ -797,9 +840,10 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
     using C = cplx<T>;
     const Geo& G = S.G;
     const int B = S.plan.B;
+    const bool fused_x = S.plan.bins == SPREAD_X;
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += B) {
         const int b = (int)std::min<int64_t>(B, r_hi - r0);
-        {
+        if (!fused_x) {
             PassTimer pt(ctx, SD_PASS_CLEAR, s, timed);
             CK(ctx, cudaMemsetAsync(S.b0, 0, (size_t)b * S.e0 * sizeof(C), s));
         }
@@ -818,15 +862,19 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         sa.out = S.b0;
         sa.out_rot_stride = S.e0;
         sa.n_full = G.n;
-        {
-            PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
-            if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
-            else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
-        }
         const int mx = S.pruned ? ROW_FWD_P : ROW_FWD;
         const int my = S.pruned ? COL_FWD_P : COL_FWD;
         const int mf = S.pruned ? COL_FUSED_P : COL_FUSED;
-        {
+        if (fused_x) {
+            // spreading and the forward x transform in one pass: no sub-box
+            PassTimer pt(ctx, SD_PASS_SPREAD_X, s, timed);
+            CK(ctx, launch_spread_x<T>(sa, S.bn, S.nbz, S.b1, S.e1, S.tw.n, b, s));
+        } else {
+            {
+                PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
+                if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
+                else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
+            }
             PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
             CK(ctx, pass_x_fwd<T>(G, S.tw, S.b0, S.e0, S.b1, S.e1, b, s, mx));
         }
@@ -914,8 +962,8 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     std::vector<Plan> cand;
     for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
         if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
-        for (int bins : {0, 8, 12, 16}) {
-            if (bins && !bins_supported(ctx)) continue;
+        for (int bins : {0, SPREAD_X, 8, 12, 16}) {
+            if (bins == SPREAD_X ? !spread_x_ok(ctx, *S) : (bins && !bins_supported(ctx))) continue;
             bool dup = false;
             for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
             if (!dup) cand.push_back(Plan{B, bins});
@@ -1202,6 +1250,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
+    else if (!strcmp(key, "spread_fused")) ctx->opt_spread_fused = (int)value;
     else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
     else if (!strcmp(key, "autotune")) ctx->opt_autotune = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
@@ -1462,7 +1511,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         std::string key(p, (size_t)(q - p));
         int B = 0, bins = -1;
         if (sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d}", &B, &bins) != 2 || B < 1 || B > 64 ||
-            (bins != 0 && bins != 8 && bins != 12 && bins != 16))
+            (bins != 0 && bins != SPREAD_X && bins != 8 && bins != 12 && bins != 16))
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
         got[key] = Plan{B, bins};
         p = q;
@@ -1484,6 +1533,8 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
         S.n_r = n_r;
         S.plan.B = choose_batch<T>(ctx, S.G, n_r);
         S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
+        S.pruned = ctx->opt_pruned && pruned_len_ok(S.G.n) && S.G.s <= S.G.N;
+        if (ctx->opt_spread_fused && spread_x_ok(ctx, S)) S.plan.bins = SPREAD_X;
         if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) {
             auto it = ctx->tuned.find(plan_key(ctx, S));
             if (it != ctx->tuned.end()) {

@@ -91,6 +91,16 @@ struct BinArgs {
 template <typename T>
 cudaError_t launch_spread_bins(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st);
 
+// Spreading fused with the forward x transform of the pruned 3D search (FP32,
+// w = 6, 2 s <= n): the samples are binned by the (y, z) of their tap box in
+// bins of SPREADX_TY x SPREADX_TZ cells (bn.nb = bins along y, nbz along z,
+// bn.nbins = nb * nbz), then each bin's CTA writes the N kept x modes of its
+// rows to out (batch x s^2 rows x N, row (y, z) at z s + y).  No sub-box.
+constexpr int SPREADX_TY = 8, SPREADX_TZ = 6;
+template <typename T>
+cudaError_t launch_spread_x(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, cplx<T>* out, int64_t out_rot_stride,
+                            const cplx<T>* tw, int batch, cudaStream_t st);
+
 // ---- line passes ------------------------------------------------------------
 // *_P modes are the pruned forward passes of the search: the sub-box is read
 // unshifted (cell a at position a, a < s <= n/2; the shift is a phase folded

@@ -533,6 +533,246 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
 }
 
 // ---------------------------------------------------------------------------
+// spreading fused with the forward x transform (3D, pruned search)
+// ---------------------------------------------------------------------------
+//
+// One CTA owns SX_TY x SX_TZ whole rows (y, z) of the sub-box, all x.  The
+// rotated samples are sorted into bins of SX_TY x SX_TZ (y, z) cells by the
+// first cell of their tap box, so the rows of bin (by, bz) receive taps only
+// from bins {by - 1, by} x {bz - 1, bz} (both sides are at least W - 1).  The
+// CTA accumulates those samples' taps, clipped to its rows, in a fixed-point
+// shared tile, then runs the pruned forward x transform of its rows straight
+// from the tile and writes the N kept modes of each row.  No sub-box is stored,
+// cleared or re-read, and no global atomic is issued.
+
+constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 8, SX_NT = 256, SX_CHUNK = 64;
+// staged record: wx[W] | ntaps | ny | base | pad | c * scale * wy * wz per clipped row (pairs)
+constexpr int SX_O_NT = SX_W, SX_O_NY = SX_W + 1, SX_O_BASE = SX_W + 2, SX_O_ROW = SX_W + 4;
+constexpr int SX_REC = SX_O_ROW + 2 * SX_W * SX_W;
+
+// Row pitch of the shared tile (cells): at least s and 6 mod 32, so that the
+// lanes of a warp on consecutive taps of one tap box (x fastest) fall in
+// distinct banks.
+__host__ __device__ inline int spread_x_pitch(int s) { return s + ((6 - s % 32) + 32) % 32; }
+
+template <int LEN>
+__host__ __device__ constexpr size_t spread_x_smem_fixed() {
+    // twiddles + the larger of the staging records and the FFT line buffer
+    return (size_t)tw_count(LEN) * sizeof(float2) +
+           ((size_t)SX_CHUNK * SX_REC * sizeof(float) > (size_t)SX_TR * line_pitch(LEN) * sizeof(float2)
+                ? (size_t)SX_CHUNK * SX_REC * sizeof(float)
+                : (size_t)SX_TR * line_pitch(LEN) * sizeof(float2));
+}
+__host__ inline size_t spread_x_smem(int len, int px) {
+    size_t fixed = 0;
+    switch (len) {
+#define SD_SXS(L) case L: fixed = spread_x_smem_fixed<L>(); break;
+        SD_FOR_EACH_LEN(SD_SXS)
+#undef SD_SXS
+    }
+    return (size_t)2 * SX_TY * SX_TZ * px * sizeof(int) + fixed;
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_bin_count_yz(SpreadArgs<T> a, BinArgs bn, int ty, int tz) {
+    __shared__ T Rm[9];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) load_rotation(a, b, Rm);
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.m) return;
+    int org[D];
+    sample_origin<T, D, W>(a, Rm, j, org);
+    const int bin = (org[2] / tz) * bn.nb + org[1] / ty;
+    const int64_t o = (int64_t)b * a.m + j;
+    bn.bin_of[o] = bin;
+    bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
+}
+
+template <int LEN>
+__global__ void __launch_bounds__(SX_NT, 2) k_spread_x(SpreadArgs<float> a, BinArgs bn, int nbz, int px,
+                                                       float2* out, int64_t out_rot_stride, const float2* twg) {
+    constexpr int W = SX_W, TY = SX_TY, TZ = SX_TZ, TR = SX_TR, NT = SX_NT, CHUNK = SX_CHUNK, REC = SX_REC;
+    constexpr int ROWS = TY * TZ;
+    constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int NH = LEN / 2;
+    constexpr int NWARP = NT / 32;
+    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+    constexpr int MAGIC_BITS = 0x4B400000;
+    extern __shared__ __align__(16) unsigned char sx_raw[];
+    int* tre = reinterpret_cast<int*>(sx_raw);
+    int* tim = tre + ROWS * px;
+    float2* tw = reinterpret_cast<float2*>(tim + ROWS * px);
+    float* stage = reinterpret_cast<float*>(tw + NTW);
+    float2* buf = reinterpret_cast<float2*>(tw + NTW);  // the same memory, after the accumulation
+    __shared__ float Rm[9];
+    __shared__ float wred[NWARP][2];
+    __shared__ unsigned char divtab[7][W * W];  // (rho / ny) << 4 | rho % ny
+    const int b = blockIdx.y;
+    const int nby = bn.nb;
+    const int by = (int)blockIdx.x % nby, bz = (int)blockIdx.x / nby;
+    const int y0 = by * TY, z0 = bz * TZ;
+    const int s = a.s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < ROWS * px; i += NT) {
+        tre[i] = 0;
+        tim[i] = 0;
+    }
+    for (int j = tid; j < NTW; j += NT) tw[j] = twg[j];
+    for (int i = tid; i < 7 * W * W; i += NT) {
+        const int ny = i / (W * W), rho = i % (W * W);
+        divtab[ny][rho] = ny ? (unsigned char)(((rho / ny) << 4) | (rho % ny)) : 0;
+    }
+    if (tid == 0) load_rotation(a, b, Rm);
+    // the source bins (by - {0, 1}) x (bz - {0, 1}) and their sample ranges
+    const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
+    __shared__ int src_lo[4], src_hi[4];
+    if (tid < 4) {
+        const int yy = by - (tid & 1), zz = bz - (tid >> 1);
+        src_lo[tid] = src_hi[tid] = 0;
+        if (yy >= 0 && zz >= 0) {
+            src_lo[tid] = off[zz * nby + yy];
+            src_hi[tid] = off[zz * nby + yy + 1];
+        }
+    }
+    __syncthreads();
+    const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
+    float2* outb = out + (int64_t)b * out_rot_stride;
+    if (src_hi[0] - src_lo[0] + src_hi[1] - src_lo[1] + src_hi[2] - src_lo[2] + src_hi[3] - src_lo[3] == 0) {
+        // no sample reaches these rows: their modes are zero
+        for (int i = tid; i < ROWS * (NH / 2); i += NT) {
+            const int l = i / (NH / 2), k = i % (NH / 2);
+            const int y = y0 + l % TY, z = z0 + l / TY;
+            if (y < s && z < s)
+                reinterpret_cast<float4*>(outb + ((int64_t)z * s + y) * NH)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+    // fixed point: taps below 2^21, a cell's sum (at most the sum of |c| over the
+    // source samples, the weights being <= 1) below 2^30
+    {
+        float mx = 0.f, sm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            for (int p = src_lo[k] + tid; p < src_hi[k]; p += NT) {
+                const float2 c = a.c[sorted[p]];
+                const float v = fmaxf(fabsf(c.x), fabsf(c.y));
+                mx = fmaxf(mx, v);
+                sm += v;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            sm += __shfl_down_sync(0xffffffffu, sm, o);
+        }
+        if (lane == 0) {
+            wred[warp][0] = mx;
+            wred[warp][1] = sm;
+        }
+    }
+    __syncthreads();
+    float mx = 0.f, sm = 0.f;
+    for (int w = 0; w < NWARP; ++w) {
+        mx = fmaxf(mx, wred[w][0]);
+        sm += wred[w][1];
+    }
+    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
+    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
+    const int se = sm > 0.f ? min(max(127 + min(21 - emx, 30 - esm), 1), 254) : 127;
+    const float scale = __int_as_float(se << 23);
+    const float inv_scale = 1.f / scale;  // a power of two: exact
+    // this lane's tap in each round of a full tap box: x tap and row (ky + ny kz flattened)
+    constexpr int ROUNDS = (W * W * W + 31) / 32;
+    int kx_of[ROUNDS], rho_of[ROUNDS];
+#pragma unroll
+    for (int q = 0; q < ROUNDS; ++q) {
+        const int tap = min(q * 32 + lane, W * W * W - 1);
+        kx_of[q] = tap % W;
+        rho_of[q] = tap / W;
+    }
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        for (int p0 = src_lo[k]; p0 < src_hi[k]; p0 += CHUNK) {
+            const int nj = min(CHUNK, src_hi[k] - p0);
+            if (tid < nj) {
+                int org[3];
+                float wt[3][W];
+                float2 c;
+                sample_taps<float, 3, W>(a, Rm, sorted[p0 + tid], org, wt, c);
+                // tap rows clipped to this CTA's rows
+                const int ly = max(0, y0 - org[1]), hy = min(W, y0 + TY - org[1]);
+                const int lz = max(0, z0 - org[2]), hz = min(W, z0 + TZ - org[2]);
+                const int ny = hy - ly, nz = hz - lz;
+                float* r = stage + tid * REC;
+#pragma unroll
+                for (int q = 0; q < W; ++q) r[q] = wt[0][q];
+                const bool any = ny > 0 && nz > 0;
+                r[SX_O_NT] = __int_as_float(any ? W * ny * nz : 0);
+                r[SX_O_NY] = __int_as_float(ny);
+                r[SX_O_BASE] = __int_as_float(((org[2] + lz - z0) * TY + (org[1] + ly - y0)) * px + org[0]);
+                if (any) {
+                    const float cx = c.x * scale, cy = c.y * scale;
+#pragma unroll
+                    for (int kz = 0; kz < W; ++kz)
+#pragma unroll
+                        for (int ky = 0; ky < W; ++ky)
+                            if (kz >= lz && kz < hz && ky >= ly && ky < hy) {
+                                const int rho = (kz - lz) * ny + (ky - ly);
+                                const float wyz = wt[1][ky] * wt[2][kz];
+                                r[SX_O_ROW + 2 * rho] = cx * wyz;
+                                r[SX_O_ROW + 2 * rho + 1] = cy * wyz;
+                            }
+                }
+            }
+            __syncthreads();
+            // the warps add the staged samples round-robin, lanes on consecutive taps
+            for (int j = warp; j < nj; j += NWARP) {
+                const float* r = stage + j * REC;
+                const int ntaps = __float_as_int(r[SX_O_NT]);
+                const int ny = __float_as_int(r[SX_O_NY]);
+                const int base = __float_as_int(r[SX_O_BASE]);
+                const unsigned char* dv = divtab[ny];
+#pragma unroll
+                for (int q = 0; q < ROUNDS; ++q) {
+                    if (q * 32 >= ntaps) break;  // uniform over the warp
+                    if (q * 32 + lane < ntaps) {
+                        const int rho = rho_of[q];
+                        const int d = dv[rho];
+                        const int cell = base + kx_of[q] + ((d >> 4) * TY + (d & 15)) * px;
+                        const float wx = r[kx_of[q]];
+                        const float2 cw = *reinterpret_cast<const float2*>(r + SX_O_ROW + 2 * rho);
+                        atomicAdd(tre + cell, __float_as_int(fmaf(cw.x, wx, MAGIC)) - MAGIC_BITS);
+                        atomicAdd(tim + cell, __float_as_int(fmaf(cw.y, wx, MAGIC)) - MAGIC_BITS);
+                    }
+                }
+            }
+            __syncthreads();  // the stage is refilled by the next chunk
+        }
+    }
+    // forward x transform of the rows, TR at a time (row l: y = y0 + l % TY, z = z0 + l / TY)
+    const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int g = 0; g < ROWS / TR; ++g) {
+        auto load = [&](int line, int i, int r) -> float2 {
+            const int l = g * TR + line;
+            const int pos = i + r * NB1;
+            const int y = y0 + l % TY, z = z0 + l / TY;
+            if (y >= s || z >= s || pos >= s) return zero;
+            return make_float2((float)tre[l * px + pos] * inv_scale, (float)tim[l * px + pos] * inv_scale);
+        };
+        auto emit = [&](int line, int i, int r, float2 v) {
+            const int l = g * TR + line;
+            const int y = y0 + l % TY, z = z0 + l / TY;
+            if (kept_out<LEN>(r) && y < s && z < s)
+                outb[((int64_t)z * s + y) * NH + i + kept_slot<LEN>(r)] = v;
+        };
+        fftp_lines<float2, LEN, false, TR, NT, LAY_ROW, true, false, true>(buf, LD, tw, load, emit);
+        __syncthreads();  // buf is rewritten by the next group
+    }
+}
+
+// ---------------------------------------------------------------------------
 // line passes: the first FFT stage reads global memory into registers and the
 // last stage writes global memory from registers; stages in between (and the
 // product step of the fused pass) go through shared memory
@@ -1139,6 +1379,47 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
     }
 }
 
+// Spreading fused with the forward x transform: bins over (y, z), then one CTA
+// per bin writes the kept x modes of its rows (out: batch x s^2 x N).
+template <typename T>
+cudaError_t launch_spread_x_t(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, cplx<T>* out,
+                              int64_t out_rot_stride, const cplx<T>* tw, int batch, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (a.w != SX_W || 2 * a.s > a.n_full) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
+        if (e != cudaSuccess) return e;
+        const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
+        if (a.m > 0) {
+            k_bin_count_yz<float, 3, SX_W><<<gpts, 256, 0, st>>>(a, bn, SX_TY, SX_TZ);
+            k_bin_scan<<<batch, 1024, 0, st>>>(bn);
+            k_bin_scatter<float><<<gpts, 256, 0, st>>>(a.m, bn);
+            note_launch(3);
+        } else {
+            k_bin_scan<<<batch, 1024, 0, st>>>(bn);
+            note_launch();
+        }
+        const int px = spread_x_pitch(a.s);
+        const size_t smem = spread_x_smem(a.n_full, px);
+        switch (a.n_full) {
+#define SD_SX_CASE(L)                                                                                    \
+    case L: {                                                                                            \
+        auto kern = k_spread_x<L>;                                                                       \
+        e = set_smem(kern, smem);                                                                        \
+        if (e != cudaSuccess) return e;                                                                  \
+        kern<<<dim3((unsigned)bn.nbins, batch), SX_NT, smem, st>>>(a, bn, nbz, px, out, out_rot_stride, tw); \
+        note_launch();                                                                                   \
+        return cudaGetLastError();                                                                       \
+    }
+            SD_FOR_EACH_PLEN(SD_SX_CASE)
+#undef SD_SX_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // small kernels
 // ---------------------------------------------------------------------------
@@ -1261,6 +1542,10 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn,
     template <> cudaError_t launch_spread_bins<T>(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, \
                                                   cudaStream_t st) {                                    \
         return launch_spread_bins_t<T>(a, bn, dim, batch, st);                                          \
+    }                                                                                                   \
+    template <> cudaError_t launch_spread_x<T>(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, cplx<T>* out, \
+                                               int64_t ors, const cplx<T>* tw, int batch, cudaStream_t st) {   \
+        return launch_spread_x_t<T>(a, bn, nbz, out, ors, tw, batch, st);                               \
     }                                                                                                   \
     template <> cudaError_t launch_twiddles<T>(cplx<T>* tw, int len, cudaStream_t st) {                 \
         return launch_twiddles_t<T>(tw, len, st);                                                       \

@@ -133,7 +133,7 @@ _SIGS = {
     "sd_pass_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
 }
 
-PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph"]
+PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph", "spread_x"]
 
 
 def library_path() -> str:

@@ -209,6 +209,37 @@ def test_pruned_and_full_forward_passes_agree(name, prec, N):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [48, 64])
+def test_fused_spreading_matches_oracle(N):
+    # spreading fused with the forward x transform: each CTA accumulates whole
+    # x rows of a (y, z) block in shared memory and transforms them there
+    # (tiny_3d: N = 48 puts the sub-box at s = N, the edge of the pruned path)
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w, "f32")
+    ctx.set_option("spread_fused", 1)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    assert ctx.search_plan(mv, g, w.n_rot)["spread_bins"] == 1
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], ref[r]) < TOL["f32"], r
+    s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g)))
+    for r in range(w.n_rot):
+        assert abs(s[r] - maps[r].real.max()) <= 1e-6 * np.abs(maps[r].real).max()
+        if top1_margin_ok(ref[r].real):
+            assert idx[r] == int(np.argmax(ref[r].real))
+    # the same maps as the other spreading paths (fixed point, so exact up to FP32 rounding of the passes)
+    ctx.set_option("spread_fused", 0)
+    other = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], other[r]) < 2e-6, r
+    ctx.close()
+
+
 def test_maps_full_size_peg_in_bore():
     # 128^3 translations, n = 256 oversampled grid, ~50,000 samples per shape;
     # weights are seeded synthetic values shared by both sides.
