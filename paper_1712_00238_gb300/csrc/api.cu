@@ -506,6 +506,7 @@ static void bins_layout(void* p, int s, int dim, int64_t m, int batch, int tb, B
     bn->rank = q;
     q += (size_t)batch * m;
     bn->sorted = q;
+    bn->org = nullptr;  // tiles re-evaluate the origin (with a safety net)
 }
 
 static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, int tb, BinArgs* bn) {
@@ -529,7 +530,7 @@ static int spread_x_bins(int s, int* nby, int* nbz) {
 static size_t bins_bytes_x(int s, int64_t m, int batch) {
     int nby, nbz;
     const int nbins = spread_x_bins(s, &nby, &nbz);
-    return ((size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m) * sizeof(int);
+    return ((size_t)batch * (2 * (size_t)nbins + 1) + 4 * (size_t)batch * (size_t)m) * sizeof(int);
 }
 static void bins_layout_x(void* p, int s, int64_t m, int batch, BinArgs* bn, int* nbz) {
     int nby;
@@ -547,6 +548,8 @@ static void bins_layout_x(void* p, int s, int64_t m, int batch, BinArgs* bn, int
     bn->rank = q;
     q += (size_t)batch * m;
     bn->sorted = q;
+    q += (size_t)batch * m;
+    bn->org = q;
 }
 
 // Binned spreading exists for FP32 and kernel widths 4-7 (tiles of tb + w - 1 cells).

@@ -85,6 +85,7 @@ struct BinArgs {
     int* bin_of;          // batch x m
     int* rank;            // batch x m
     int32_t* sorted;      // batch x m: sample indices in bin order
+    int32_t* org;         // batch x m: packed tap-box origin (x | y << 10 | z << 20), fused spreading only
 };
 // Spread by bins; accumulates into the batch's sub-boxes, which must be cleared first.
 // Supports w = 4..7 and tb = 8, 12, 16 (shared tile of (tb + w - 1)^d cells).

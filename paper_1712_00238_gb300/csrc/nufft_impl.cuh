@@ -546,9 +546,9 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
 // cleared or re-read, and no global atomic is issued.
 
 constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 8, SX_NT = 256, SX_CHUNK = 64;
-// staged record: wx[W] | ntaps | ny | base | pad | c * scale * wy * wz per clipped row (pairs)
-constexpr int SX_O_NT = SX_W, SX_O_NY = SX_W + 1, SX_O_BASE = SX_W + 2, SX_O_ROW = SX_W + 4;
-constexpr int SX_REC = SX_O_ROW + 2 * SX_W * SX_W;
+// staged record: w[axis][W] | origin[3] | c * scale (pair)
+constexpr int SX_O_ORG = 3 * SX_W, SX_O_C = 3 * SX_W + 4;
+constexpr int SX_REC = SX_O_C + 2;
 
 // Row pitch of the shared tile (cells): at least s and 6 mod 32, so that the
 // lanes of a warp on consecutive taps of one tap box (x fastest) fall in
@@ -586,11 +586,12 @@ __global__ void __launch_bounds__(256) k_bin_count_yz(SpreadArgs<T> a, BinArgs b
     const int bin = (org[2] / tz) * bn.nb + org[1] / ty;
     const int64_t o = (int64_t)b * a.m + j;
     bn.bin_of[o] = bin;
+    bn.org[o] = org[0] | (org[1] << 10) | (org[2] << 20);  // the spreading uses this very origin
     bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
 }
 
 template <int LEN>
-__global__ void __launch_bounds__(SX_NT, 2) k_spread_x(SpreadArgs<float> a, BinArgs bn, int nbz, int px,
+__global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinArgs bn, int nbz, int px,
                                                        float2* out, int64_t out_rot_stride, const float2* twg) {
     constexpr int W = SX_W, TY = SX_TY, TZ = SX_TZ, TR = SX_TR, NT = SX_NT, CHUNK = SX_CHUNK, REC = SX_REC;
     constexpr int ROWS = TY * TZ;
@@ -695,55 +696,60 @@ __global__ void __launch_bounds__(SX_NT, 2) k_spread_x(SpreadArgs<float> a, BinA
     for (int k = 0; k < 4; ++k) {
         for (int p0 = src_lo[k]; p0 < src_hi[k]; p0 += CHUNK) {
             const int nj = min(CHUNK, src_hi[k] - p0);
-            if (tid < nj) {
-                int org[3];
-                float wt[3][W];
-                float2 c;
-                sample_taps<float, 3, W>(a, Rm, sorted[p0 + tid], org, wt, c);
-                // tap rows clipped to this CTA's rows
-                const int ly = max(0, y0 - org[1]), hy = min(W, y0 + TY - org[1]);
-                const int lz = max(0, z0 - org[2]), hz = min(W, z0 + TZ - org[2]);
-                const int ny = hy - ly, nz = hz - lz;
-                float* r = stage + tid * REC;
+            // four threads per sample: the kernel weights of one axis each, and c
+            {
+                const int j = tid >> 2, part = tid & 3;
+                if (j < nj) {
+                    const int64_t js = sorted[p0 + j];
+                    float* r = stage + j * REC;
+                    if (part < 3) {
+                        // the origin the binning pass used, and the weights about it
+                        const int o = (bn.org[(int64_t)b * a.m + js] >> (10 * part)) & 1023;
+                        const float4 p = a.pos[js];
+                        const float y = a.sign * (Rm[3 * part] * p.x + Rm[3 * part + 1] * p.y + Rm[3 * part + 2] * p.z);
+                        const float g = y * a.inv_h;
+                        const int u0 = o - a.s_h;
 #pragma unroll
-                for (int q = 0; q < W; ++q) r[q] = wt[0][q];
-                const bool any = ny > 0 && nz > 0;
-                r[SX_O_NT] = __int_as_float(any ? W * ny * nz : 0);
-                r[SX_O_NY] = __int_as_float(ny);
-                r[SX_O_BASE] = __int_as_float(((org[2] + lz - z0) * TY + (org[1] + ly - y0)) * px + org[0]);
-                if (any) {
-                    const float cx = c.x * scale, cy = c.y * scale;
-#pragma unroll
-                    for (int kz = 0; kz < W; ++kz)
-#pragma unroll
-                        for (int ky = 0; ky < W; ++ky)
-                            if (kz >= lz && kz < hz && ky >= ly && ky < hy) {
-                                const int rho = (kz - lz) * ny + (ky - ly);
-                                const float wyz = wt[1][ky] * wt[2][kz];
-                                r[SX_O_ROW + 2 * rho] = cx * wyz;
-                                r[SX_O_ROW + 2 * rho + 1] = cy * wyz;
-                            }
+                        for (int q = 0; q < W; ++q) {
+                            const float zz = ((float)(u0 + q) - g) * (2.f / W);
+                            const float z2 = zz * zz;
+                            r[part * W + q] = (z2 <= 1.f) ? exp(a.beta * (sqrt(1.f - z2) - 1.f)) : 0.f;
+                        }
+                        r[SX_O_ORG + part] = __int_as_float(o);
+                    } else {
+                        const float2 c = a.c[js];
+                        r[SX_O_C] = c.x * scale;
+                        r[SX_O_C + 1] = c.y * scale;
+                    }
                 }
             }
             __syncthreads();
             // the warps add the staged samples round-robin, lanes on consecutive taps
+            // of the sample's tap box clipped to this CTA's rows
             for (int j = warp; j < nj; j += NWARP) {
                 const float* r = stage + j * REC;
-                const int ntaps = __float_as_int(r[SX_O_NT]);
-                const int ny = __float_as_int(r[SX_O_NY]);
-                const int base = __float_as_int(r[SX_O_BASE]);
+                const int ox = __float_as_int(r[SX_O_ORG]);
+                const int oy = __float_as_int(r[SX_O_ORG + 1]);
+                const int oz = __float_as_int(r[SX_O_ORG + 2]);
+                const int ly = max(0, y0 - oy), hy = min(W, y0 + TY - oy);
+                const int lz = max(0, z0 - oz), hz = min(W, z0 + TZ - oz);
+                const int ny = hy - ly, nz = hz - lz;
+                if (ny <= 0 || nz <= 0) continue;  // uniform over the warp
+                const int ntaps = W * ny * nz;
+                const int base = ((oz + lz - z0) * TY + (oy + ly - y0)) * px + ox;
+                const float cx = r[SX_O_C], cy = r[SX_O_C + 1];
                 const unsigned char* dv = divtab[ny];
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
                     if (q * 32 >= ntaps) break;  // uniform over the warp
                     if (q * 32 + lane < ntaps) {
-                        const int rho = rho_of[q];
-                        const int d = dv[rho];
-                        const int cell = base + kx_of[q] + ((d >> 4) * TY + (d & 15)) * px;
-                        const float wx = r[kx_of[q]];
-                        const float2 cw = *reinterpret_cast<const float2*>(r + SX_O_ROW + 2 * rho);
-                        atomicAdd(tre + cell, __float_as_int(fmaf(cw.x, wx, MAGIC)) - MAGIC_BITS);
-                        atomicAdd(tim + cell, __float_as_int(fmaf(cw.y, wx, MAGIC)) - MAGIC_BITS);
+                        const int d = dv[rho_of[q]];
+                        const int ky = d & 15, kz = d >> 4;
+                        const int kx = kx_of[q];
+                        const int cell = base + kx + (kz * TY + ky) * px;
+                        const float w = r[kx] * r[W + ly + ky] * r[2 * W + lz + kz];
+                        atomicAdd(tre + cell, __float_as_int(fmaf(cx, w, MAGIC)) - MAGIC_BITS);
+                        atomicAdd(tim + cell, __float_as_int(fmaf(cy, w, MAGIC)) - MAGIC_BITS);
                     }
                 }
             }
