@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=0, help="rotations per batch (0: automatic)")
-    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: replay each search's launch sequence from a captured CUDA graph")
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
     ap.add_argument("--spread-direct", type=int, default=1,
                     help="with --autotune 0: 1 global vector atomics, 0 spread by bins")
@@ -318,14 +319,15 @@ def run_ours(args):
             out = (poses, hist)
         return times, out
 
-    # warm-up (also captures the search graph on this stream)
+    # warm-up (also captures the search graph on this stream); pass timing is on
+    # from here so that the graph carries its pass events as nodes
+    ctx.set_option("timing", 1)
     timed_steps(max(args.warmup, 0), False)
 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
-    ctx.set_option("timing", 1)
     ctx.pass_times(reset=True)
     for k in phase_ms:
         phase_ms[k] = 0.0
@@ -334,7 +336,6 @@ def run_ours(args):
     launches = sd.launch_count() - l0
     phases = {k: round(v / max(args.steps, 1), 3) for k, v in phase_ms.items()}
     ptimes = ctx.pass_times(reset=True)
-    ctx.set_option("timing", 0)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     # end to end: the same steps with inputs copied from pinned host memory (at most
@@ -478,13 +479,12 @@ def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# search passes from one ncu capture of a 34-rotation launch of this workload,
-# keyed by (pass, sub-box side, N, rotations per launch); a launch of another
-# shape reports null.
+# search passes from one ncu capture of the current kernels, keyed by (pass,
+# sub-box side, N, rotations per launch); a launch of another shape reports
+# null.  Docking pair: one 20-rotation launch of the pruned fused pass, whose
+# product table is read from DRAM once per launch (its other rotations hit L2).
 TRAFFIC_PER_LAUNCH: dict = {
-    ("fused", 108, 128, 34): 554573824 + 527024896,
-    ("fwd_y", 108, 128, 34): 406127104 + 432105984,
-    ("inv_y", 108, 128, 34): 570511360 + 506710784,
+    ("fused", 156, 192, 20): 976803840 + 1081333248,
 }
 
 

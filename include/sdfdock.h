@@ -452,9 +452,12 @@ int64_t sd_launch_count(void);
 #define SD_PASS_COUNT 10
 
 /* With the context option "timing" = 1, every pass launch of the search is
- * bracketed by CUDA events on its stream.  Returns the number of timed
- * launches and their summed device time (ms) for `kind`; synchronises on the
- * recorded events.  kind < 0 resets the totals. */
+ * bracketed by CUDA events on its stream; a search replayed from a captured
+ * graph (option "graph") carries those events as event-record nodes of the
+ * graph, and each replay's times are read back before the graph's next replay
+ * (the graph is captured separately with and without timing).  Returns the
+ * number of timed launches and their summed device time (ms) for `kind`;
+ * synchronises on the recorded events.  kind < 0 resets the totals. */
 int sd_pass_times(sd_ctx* ctx, int kind, int64_t* launches, double* ms);
 
 #ifdef __cplusplus

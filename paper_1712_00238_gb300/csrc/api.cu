@@ -40,9 +40,16 @@ struct Prep {  // fixed-shape tables for one grid
     std::vector<std::pair<int, void*>> Wsh;
 };
 
+struct TimerRec {
+    int kind;
+    cudaEvent_t a, b;
+    bool pooled = true;  // false: the events belong to a captured graph
+};
+
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> events;  // event nodes of a multi-job graph (owned)
+    std::vector<TimerRec> timers;     // pass-timing event nodes (owned), read back after each replay
     long long kernels = 0;            // kernel launches captured (counted again at every replay)
 };
 
@@ -52,15 +59,11 @@ struct Plan {      // launch plan of one scoring job
                    // 1: spreading fused with the forward x transform (SPREAD_X)
 };
 
-struct TimerRec {
-    int kind;
-    cudaEvent_t a, b;
-};
-
 struct sd_ctx {
     int device = 0;
     int opt_timing = 0;
     std::vector<TimerRec> pending;       // event pairs not yet read back
+    std::vector<TimerRec>* capture_timers = nullptr;  // while capturing a graph with "timing" on
     std::vector<cudaEvent_t> event_pool;
     double pass_ms[SD_PASS_COUNT] = {};
     int64_t pass_n[SD_PASS_COUNT] = {};
@@ -101,7 +104,8 @@ static std::atomic<long long> g_launches{0};
 void sd::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // CUDA-event timing of one pass launch on the stream (when the context's
-// "timing" option is on and no graph is being captured).
+// "timing" option is on).  While a graph is captured the two events become
+// event-record nodes of the graph, read back after each of its replays.
 static cudaEvent_t pool_event(sd_ctx* ctx) {
     if (!ctx->event_pool.empty()) {
         cudaEvent_t e = ctx->event_pool.back();
@@ -122,13 +126,31 @@ struct PassTimer {
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     PassTimer(sd_ctx* c, int k, cudaStream_t s, bool on) : ctx(c), kind(k), st(s) {
-        if (on && c->opt_timing) {
-            a = pool_event(c);
-            if (a) cudaEventRecord(a, s);
+        if (!on || !c->opt_timing) return;
+        if (c->capture_timers) {
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecordWithFlags(a, s, cudaEventRecordExternal) != cudaSuccess) {
+                if (a) cudaEventDestroy(a);
+                a = nullptr;
+                cudaGetLastError();
+            }
+            return;
         }
+        a = pool_event(c);
+        if (a) cudaEventRecord(a, s);
     }
     ~PassTimer() {
         if (!a) return;
+        if (ctx->capture_timers) {
+            cudaEvent_t b = nullptr;
+            if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecordWithFlags(b, st, cudaEventRecordExternal) != cudaSuccess) {
+                if (b) cudaEventDestroy(b);
+                cudaEventDestroy(a);
+                cudaGetLastError();
+                return;
+            }
+            ctx->capture_timers->push_back({kind, a, b, false});
+            return;
+        }
         cudaEvent_t b = pool_event(ctx);
         if (!b) return;
         cudaEventRecord(b, st);
@@ -145,8 +167,10 @@ static void harvest_timers(sd_ctx* ctx) {
         } else {
             cudaGetLastError();
         }
-        ctx->event_pool.push_back(r.a);
-        ctx->event_pool.push_back(r.b);
+        if (r.pooled) {
+            ctx->event_pool.push_back(r.a);
+            ctx->event_pool.push_back(r.b);
+        }
     }
     ctx->pending.clear();
 }
@@ -204,11 +228,18 @@ void sd::pool_free(void* p, cudaStream_t st) {
 
 // Captured graphs hold raw workspace and table pointers: drop them before any
 // of those buffers is freed.
-static void drop_graphs(sd_ctx* ctx) {
-    for (auto& kv : ctx->graphs) {
-        cudaGraphExecDestroy(kv.second.exec);
-        for (auto e : kv.second.events) cudaEventDestroy(e);
+static void release_graph(GraphEntry& g) {
+    cudaGraphExecDestroy(g.exec);
+    for (auto e : g.events) cudaEventDestroy(e);
+    for (auto& t : g.timers) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
     }
+}
+
+static void drop_graphs(sd_ctx* ctx) {
+    harvest_timers(ctx);  // pending reads may name a graph's timing events
+    for (auto& kv : ctx->graphs) release_graph(kv.second);
     ctx->graph_order.clear();
     ctx->graphs.clear();
     ctx->seen.clear();
@@ -223,8 +254,8 @@ static std::map<std::string, GraphEntry>::iterator keep_graph(sd_ctx* ctx, const
     while (ctx->graphs.size() >= kMaxGraphs && !ctx->graph_order.empty()) {
         auto old = ctx->graphs.find(ctx->graph_order.front());
         if (old != ctx->graphs.end()) {
-            cudaGraphExecDestroy(old->second.exec);
-            for (auto e : old->second.events) cudaEventDestroy(e);
+            if (!old->second.timers.empty()) harvest_timers(ctx);
+            release_graph(old->second);
             ctx->graphs.erase(old);
         }
         ctx->graph_order.pop_front();
@@ -1028,31 +1059,52 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
 
     if (ctx->opt_graph && !ctx->opt_plain && st != nullptr) {
         char key[256];
-        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d", (const void*)fixed, (const void*)moving,
-                 (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B, S.plan.bins);
+        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d|%d|%d", (const void*)fixed,
+                 (const void*)moving, (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B,
+                 S.plan.bins, (int)S.pruned, ctx->opt_timing);
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
             if (ctx->seen[k]++ == 0) return search_enqueue(ctx, S, 0, n_r, st, true);  // first call runs eagerly
             cudaGraph_t graph;
             const long long l0 = g_launches.load();
+            std::vector<TimerRec> timers;  // with "timing" on: pass events as graph nodes
             CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = search_enqueue(ctx, S, 0, n_r, st, false);
+            ctx->capture_timers = ctx->opt_timing ? &timers : nullptr;
+            int rc = search_enqueue(ctx, S, 0, n_r, st, ctx->opt_timing != 0);
+            ctx->capture_timers = nullptr;
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
-            if (rc != SD_OK) return rc;
-            CK(ctx, ec);
             GraphEntry ge;
+            ge.timers = timers;
+            if (rc != SD_OK || ec != cudaSuccess) {
+                ge.exec = nullptr;
+                for (auto& t : ge.timers) {
+                    cudaEventDestroy(t.a);
+                    cudaEventDestroy(t.b);
+                }
+                if (ec == cudaSuccess) cudaGraphDestroy(graph);
+                if (rc != SD_OK) return rc;
+                CK(ctx, ec);
+            }
             ge.kernels = g_launches.load() - l0;
             g_launches.fetch_sub(ge.kernels);  // counted when the graph runs
             ec = cudaGraphInstantiate(&ge.exec, graph, 0);
             cudaGraphDestroy(graph);
+            if (ec != cudaSuccess)
+                for (auto& t : ge.timers) {
+                    cudaEventDestroy(t.a);
+                    cudaEventDestroy(t.b);
+                }
             CK(ctx, ec);
             it = keep_graph(ctx, k, ge);
         }
+        // the graph's pass events still hold its previous replay: read them first
+        if (!it->second.timers.empty()) harvest_timers(ctx);
         {
             PassTimer pt(ctx, SD_PASS_GRAPH, st, true);
             CK(ctx, cudaGraphLaunch(it->second.exec, st));
         }
+        for (auto& t : it->second.timers) ctx->pending.push_back(t);
         note_launch((int)it->second.kernels);
         return SD_OK;
     }

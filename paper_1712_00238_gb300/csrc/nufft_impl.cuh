@@ -1115,6 +1115,84 @@ __global__ void __launch_bounds__(cta_threads<T, LENF>(), MB) k_cols_fused_p(Col
     cols_fused_p_body<T, LENF>(a);
 }
 
+// Inverse y (3D), in place: columns of N points, full input and output.  Each
+// CTA reads its columns completely in the first stage before any write.
+template <typename T, int LEN>
+__device__ __forceinline__ void cols_inv_p_body(const ColArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LEN>();
+    constexpr int NT = cta_threads<T, LEN>();
+    constexpr int LD = col_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int PL = LEN / plan_last_radix(LEN);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TC * LD;
+    const int col0 = blockIdx.x * TC;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.twF[j];
+    __syncthreads();
+    const int ncols = a.ncols;
+    const int ncl = ncols - col0;
+    const C* in = a.in + (int64_t)blockIdx.z * a.in_rot_stride + (int64_t)blockIdx.y * a.in_outer_stride + col0;
+    C* out = a.out + (int64_t)blockIdx.z * a.out_rot_stride + (int64_t)blockIdx.y * a.out_outer_stride + col0;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C { return line < ncl ? in[(i + r * NB1) * ncols + line] : zero; };
+    auto emit = [&](int line, int i, int r, C v) {
+        if (line < ncl) out[(i + r * PL) * ncols + line] = v;
+    };
+    fftp_lines<C, LEN, true, TC, NT, LAY_COL, false, false, false>(buf, LD, tw, load, emit);
+}
+
+template <typename T, int LEN>
+__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_cols_inv_p(ColArgs<T> a) {
+    cols_inv_p_body<T, LEN>(a);
+}
+
+// Inverse x of rows of N points: the per-block argmax of the real part (ties to
+// the lowest index) or the complex map.
+template <typename T, int LEN, int MODE>
+__device__ __forceinline__ void rows_inv_p_body(const RowArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int PL = LEN / plan_last_radix(LEN);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TR * LD;
+    const int row0 = blockIdx.x * TR;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
+    __syncthreads();
+    const C* in = a.in + (int64_t)blockIdx.y * a.in_rot_stride + (int64_t)row0 * LEN;
+    const int nrows = a.nrows - row0;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C { return line < nrows ? in[line * LEN + i + r * NB1] : zero; };
+    T best = -INFINITY;
+    int bidx = INT_MAX;
+    C* out = (MODE == ROW_INV_MAP) ? a.out + (int64_t)blockIdx.y * a.out_rot_stride + (int64_t)row0 * LEN : nullptr;
+    auto emit = [&](int line, int i, int r, C v) {
+        if (line >= nrows) return;
+        if constexpr (MODE == ROW_INV_ARGMAX) argmax_merge(best, bidx, v.x, (row0 + line) * LEN + i + r * PL);
+        else out[line * LEN + i + r * PL] = v;
+    };
+    fftp_lines<C, LEN, true, TR, cta_threads<T, LEN>(), LAY_ROW, true, false, false>(buf, LD, tw, load, emit);
+    if constexpr (MODE == ROW_INV_ARGMAX) {
+        block_argmax(best, bidx);
+        if (threadIdx.x == 0) {
+            const int64_t o = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+            a.part_score[o] = (double)best;
+            a.part_idx[o] = bidx;
+        }
+    }
+}
+
+template <typename T, int LEN, int MODE>
+__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_p(RowArgs<T> a) {
+    rows_inv_p_body<T, LEN, MODE>(a);
+}
+
 // Resident CTAs per SM the pruned passes are compiled for (0: the compiler's choice).
 // 512-point FP32 lines (256 threads, two butterflies each) take 2 (at most 128
 // registers; 146 otherwise); 384-point ones 3 (384 threads: at most 56).
@@ -1262,8 +1340,52 @@ static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_
     return cudaGetLastError();
 }
 
+template <typename T, int LEN, int MODE>
+static cudaError_t rows_inv_p_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    const int nb = (a.nrows + TR - 1) / TR;
+    if (nparts) *nparts = nb;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    if (a.in_row_stride != LEN || (MODE == ROW_INV_MAP && a.out_row_stride != LEN)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C);
+    auto kern = k_rows_inv_p<T, LEN, MODE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, batch), cta_threads<T, LEN>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int LEN>
+static cudaError_t cols_inv_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    constexpr int TC = lines_per_cta<T, LEN>();
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
+    const size_t smem = (size_t)(TC * col_pitch(LEN) + tw_count(LEN)) * sizeof(C);
+    auto kern = k_cols_inv_p<T, LEN>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LEN>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_rows_t(int mode, const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    if (mode == ROW_INV_ARGMAX || mode == ROW_INV_MAP) {
+        switch (a.N) {
+#define SD_ROWI_CASE(L)                                                                                    \
+    case L:                                                                                                \
+        return mode == ROW_INV_ARGMAX ? rows_inv_p_impl<T, L, ROW_INV_ARGMAX>(a, batch, nparts, st)       \
+                                      : rows_inv_p_impl<T, L, ROW_INV_MAP>(a, batch, nparts, st);
+            SD_ROWI_CASE(8) SD_ROWI_CASE(16) SD_ROWI_CASE(24) SD_ROWI_CASE(32) SD_ROWI_CASE(48) SD_ROWI_CASE(64)
+            SD_ROWI_CASE(96) SD_ROWI_CASE(128) SD_ROWI_CASE(192) SD_ROWI_CASE(256)
+#undef SD_ROWI_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
     if (mode == ROW_FWD_P) {
         if (nparts) *nparts = 0;
         switch (a.n) {
@@ -1309,6 +1431,16 @@ cudaError_t launch_cols_t(int mode, const ColArgs<T>& a, int batch, cudaStream_t
             SD_FUSED_CASE(8) SD_FUSED_CASE(16) SD_FUSED_CASE(24) SD_FUSED_CASE(32) SD_FUSED_CASE(48)
             SD_FUSED_CASE(64) SD_FUSED_CASE(96) SD_FUSED_CASE(128) SD_FUSED_CASE(192) SD_FUSED_CASE(256)
 #undef SD_FUSED_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (mode == COL_INV) {
+        switch (a.N) {
+#define SD_COLI_CASE(L) \
+    case L: return cols_inv_p_impl<T, L>(a, batch, st);
+            SD_COLI_CASE(8) SD_COLI_CASE(16) SD_COLI_CASE(24) SD_COLI_CASE(32) SD_COLI_CASE(48) SD_COLI_CASE(64)
+            SD_COLI_CASE(96) SD_COLI_CASE(128) SD_COLI_CASE(192) SD_COLI_CASE(256)
+#undef SD_COLI_CASE
         }
         return cudaErrorInvalidValue;
     }
