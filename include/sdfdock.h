@@ -432,6 +432,22 @@ int sd_top_k_static(sd_ctx* ctx, const sd_cand* cand, int64_t n_cand, int k, sd_
  * unnormalised.  in, out: host, len x 2 double.  Needs no GPU. */
 int sd_host_line_fft(int len, int inverse, const double* in, double* out);
 
+/* Probe of an arithmetic rate of this GPU, for the rooflines of the kernels
+ * bound by arithmetic rather than memory (the SDF sums: FP32 FMA and the
+ * special-function unit; the FP64 re-score: FP64 FMA).  The paper has no
+ * counterpart.  Runs a probe kernel (eight independent dependency chains per
+ * thread, eight CTAs of 256 threads per SM) on `device` for a few to tens of
+ * milliseconds, synchronously on the legacy default stream, and stores the best
+ * of three timed launches in *ops_per_s: floating-point operations per second
+ * for the FMA kinds (two per FMA), instructions per second for the others.
+ * Allocates 4 bytes of device memory for the duration of the call.  SD_ERR_ARG
+ * for an unknown kind or device, SD_ERR_CUDA if a CUDA call fails. */
+#define SD_PEAK_FP32_FMA 0
+#define SD_PEAK_FP64_FMA 1
+#define SD_PEAK_SFU_EX2 2   /* ex2.approx.f32 (the exponential's special-function step) */
+#define SD_PEAK_SFU_RSQRT 3 /* rsqrt.approx.f32 */
+int sd_alu_peak(int device, int kind, double* ops_per_s);
+
 /* Library version string (static storage). */
 const char* sd_version(void);
 

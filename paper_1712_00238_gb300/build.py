@@ -21,7 +21,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libsdfdock.so")
 
 SOURCES = ["api.cu", "sdf.cu", "nufft_f32.cu", "nufft_f64.cu", "search.cu", "grad_f32.cu", "grad_f64.cu",
-           "topk_static.cu", "order.cu", "octree.cu"]
+           "topk_static.cu", "order.cu", "octree.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "-diag-suppress", "1444"]  # 1444: deprecated vector types in CUDA headers

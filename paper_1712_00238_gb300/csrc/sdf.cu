@@ -12,6 +12,10 @@
 // eta/|xi| - 1 <= eps (Eq. 17t).  In 2D every element is weighted by its planar
 // angle over 2 pi, i.e. the 3D summand times 2 eta.
 // Both passes stage boundary tiles in shared memory; one query point per thread.
+// A block of queries may split its boundary tiles across several CTAs (grid
+// y), each writing a partial (nearest distance and winding sum; rho); a
+// finishing kernel combines the partials in a fixed order, so the results do
+// not depend on how many CTAs shared the work's scheduling.
 #include <float.h>
 #include <math.h>
 
@@ -32,7 +36,7 @@ template <>
 __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
+__global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a, int tiles_per_split, T* part_d2, T* part_w) {
     __shared__ vec4<T> sq[SDF_TILE];
     __shared__ vec4<T> sn[SDF_TILE];  // normal with the area in .w
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,7 +47,9 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
     else { p.x = p.y = p.z = p.w = T(0); }
     T dmin = INFINITY;
     T wind = T(0);
-    for (int64_t t0 = 0; t0 < a.n_b; t0 += SDF_TILE) {
+    const int64_t t_lo = (int64_t)blockIdx.y * tiles_per_split * SDF_TILE;
+    const int64_t t_hi = min(a.n_b, t_lo + (int64_t)tiles_per_split * SDF_TILE);
+    for (int64_t t0 = t_lo; t0 < t_hi; t0 += SDF_TILE) {
         const int64_t j = t0 + threadIdx.x;
         if (j < a.n_b) {
             sq[threadIdx.x] = a.bnd[j];
@@ -68,10 +74,29 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_nearest(SdfArgs<T> a) {
         __syncthreads();
     }
     if (!live) return;
+    part_d2[(int64_t)blockIdx.y * a.m + i] = dmin;
+    part_w[(int64_t)blockIdx.y * a.m + i] = wind;
+}
+
+// Nearest distance (the smallest partial) and membership (the partial winding
+// sums added in split order) of each query.
+template <typename T, int D>
+__global__ void k_sdf_nearest_finish(SdfArgs<T> a, int splits, const T* part_d2, const T* part_w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    T dmin = INFINITY, wind = T(0);
+    for (int k = 0; k < splits; ++k) {
+        const T d = part_d2[(int64_t)k * a.m + i];
+        dmin = d < dmin ? d : dmin;
+        wind += part_w[(int64_t)k * a.m + i];
+    }
     const T S = (D == 3) ? T(4.0 * M_PI) : T(2.0 * M_PI);
     a.xi_abs[i] = sqrt(dmin);
     int8_t m = (wind > T(0.5) * S) ? int8_t(-1) : int8_t(1);
-    if (a.pmc_override) m = a.pmc_override[src] < 0 ? int8_t(-1) : int8_t(1);
+    if (a.pmc_override) {
+        const int64_t src = a.perm_q ? (int64_t)a.perm_q[i] : i;
+        m = a.pmc_override[src] < 0 ? int8_t(-1) : int8_t(1);
+    }
     a.pmc[i] = m;
 }
 
@@ -85,7 +110,7 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
 }
 
 template <typename T, int D, int PHI>
-__global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
+__global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a, int tiles_per_split, cplx<T>* part) {
     __shared__ vec4<T> sq[SDF_TILE];
     __shared__ vec4<T> sn[SDF_TILE];
     __shared__ float wred[SDF_TILE / 32][7];
@@ -139,7 +164,9 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
     const T inv_2s2 = recip(T(2) * a.sigma * a.sigma);
     const T xi2 = xi * xi;
     T sr = 0, cr = 0, si = 0, ci = 0;
-    for (int64_t t0 = 0, tile = 0; t0 < a.n_b; t0 += SDF_TILE, ++tile) {
+    const int64_t tile_lo = (int64_t)blockIdx.y * tiles_per_split;
+    const int64_t t_hi = min(a.n_b, (tile_lo + tiles_per_split) * SDF_TILE);
+    for (int64_t t0 = tile_lo * SDF_TILE, tile = tile_lo; t0 < t_hi; t0 += SDF_TILE, ++tile) {
         if (cull) {
             const float* tb = a.tile_box + tile * 6;
             const float g0 = fmaxf(0.f, fmaxf(tb[0] - box[3], box[0] - tb[3]));
@@ -184,10 +211,26 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a) {
         }
     }
     if (!live) return;
+    part[(int64_t)blockIdx.y * a.m + i] = mk(sr, si);
+}
+
+// rho of each query: the partial sums added in split order (compensated), then
+// the shape's sample c = rho v and position.
+template <typename T>
+__global__ void k_sdf_sum_finish(SdfArgs<T> a, int splits, const cplx<T>* part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    T sr = 0, cr = 0, si = 0, ci = 0;
+    for (int k = 0; k < splits; ++k) {
+        const cplx<T> v = part[(int64_t)k * a.m + i];
+        kahan_add(sr, cr, v.x);
+        kahan_add(si, ci, v.y);
+    }
+    const int64_t src = a.perm_q ? (int64_t)a.perm_q[i] : i;
     const T v = a.vol[src];
     a.c_out[i] = mk(sr * v, si * v);
     if (a.rho_out) a.rho_out[src] = mk(sr, si);
-    vec4<T> po = p;
+    vec4<T> po = a.qry[src];
     po.w = T(0);
     a.pos_out[i] = po;
 }
@@ -261,32 +304,76 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_skin(SdfArgs<T> a) {
     a.pos_out[i] = po;
 }
 
+// Boundary-tile splits per query block: enough CTAs for about four per SM.
+static int sdf_splits(int64_t query_blocks, int64_t tiles) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int64_t s = (4 * (int64_t)sms + query_blocks - 1) / query_blocks;
+    s = s < 1 ? 1 : (s > tiles ? tiles : s);
+    return (int)(s > 64 ? 64 : s);
+}
+
 template <typename T>
 cudaError_t launch_sdf(const SdfArgs<T>& a, int dim, cudaStream_t st) {
     if (a.m == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((a.m + SDF_TILE - 1) / SDF_TILE);
-    if (dim == 2) k_sdf_nearest<T, 2><<<nb, SDF_TILE, 0, st>>>(a);
-    else k_sdf_nearest<T, 3><<<nb, SDF_TILE, 0, st>>>(a);
+    if (a.phi == SD_PHI_SKIN) {
+        // membership and distance only (one split), then the pointwise layers
+        const int64_t tiles = (a.n_b + SDF_TILE - 1) / SDF_TILE;
+        T *d2 = nullptr, *w = nullptr;
+        cudaError_t e = pool_alloc((void**)&d2, (size_t)2 * a.m * sizeof(T), st);
+        if (e != cudaSuccess) return e;
+        w = d2 + a.m;
+        if (dim == 2) k_sdf_nearest<T, 2><<<dim3(nb, 1), SDF_TILE, 0, st>>>(a, (int)tiles, d2, w);
+        else k_sdf_nearest<T, 3><<<dim3(nb, 1), SDF_TILE, 0, st>>>(a, (int)tiles, d2, w);
+        if (dim == 2) k_sdf_nearest_finish<T, 2><<<nb, SDF_TILE, 0, st>>>(a, 1, d2, w);
+        else k_sdf_nearest_finish<T, 3><<<nb, SDF_TILE, 0, st>>>(a, 1, d2, w);
+        k_sdf_skin<T><<<nb, SDF_TILE, 0, st>>>(a);
+        note_launch(3);
+        pool_free(d2, st);
+        return cudaGetLastError();
+    }
+    if (a.phi != SD_PHI_SDF && a.phi != SD_PHI_PROXIMAL && a.phi != SD_PHI_RADIAL) return cudaErrorInvalidValue;
+    const int64_t tiles = (a.n_b + SDF_TILE - 1) / SDF_TILE;
+    const int splits = sdf_splits(nb, tiles < 1 ? 1 : tiles);
+    const int tps = (int)((tiles + splits - 1) / splits);
+    // partials: nearest distance and winding sum (2 reals), then rho (one complex), per split and query
+    char* scratch = nullptr;
+    const size_t real_bytes = (size_t)splits * a.m * sizeof(T);
+    cudaError_t e = pool_alloc((void**)&scratch, 2 * real_bytes + (size_t)splits * a.m * sizeof(cplx<T>), st);
+    if (e != cudaSuccess) return e;
+    T* d2 = reinterpret_cast<T*>(scratch);
+    T* w = reinterpret_cast<T*>(scratch + real_bytes);
+    cplx<T>* part = reinterpret_cast<cplx<T>*>(scratch + 2 * real_bytes);
+    const dim3 grid(nb, splits);
+    if (dim == 2) k_sdf_nearest<T, 2><<<grid, SDF_TILE, 0, st>>>(a, tps, d2, w);
+    else k_sdf_nearest<T, 3><<<grid, SDF_TILE, 0, st>>>(a, tps, d2, w);
+    if (dim == 2) k_sdf_nearest_finish<T, 2><<<nb, SDF_TILE, 0, st>>>(a, splits, d2, w);
+    else k_sdf_nearest_finish<T, 3><<<nb, SDF_TILE, 0, st>>>(a, splits, d2, w);
+#define SD_SUM(DD, PP) k_sdf_sum<T, DD, PP><<<grid, SDF_TILE, 0, st>>>(a, tps, part)
     switch (a.phi) {
         case SD_PHI_SDF:
-            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_SDF><<<nb, SDF_TILE, 0, st>>>(a);
-            else k_sdf_sum<T, 3, SD_PHI_SDF><<<nb, SDF_TILE, 0, st>>>(a);
+            if (dim == 2) SD_SUM(2, SD_PHI_SDF);
+            else SD_SUM(3, SD_PHI_SDF);
             break;
         case SD_PHI_PROXIMAL:
-            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_PROXIMAL><<<nb, SDF_TILE, 0, st>>>(a);
-            else k_sdf_sum<T, 3, SD_PHI_PROXIMAL><<<nb, SDF_TILE, 0, st>>>(a);
-            break;
-        case SD_PHI_RADIAL:
-            if (dim == 2) k_sdf_sum<T, 2, SD_PHI_RADIAL><<<nb, SDF_TILE, 0, st>>>(a);
-            else k_sdf_sum<T, 3, SD_PHI_RADIAL><<<nb, SDF_TILE, 0, st>>>(a);
-            break;
-        case SD_PHI_SKIN:
-            k_sdf_skin<T><<<nb, SDF_TILE, 0, st>>>(a);
+            if (dim == 2) SD_SUM(2, SD_PHI_PROXIMAL);
+            else SD_SUM(3, SD_PHI_PROXIMAL);
             break;
         default:
-            return cudaErrorInvalidValue;
+            if (dim == 2) SD_SUM(2, SD_PHI_RADIAL);
+            else SD_SUM(3, SD_PHI_RADIAL);
+            break;
     }
-    note_launch(2);
+#undef SD_SUM
+    k_sdf_sum_finish<T><<<nb, SDF_TILE, 0, st>>>(a, splits, part);
+    note_launch(4);
+    pool_free(scratch, st);
     return cudaGetLastError();
 }
 

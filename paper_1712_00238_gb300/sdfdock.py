@@ -131,6 +131,7 @@ _SIGS = {
     "sd_launch_count": (ct.c_int64, []),
     "sd_top_k_static": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "sd_pass_times": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
+    "sd_alu_peak": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(ct.c_double)]),
 }
 
 PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph", "spread_x"]
@@ -525,6 +526,20 @@ class Octree:
             self.close()
         except Exception:
             pass
+
+
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "sfu_ex2": 2, "sfu_rsqrt": 3}
+
+
+def alu_peak(kind: str, device: int = 0) -> float:
+    """Measured rate of one arithmetic class on a device (sd_alu_peak): FLOP/s for
+    the FMA kinds, instructions/s for the special-function kinds."""
+    lib = load()
+    v = ct.c_double()
+    rc = lib.sd_alu_peak(int(device), PEAK_KINDS[kind], ct.byref(v))
+    if rc != 0:
+        raise SdError(rc, f"sd_alu_peak({kind}) failed")
+    return v.value
 
 
 def launch_count() -> int:

@@ -71,15 +71,20 @@ def _under(leaf_d, leaf_k, cells):
     return m
 
 
-@pytest.mark.parametrize("name,d_min,d_max,tau", [("tiny_2d", 2, 7, 2e-3), ("tiny_3d", 1, 4, 2e-2)])
-def test_tree_and_samples_match_oracle_fp64(name, d_min, d_max, tau):
+@pytest.mark.parametrize("name,d_min,d_max,tau,band", [("tiny_2d", 2, 7, 2e-3, np.inf), ("tiny_3d", 1, 4, 2e-2, np.inf),
+                                                        ("tiny_2d", 2, 7, 2e-3, 0.3), ("tiny_3d", 1, 4, 2e-2, 0.5)])
+def test_tree_and_samples_match_oracle_fp64(name, d_min, d_max, tau, band):
+    # band < inf keeps only the leaves within `band` of the nearest boundary
+    # sample and drops whole cells beyond band + half their diagonal unevaluated
     w, s, rho_fn, xi_fn, lo, size = _setup(name, "moving")
     b = s.boundary
-    c, v, k, d, asked = ooct.octree_leaves(rho_fn, xi_fn, lo, size, w.dim, d_min, d_max, tau, b.spacing)
+    c, v, k, d, asked = ooct.octree_leaves(rho_fn, xi_fn, lo, size, w.dim, d_min, d_max, tau, b.spacing, band)
     assert not _fragile(asked, rho_fn, lo, size, w.dim, d_min, tau, 1e-7)
+    if np.isfinite(band):
+        assert np.all(xi_fn(c) <= band)
     ctx = make_ctx(w, "f64")
     shape, (cen, vol, crd, rho) = ctx.sdf_build_octree(b.pos, b.normal, b.area, lo, size, d_min, d_max, tau,
-                                                       b.spacing, return_leaves=True)
+                                                       b.spacing, return_leaves=True, band=band)
     assert np.array_equal(crd[:, :w.dim], k) and np.array_equal(crd[:, 3], d)
     assert np.allclose(cen[:, :w.dim], c, rtol=0, atol=1e-12 * size) and np.array_equal(vol, v)
     got = rho.cpu().numpy()

@@ -695,3 +695,16 @@ def test_sdf_docking_pair_sampled_points():
                            LAM_DEFAULT[2], LAM_DEFAULT[3])
         assert rel_err(got[sel, 0] + 1j * got[sel, 1], ref) < 1e-4
     ctx.close()
+
+
+def test_alu_peak_probe_rates_are_plausible():
+    # the probe behind the ALU rooflines: rates are positive and ordered as the
+    # hardware is built (FP32 FMA far above FP64 FMA; ex2 at least as fast as rsqrt)
+    rates = {k: sd.alu_peak(k) for k in sd.PEAK_KINDS}
+    assert all(v > 0 for v in rates.values())
+    assert rates["fp32_fma"] > 10 * rates["fp64_fma"]
+    assert rates["sfu_ex2"] >= 0.5 * rates["sfu_rsqrt"]
+    lib = sd.load()
+    import ctypes as ct
+    v = ct.c_double()
+    assert lib.sd_alu_peak(0, 9, ct.byref(v)) == sd.SD_ERR_ARG
