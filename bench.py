@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--spread-fused", type=int, default=0,
                     help="with --autotune 0: 1 spreads straight into rows held in shared memory and runs the "
                          "forward x transform there (3D FP32)")
+    ap.add_argument("--spread-box", type=int, default=0,
+                    help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library times candidate plans (batch, spreading) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
@@ -255,6 +257,7 @@ def run_ours(args):
     ctx.set_option("graph", 0 if args.plain else args.graph)
     ctx.set_option("spread_direct", args.spread_direct)
     ctx.set_option("spread_fused", args.spread_fused)
+    ctx.set_option("spread_box", args.spread_box)
     ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
     plan_used = {}
@@ -407,6 +410,8 @@ def run_ours(args):
                    "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
                    "spread": ("fused with the forward x transform (8x6 row bins, shared fixed-point tile)"
                               if plan_used.get("spread_bins") == 1 else
+                              "shared boxes of 128 Morton-consecutive samples, 16-byte pair atomics"
+                              if plan_used.get("spread_bins") == 2 else
                               f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
                               if plan_used.get("spread_bins") else "global vector atomics"),
                    "l2": "flushed between timed steps (512 MB write)",
@@ -733,7 +738,7 @@ def run_pairs(args):
     pair_ms = [x["ms"] for st in per_pair for x in st]
     plans = {}
     for x in per_pair[-1]:
-        sp = {0: "direct", 1: "spread_x"}.get(x["spread_bins"], f"bins{x['spread_bins']}")
+        sp = {0: "direct", 1: "spread_x", 2: "box"}.get(x["spread_bins"], f"bins{x['spread_bins']}")
         key = f"n={x['n']} B={x['batch']} {sp}"
         plans[key] = plans.get(key, 0) + 1
     grids = {}

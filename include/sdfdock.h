@@ -138,7 +138,10 @@ const char* sd_last_error(const sd_ctx* ctx);
  * shared memory first), "pruned" (1, the default: the forward FFT passes of the
  * search read the spread sub-box unshifted and compute only the kept modes, with
  * the shift applied as a phase in the product table; 0: the shifted sub-box and
- * every mode; results are the same up to FP rounding), "spread_fused" (1: in
+ * every mode; results are the same up to FP rounding), "spread_box" (1: each
+ * CTA spreads a block of Morton-consecutive samples into a shared box of the
+ * sub-box and adds the box's nonzero cells with 16-byte atomics; FP32, w 4-7;
+ * default 0), "spread_fused" (1: in
  * pruned 3D FP32 searches with w = 6, spread each rotation's samples straight
  * into whole rows held in shared memory and run the forward x transform there,
  * with no sub-box in device memory; default 0), "sdf_cull" (1, the
@@ -146,7 +149,8 @@ const char* sd_last_error(const sd_ctx* ctx);
  * tiles that lie beyond the truncation radius of every query of a block; 0: sum
  * over every tile; results are the same), "autotune" (1: before a scoring job
  * runs, time its candidate plans -- rotations per batch from a quarter to
- * twice the automatic choice, direct spreading, bins of 8, 12 or 16 cells, or
+ * twice the automatic choice, direct spreading, shared boxes of sample blocks,
+ * bins of 8, 12 or 16 cells, or
  * (pruned 3D FP32 searches with w = 6) spreading fused with the forward x
  * transform -- on its first
  * rotations and keep the fastest; the choice is cached per precision, grid,
@@ -278,7 +282,8 @@ typedef struct sd_pair_stat {
     double ms;            /* device time of the job within the call */
     int32_t batch;        /* rotations per batch of its plan */
     int32_t spread_bins;  /* bin side of its plan's binned spreading, 0: direct,
-                             1: spreading fused with the forward x transform */
+                             1: spreading fused with the forward x transform,
+                             2: shared boxes of sample blocks */
     int32_t n;            /* oversampled grid size per axis */
     int32_t s;            /* sub-box side of its moving shape */
 } sd_pair_stat;
@@ -304,7 +309,8 @@ int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair
 
 /* The plan a search of n_r rotations of `moving` on grid g would run with now:
  * rotations per batch and the bin side of binned spreading (0: direct; 1:
- * spreading fused with the forward x transform).  With the
+ * spreading fused with the forward x transform; 2: shared boxes of sample
+ * blocks).  With the
  * "autotune" option it is the cached choice for this geometry if there is one
  * (the first search of a geometry makes it), else the default.  No device work. */
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
@@ -320,7 +326,7 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
 /* Add the plans of a JSON text written by sd_tune_export to this context's
  * cache (entries with a key already present are replaced), so searches of those
  * geometries skip the timing trials.  A text that is not such a table, or an
- * entry with batch outside [1, 64] or spread_bins not 0, 1, 8, 12 or 16, is SD_ERR_ARG and
+ * entry with batch outside [1, 64] or spread_bins not 0, 1, 2, 8, 12 or 16, is SD_ERR_ARG and
  * leaves the cache unchanged. */
 int sd_tune_import(sd_ctx* ctx, const char* json);
 

@@ -56,7 +56,8 @@ struct GraphEntry {
 struct Plan {      // launch plan of one scoring job
     int B = 1;     // rotations per launch sequence
     int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct,
-                   // 1: spreading fused with the forward x transform (SPREAD_X)
+                   // 1: spreading fused with the forward x transform (SPREAD_X),
+                   // 2: shared boxes of sample blocks (SPREAD_BOX)
 };
 
 struct sd_ctx {
@@ -75,6 +76,7 @@ struct sd_ctx {
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
+    int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
     int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
     int opt_autotune = 0;       // 1: time candidate plans per job geometry
     std::map<std::string, Plan> tuned;
@@ -551,6 +553,8 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, int tb, B
 constexpr int DEFAULT_BIN = 16;
 // Plan.bins value of spreading fused with the forward x transform.
 constexpr int SPREAD_X = 1;
+// Plan.bins value of spreading by blocks of Morton-consecutive samples.
+constexpr int SPREAD_BOX = 2;
 
 // Bin workspace of the fused spreading (bins over (y, z)).
 static int spread_x_bins(int s, int* nby, int* nbz) {
@@ -833,6 +837,7 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
         }
         S->W = (const cplx<T>*)ws;
     }
+    if (ctx->opt_spread_box && bins_supported(ctx)) S->plan.bins = SPREAD_BOX;
     if (ctx->opt_spread_fused && spread_x_ok(ctx, *S)) S->plan.bins = SPREAD_X;
     return SD_OK;
 }
@@ -846,7 +851,8 @@ static void search_need(const Search<T>& S, size_t need[8]) {
     need[2] = std::max(need[2], B * S.rows_last * sizeof(double));  // at most one partial per row
     need[3] = std::max(need[3], B * S.rows_last * sizeof(int));
     if (S.plan.bins == SPREAD_X) need[6] = std::max(need[6], bins_bytes_x(S.G.s, S.moving->m, S.plan.B));
-    else if (S.plan.bins) need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
+    else if (S.plan.bins > SPREAD_BOX)
+        need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
 }
 
 static int ws_reserve(sd_ctx* ctx, const size_t need[8]) {
@@ -864,7 +870,8 @@ static void search_bind(sd_ctx* ctx, Search<T>* S) {
     S->ps = (double*)ctx->ws[2].p;
     S->pi = (int*)ctx->ws[3].p;
     if (S->plan.bins == SPREAD_X) bins_layout_x(ctx->ws[6].p, S->G.s, S->moving->m, S->plan.B, &S->bn, &S->nbz);
-    else if (S->plan.bins) bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, S->plan.bins, &S->bn);
+    else if (S->plan.bins > SPREAD_BOX)
+        bins_layout(ctx->ws[6].p, S->G.s, S->G.dim, S->moving->m, S->plan.B, S->plan.bins, &S->bn);
 }
 
 // Launch sequence of rotations [r_lo, r_hi), plan.B rotations at a time.
@@ -906,7 +913,8 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         } else {
             {
                 PassTimer pt(ctx, SD_PASS_SPREAD, s, timed);
-                if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
+                if (S.plan.bins == SPREAD_BOX) CK(ctx, launch_spread_box<T>(sa, G.dim, b, s));
+                else if (S.plan.bins) CK(ctx, launch_spread_bins<T>(sa, S.bn, G.dim, b, s));
                 else CK(ctx, launch_spread<T>(sa, G.dim, b, s));
             }
             PassTimer pt(ctx, SD_PASS_FWD_X, s, timed);
@@ -996,7 +1004,7 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     std::vector<Plan> cand;
     for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
         if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
-        for (int bins : {0, SPREAD_X, 8, 12, 16}) {
+        for (int bins : {0, SPREAD_BOX, SPREAD_X, 8, 12, 16}) {
             if (bins == SPREAD_X ? !spread_x_ok(ctx, *S) : (bins && !bins_supported(ctx))) continue;
             bool dup = false;
             for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
@@ -1306,6 +1314,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
     else if (!strcmp(key, "spread_fused")) ctx->opt_spread_fused = (int)value;
+    else if (!strcmp(key, "spread_box")) ctx->opt_spread_box = (int)value;
     else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
     else if (!strcmp(key, "autotune")) ctx->opt_autotune = (int)value;
     else return fail(ctx, SD_ERR_ARG, "unknown option '%s'", key);
@@ -1566,7 +1575,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         std::string key(p, (size_t)(q - p));
         int B = 0, bins = -1;
         if (sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d}", &B, &bins) != 2 || B < 1 || B > 64 ||
-            (bins != 0 && bins != SPREAD_X && bins != 8 && bins != 12 && bins != 16))
+            (bins != 0 && bins != SPREAD_X && bins != SPREAD_BOX && bins != 8 && bins != 12 && bins != 16))
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
         got[key] = Plan{B, bins};
         p = q;
@@ -1589,6 +1598,7 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
         S.plan.B = choose_batch<T>(ctx, S.G, n_r);
         S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
         S.pruned = ctx->opt_pruned && pruned_len_ok(S.G.n) && S.G.s <= S.G.N;
+        if (ctx->opt_spread_box && bins_supported(ctx)) S.plan.bins = SPREAD_BOX;
         if (ctx->opt_spread_fused && spread_x_ok(ctx, S)) S.plan.bins = SPREAD_X;
         if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) {
             auto it = ctx->tuned.find(plan_key(ctx, S));

@@ -33,6 +33,39 @@ template <bool INV, typename C> __host__ __device__ __forceinline__ C mul_mi(C a
     return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+// a + (-i) d and a - (-i) d (forward sign; +i for the inverse) without forming the
+// rotated operand
+template <bool INV, typename C> __host__ __device__ __forceinline__ C add_mi(C a, C d) {
+    return INV ? mk(a.x - d.y, a.y + d.x) : mk(a.x + d.y, a.y - d.x);
+}
+template <bool INV, typename C> __host__ __device__ __forceinline__ C sub_mi(C a, C d) {
+    return INV ? mk(a.x + d.y, a.y - d.x) : mk(a.x - d.y, a.y + d.x);
+}
+
+// Single-precision pairs: on sm_100+ one paired instruction adds, subtracts or
+// scales both components (IEEE round-to-nearest per component, the same values
+// as two scalar operations; a - b is the exact product b * -1 plus a, rounded once).
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fmul2_rn(a, make_float2(s, s));
+#else
+    return make_float2(a.x * s, a.y * s);
+#endif
+}
 
 // Complex accumulation into global memory (atomic).
 __device__ __forceinline__ void atomic_cadd(float2* p, float2 v) {

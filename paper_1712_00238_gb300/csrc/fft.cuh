@@ -52,11 +52,11 @@ __host__ __device__ constexpr int line_pitch(int len) { return ((len + (len >> 4
 
 template <bool INV, typename C>
 __host__ __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
+    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(t0, t2);
     a2 = csub(t0, t2);
-    a1 = cadd(t1, t3);
-    a3 = csub(t1, t3);
+    a1 = add_mi<INV>(t1, d);
+    a3 = sub_mi<INV>(t1, d);
 }
 
 // exp(-+2 pi i m / 16) as constants (cos and sin of multiples of pi/8).

@@ -42,11 +42,10 @@ __device__ __forceinline__ void dft_lowhalf(C* v) {
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) {
             const C a0 = v[n2], a1 = v[4 + n2];
-            const C m = mul_mi<INV>(a1);
             b[n2][0] = cadd(a0, a1);
-            b[n2][1] = cadd(a0, m);
+            b[n2][1] = add_mi<INV>(a0, a1);
             b[n2][2] = csub(a0, a1);
-            b[n2][3] = csub(a0, m);
+            b[n2][3] = sub_mi<INV>(a0, a1);
         }
 #pragma unroll
         for (int n2 = 1; n2 < 4; ++n2)
@@ -61,9 +60,8 @@ __device__ __forceinline__ void dft_lowhalf(C* v) {
     } else if constexpr (R == 8) {
         // even / odd inputs each (a0, a1, 0, 0)
         const T r = T(0.70710678118654752440);
-        const C me = mul_mi<INV>(v[2]), mo = mul_mi<INV>(v[3]);
-        C e0 = cadd(v[0], v[2]), e1 = cadd(v[0], me), e2 = csub(v[0], v[2]), e3 = csub(v[0], me);
-        C o0 = cadd(v[1], v[3]), o1 = cadd(v[1], mo), o2 = csub(v[1], v[3]), o3 = csub(v[1], mo);
+        C e0 = cadd(v[0], v[2]), e1 = add_mi<INV>(v[0], v[2]), e2 = csub(v[0], v[2]), e3 = sub_mi<INV>(v[0], v[2]);
+        C o0 = cadd(v[1], v[3]), o1 = add_mi<INV>(v[1], v[3]), o2 = csub(v[1], v[3]), o3 = sub_mi<INV>(v[1], v[3]);
         o1 = cmul(o1, INV ? mk(r, r) : mk(r, -r));
         o2 = mul_mi<INV>(o2);
         o3 = cmul(o3, INV ? mk(-r, r) : mk(-r, -r));

@@ -92,6 +92,11 @@ struct BinArgs {
 template <typename T>
 cudaError_t launch_spread_bins(const SpreadArgs<T>& a, const BinArgs& bn, int dim, int batch, cudaStream_t st);
 
+// Spread by blocks of Morton-consecutive samples: each CTA accumulates its
+// samples' taps in a shared box and adds the box to the sub-box (which must be
+// cleared first).  FP32, w = 4..7; other precisions spread directly.
+template <typename T> cudaError_t launch_spread_box(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st);
+
 // Spreading fused with the forward x transform of the pruned 3D search (FP32,
 // w = 6, 2 s <= n): the samples are binned by the (y, z) of their tap box in
 // bins of SPREADX_TY x SPREADX_TZ cells (bn.nb = bins along y, nbz along z,

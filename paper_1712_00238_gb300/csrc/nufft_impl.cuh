@@ -533,6 +533,195 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
 }
 
 // ---------------------------------------------------------------------------
+// spreading by sample blocks (no sort)
+// ---------------------------------------------------------------------------
+//
+// A shape's samples are stored in Morton order, so a CTA's BOX_SPC consecutive
+// samples form a compact patch that, rotated, still fits a small box of the
+// sub-box.  The CTA finds that box (block min / max of the tap-box origins),
+// accumulates its samples' taps there in a fixed-point shared tile (warps take
+// the samples round-robin, lanes on consecutive taps), then adds the box's
+// nonzero cells to the sub-box with 16-byte pair atomics: the global atomics
+// fall from about W^d / 2 per sample to about one per two cells of the box.  A
+// box larger than the tile, or one that wraps around a periodic sub-box, is
+// spread with global atomics per tap instead.
+
+constexpr int BOX_SPC = 128;      // samples per CTA
+constexpr int BOX_MAXC = 8192;    // cells of the shared tile (2 x 32 KB)
+
+template <int D, int W>
+__global__ void __launch_bounds__(BOX_SPC) k_spread_box(SpreadArgs<float> a) {
+    constexpr int REC = D * W + 4;  // weights | c.x c.y | packed origin | pad
+    constexpr int TAPS = (D == 3) ? W * W * W : W * W;
+    constexpr int ROUNDS = (TAPS + 31) / 32;
+    constexpr int NWARP = BOX_SPC / 32;
+    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+    constexpr int MAGIC_BITS = 0x4B400000;
+    extern __shared__ __align__(16) int bsm[];
+    int* tre = bsm;
+    int* tim = bsm + BOX_MAXC;
+    __shared__ float stage[BOX_SPC * REC];
+    __shared__ float Rm[9];
+    __shared__ int wlo[NWARP][3], whi[NWARP][3];
+    __shared__ float wmx[NWARP], wsm[NWARP];
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) load_rotation(a, b, Rm);
+    __syncthreads();
+    const int64_t j0 = (int64_t)blockIdx.x * BOX_SPC;
+    const int nj = (int)min((int64_t)BOX_SPC, a.m - j0);
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    float mx = 0.f, sm = 0.f;
+    if (tid < nj) {
+        int org[D];
+        float wt[D][W];
+        float2 c;
+        sample_taps<float, D, W>(a, Rm, j0 + tid, org, wt, c);
+        float* r = stage + tid * REC;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) r[d * W + k] = wt[d][k];
+            lo[d] = hi[d] = org[d];
+        }
+        r[D * W] = c.x;
+        r[D * W + 1] = c.y;
+        r[D * W + 2] = __int_as_float(org[0] | (org[1] << 10) | ((D == 3 ? org[2] : 0) << 20));
+        mx = fmaxf(fabsf(c.x), fabsf(c.y));
+        sm = mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            lo[d] = min(lo[d], __shfl_down_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_down_sync(0xffffffffu, hi[d], o));
+        }
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        sm += __shfl_down_sync(0xffffffffu, sm, o);
+    }
+    if (lane == 0) {
+        for (int d = 0; d < D; ++d) {
+            wlo[warp][d] = lo[d];
+            whi[warp][d] = hi[d];
+        }
+        wmx[warp] = mx;
+        wsm[warp] = sm;
+    }
+    __syncthreads();
+    int blo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+    mx = 0.f;
+    sm = 0.f;
+    for (int w = 0; w < NWARP; ++w) {
+        mx = fmaxf(mx, wmx[w]);
+        sm += wsm[w];
+    }
+    bool fits = true;
+    int cells = 1;
+    for (int d = 0; d < D; ++d) {
+        int l = INT_MAX, h = INT_MIN;
+        for (int w = 0; w < NWARP; ++w) {
+            l = min(l, wlo[w][d]);
+            h = max(h, whi[w][d]);
+        }
+        blo[d] = l;
+        ext[d] = h - l + W;
+        fits &= (l + ext[d] <= a.s);  // no wrap around a periodic sub-box
+        cells *= ext[d];
+    }
+    fits &= cells <= BOX_MAXC;
+    float2* out = a.out + (int64_t)b * a.out_rot_stride;
+    const int s = a.s;
+    if (!fits) {
+        // global atomics per tap (lanes on consecutive taps of one sample)
+        for (int jj = warp; jj < nj; jj += NWARP) {
+            const float* r = stage + jj * REC;
+            const int packed = __float_as_int(r[D * W + 2]);
+            const float cx = r[D * W], cy = r[D * W + 1];
+            for (int q = 0; q < ROUNDS; ++q) {
+                const int tap = q * 32 + lane;
+                if (tap < TAPS) {
+                    const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
+                    float w = r[kx] * r[W + ky];
+                    int64_t o = (int64_t)wrap_index(((packed >> 10) & 1023) + ky, s) * s +
+                                wrap_index((packed & 1023) + kx, s);
+                    if (D == 3) {
+                        w *= r[2 * W + kz];
+                        o += (int64_t)wrap_index(((packed >> 20) & 1023) + kz, s) * s * s;
+                    }
+                    atomic_cadd(out + o, make_float2(cx * w, cy * w));
+                }
+            }
+        }
+        return;
+    }
+    for (int i = tid; i < cells; i += BOX_SPC) {
+        tre[i] = 0;
+        tim[i] = 0;
+    }
+    // taps below 2^21, a cell's sum below 2^30 (the weights are <= 1)
+    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
+    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
+    const int se = sm > 0.f ? min(max(127 + min(21 - emx, 30 - esm), 1), 254) : 127;
+    const float scale = __int_as_float(se << 23);
+    const float inv_scale = 1.f / scale;
+    const int sy = ext[0], sz = ext[0] * ext[1];
+    int kx_of[ROUNDS], off_of[ROUNDS];
+#pragma unroll
+    for (int q = 0; q < ROUNDS; ++q) {
+        const int tap = min(q * 32 + lane, TAPS - 1);
+        const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
+        kx_of[q] = tap;  // the tap itself: weights are read per axis below
+        off_of[q] = kx + ky * sy + kz * sz;
+    }
+    __syncthreads();
+    for (int jj = warp; jj < nj; jj += NWARP) {
+        const float* r = stage + jj * REC;
+        const int packed = __float_as_int(r[D * W + 2]);
+        int base = ((packed & 1023) - blo[0]) + (((packed >> 10) & 1023) - blo[1]) * sy;
+        if (D == 3) base += (((packed >> 20) & 1023) - blo[2]) * sz;
+        const float cx = r[D * W] * scale, cy = r[D * W + 1] * scale;
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q) {
+            if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
+                const int tap = kx_of[q];
+                const int kx = tap % W, ky = (tap / W) % W;
+                float w = r[kx] * r[W + ky];
+                if (D == 3) w *= r[2 * W + tap / (W * W)];
+                const int cell = base + off_of[q];
+                atomicAdd(tre + cell, __float_as_int(fmaf(cx, w, MAGIC)) - MAGIC_BITS);
+                atomicAdd(tim + cell, __float_as_int(fmaf(cy, w, MAGIC)) - MAGIC_BITS);
+            }
+        }
+    }
+    __syncthreads();
+    // flush: pairs of x-adjacent cells starting at even global x
+    const int x0 = blo[0] & ~1;
+    const int npair = (blo[0] + ext[0] - x0 + 1) / 2;
+    const int rows = ext[1] * (D == 3 ? ext[2] : 1);
+    for (int i = tid; i < rows * npair; i += BOX_SPC) {
+        const int row = i / npair, k = i - row * npair;
+        const int gx = x0 + 2 * k;
+        const int lx = gx - blo[0];
+        const int li = row * sy + lx;
+        const bool in0 = lx >= 0, in1 = lx + 1 < ext[0];
+        const int r0 = in0 ? tre[li] : 0, i0 = in0 ? tim[li] : 0;
+        const int r1 = in1 ? tre[li + 1] : 0, i1 = in1 ? tim[li + 1] : 0;
+        if ((r0 | i0 | r1 | i1) == 0) continue;
+        const int gy = blo[1] + row % ext[1];
+        int64_t o = (int64_t)gy * s + gx;
+        if (D == 3) o += (int64_t)(blo[2] + row / ext[1]) * s * s;
+        const float2 v0 = make_float2((float)r0 * inv_scale, (float)i0 * inv_scale);
+        const float2 v1 = make_float2((float)r1 * inv_scale, (float)i1 * inv_scale);
+        if (gx + 1 < s) {
+            add_pair(out + o, v0, v1);
+        } else {
+            atomic_cadd(out + o, v0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // spreading fused with the forward x transform (3D, pruned search)
 // ---------------------------------------------------------------------------
 //
@@ -1517,6 +1706,29 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
     }
 }
 
+template <typename T>
+cudaError_t launch_spread_box_t(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st) {
+    if (a.m == 0 || batch == 0) return cudaSuccess;
+    if constexpr (sizeof(T) != 4) {
+        return launch_spread_t<T>(a, dim, batch, st);
+    } else {
+        const dim3 grid((unsigned)((a.m + BOX_SPC - 1) / BOX_SPC), batch);
+        const size_t smem = (size_t)2 * BOX_MAXC * sizeof(int);
+#define SD_BOX_CASE(WW)                                                   \
+    case WW: {                                                            \
+        auto kern = dim == 2 ? k_spread_box<2, WW> : k_spread_box<3, WW>; \
+        cudaError_t e = set_smem(kern, smem);                             \
+        if (e != cudaSuccess) return e;                                   \
+        kern<<<grid, BOX_SPC, smem, st>>>(a);                             \
+        note_launch();                                                    \
+        return cudaGetLastError();                                        \
+    }
+        switch (a.w) { SD_BOX_CASE(4) SD_BOX_CASE(5) SD_BOX_CASE(6) SD_BOX_CASE(7) }
+#undef SD_BOX_CASE
+        return cudaErrorInvalidValue;
+    }
+}
+
 // Spreading fused with the forward x transform: bins over (y, z), then one CTA
 // per bin writes the kept x modes of its rows (out: batch x s^2 x N).
 template <typename T>
@@ -1684,6 +1896,9 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn,
     template <> cudaError_t launch_spread_x<T>(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, cplx<T>* out, \
                                                int64_t ors, const cplx<T>* tw, int batch, cudaStream_t st) {   \
         return launch_spread_x_t<T>(a, bn, nbz, out, ors, tw, batch, st);                               \
+    }                                                                                                   \
+    template <> cudaError_t launch_spread_box<T>(const SpreadArgs<T>& a, int dim, int batch, cudaStream_t st) { \
+        return launch_spread_box_t<T>(a, dim, batch, st);                                               \
     }                                                                                                   \
     template <> cudaError_t launch_twiddles<T>(cplx<T>* tw, int len, cudaStream_t st) {                 \
         return launch_twiddles_t<T>(tw, len, st);                                                       \

@@ -88,7 +88,7 @@ def test_score_pairs_equals_per_pair_search_and_replays():
             if stats is not None:
                 x = stats[j]
                 assert np.isfinite(x["ms"]) and x["ms"] > 0
-                assert 1 <= x["batch"] <= 64 and x["spread_bins"] in (0, 1, 8, 12, 16)
+                assert 1 <= x["batch"] <= 64 and x["spread_bins"] in (0, 1, 2, 8, 12, 16)
                 assert x["n"] == 2 * g.N and 0 < x["s"] <= x["n"] and x["s"] % 2 == 0
     ctx.close()
 
@@ -122,7 +122,7 @@ def test_tuned_plans_export_and_import():
     text = ctx.tune_export()
     table = json.loads(text)
     assert table["sdfdock_plans"] == 1 and len(table["plans"]) == 1
-    assert table["plans"][0]["batch"] >= 1 and table["plans"][0]["spread_bins"] in (0, 1, 8, 12, 16)
+    assert table["plans"][0]["batch"] >= 1 and table["plans"][0]["spread_bins"] in (0, 1, 2, 8, 12, 16)
 
     ctx2 = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
     fx2, mv2, _, _, _ = _jobs(ctx2)[2]

@@ -174,6 +174,35 @@ def test_binned_spreading_matches_oracle(name, N, swap):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,N,swap", [("tiny_2d", 48, False), ("tiny_3d", 16, False), ("tiny_3d", 48, False),
+                                         ("tiny_3d", 8, True)])
+def test_box_spreading_matches_oracle(name, N, swap):
+    # each CTA spreads 128 Morton-consecutive samples into a shared box; with the
+    # block as the moving shape on the 8^3 grid the sub-box is the whole periodic
+    # grid and boxes that wrap take the global-atomic path
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    if swap:
+        p1, c1, p2, c2 = p2, c2, p1, c1
+    ctx = make_ctx(w, "f32")
+    ctx.set_option("spread_box", 1)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    assert ctx.search_plan(mv, g, w.n_rot)["spread_bins"] == 2
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], ref[r]) < TOL["f32"], r
+    s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g)))
+    for r in range(w.n_rot):
+        assert abs(s[r] - maps[r].real.max()) <= 1e-6 * np.abs(maps[r].real).max()
+        if top1_margin_ok(ref[r].real):
+            assert idx[r] == int(np.argmax(ref[r].real))
+    ctx.close()
+
+
 def _sub_box(radius, N, L, w):
     # side of the moving shape's sub-box on the oversampled grid n = 2N
     n = 2 * N
