@@ -73,7 +73,7 @@ def parse_args():
                     help="1: the library times candidate plans (batch, spreading) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--workload", choices=["peg_in_bore_3d", "peg_in_hole_2d", "docking_2000_500", "refine_256",
-                                           "uneven_batch", "multistart_2d"],
+                                           "uneven_batch", "multistart_2d", "sdf_large"],
                     default="docking_2000_500")
     ap.add_argument("--pairs", type=int, default=0, help="uneven_batch: use only the first P pairs")
     ap.add_argument("--refine-method", choices=["autograd", "ascent", "cg", "dynamics"], default="autograd",
@@ -837,6 +837,55 @@ def run_multistart(args):
     ctx.close()
 
 
+def run_sdf_large(args):
+    """The SDF build of one shape at the top of the uneven batch's size range
+    (5,000 spheres: ~2e5 query points, ~3e5 boundary samples), timed at each
+    level of the eps-neighbour restriction of the sums (sdf_cull 0, 1, 2)."""
+    import torch
+
+    from paper_1712_00238_gb300 import sdfdock as sd
+    from synth import configs
+
+    dev = torch.device("cuda", 0)
+    s = configs.large_sphere_shape()
+    w = configs.docking_2000_500()
+    ctx = sd.Context(3, "f32", 0, lambda1=w.lam1, lambda2=w.lam2, sigma_t=w.sigma_t, eps=w.eps,
+                     sigma_g=w.sigma_g, w=w.w)
+    b, q = s.boundary, s.query
+    inp = [ctx._dev(b.pos, cols=4), ctx._dev(b.normal, cols=4), ctx._dev(b.area), ctx._dev(q.pos, cols=4),
+           ctx._dev(q.vol)]
+    out = {}
+    for level in (2, 1, 0):
+        ctx.set_option("sdf_cull", level)
+        times = []
+        for k in range(max(args.warmup, 1) + args.steps):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            shape = ctx.sdf_build(*inp)
+            e1.record()
+            e1.synchronize()
+            if k >= max(args.warmup, 1):
+                times.append(e0.elapsed_time(e1))
+            ctx.shapes.remove(shape)
+            shape.free()
+        out[level] = statistics.mean(times)
+    ms = out[2]
+    result = {
+        "metric": "SDF samples built/s", "value": q.m / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"sdf_large: one sphere-union shape of 5,000 spheres, {q.m} query points, "
+                               f"{len(b.pos)} boundary samples (nearest distance + winding number over all "
+                               f"pairs, then the truncated sums)"},
+        "ms_by_cull_level": {"0_all_tiles": round(out[0], 3), "1_tiles": round(out[1], 3),
+                             "2_tiles_and_warp_subtiles": round(out[2], 3)},
+        "roofline": None,
+    }
+    print(json.dumps(result), flush=True)
+    ctx.close()
+
+
 def refine_cpu_baseline(w, q0, t0, n1=4000, n2=1000):
     """The oracle's band-limited score + gradient on seeded sample subsets, scaled to full size."""
     from oracle import score as oscore
@@ -865,6 +914,8 @@ def main():
         run_pairs(args)
     elif args.workload == "multistart_2d":
         run_multistart(args)
+    elif args.workload == "sdf_large":
+        run_sdf_large(args)
     else:
         run_ours(args)
 

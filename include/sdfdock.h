@@ -144,10 +144,13 @@ const char* sd_last_error(const sd_ctx* ctx);
  * default 0), "spread_fused" (1: in
  * pruned 3D FP32 searches with w = 6, spread each rotation's samples straight
  * into whole rows held in shared memory and run the forward x transform there,
- * with no sub-box in device memory; default 0), "sdf_cull" (1, the
- * default: the SDF sums skip boundary
- * tiles that lie beyond the truncation radius of every query of a block; 0: sum
- * over every tile; results are the same), "autotune" (1: before a scoring job
+ * with no sub-box in device memory; default 0), "sdf_cull" (2, the default:
+ * the SDF sums skip every 256-sample boundary tile that lies beyond the
+ * truncation radius (1 + eps)|xi| of every query of a block, and each warp skips
+ * the 32-sample sub-tiles beyond that radius of its own 32 queries -- the
+ * restriction of Eq. 13's sum to the eps-approximate neighbours of Section 4
+ * through the Morton-ordered samples; 1: tiles only; 0: sum over every tile;
+ * results are the same), "autotune" (1: before a scoring job
  * runs, time its candidate plans -- rotations per batch from a quarter to
  * twice the automatic choice, direct spreading, shared boxes of sample blocks,
  * bins of 8, 12 or 16 cells, or
@@ -248,8 +251,9 @@ int sd_octree_free(sd_octree* t);
 
 /* For each rotation r, the best translation of Re f_N(R_r, t) over the grid.
  *   quats     device, n_r x 4 double
- *   k_r       candidates per rotation; only 1 is supported
- *   cand_out  device, n_r x k_r sd_cand, ordered by rotation
+ *   k_r       candidates per rotation, 1 <= k_r <= 16: the k_r best translations
+ *             of each rotation (score descending, index ascending)
+ *   cand_out  device, n_r x k_r sd_cand, ordered by rotation, then rank
  * f_N is the band-limited periodic score: the pair sum of c1_i c2_j times the
  * Fourier series of the Gaussian of width sigma_g*sqrt(2) on the box, modes
  * |kappa_d| < N/2.  Computed per rotation as: rotate S2's samples, spread them

@@ -77,7 +77,7 @@ struct sd_ctx {
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
-    int opt_sdf_cull = 1;       // 0: SDF sums over every boundary tile
+    int opt_sdf_cull = 2;       // 0: SDF sums over every boundary tile; 1: skip far tiles; 2: and far sub-tiles per warp
     int opt_autotune = 0;       // 1: time candidate plans per job geometry
     std::map<std::string, Plan> tuned;
     DevBuf ws[8];
@@ -789,6 +789,7 @@ struct Search {
     int maps = 0;
     Plan plan{};
     bool pruned = false;  // pruned forward passes with the shifted table W'
+    int k_r = 1;          // candidates per rotation (argmax output)
     int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
     cplx<T>* b0 = nullptr;
     cplx<T>* b1 = nullptr;
@@ -848,8 +849,11 @@ static void search_need(const Search<T>& S, size_t need[8]) {
     const size_t B = (size_t)S.plan.B;
     need[0] = std::max(need[0], B * S.e0 * sizeof(cplx<T>));
     need[1] = std::max(need[1], B * S.e1 * sizeof(cplx<T>));
-    need[2] = std::max(need[2], B * S.rows_last * sizeof(double));  // at most one partial per row
-    need[3] = std::max(need[3], B * S.rows_last * sizeof(int));
+    // argmax partials: one per block of rows, or up to 16 per block (k_r > 1):
+    // blocks hold at least 8 rows, so twice the rows rounded up to 16 bounds both
+    const size_t parts = 2 * (((size_t)S.rows_last + 15) / 16) * 16;
+    need[2] = std::max(need[2], B * parts * sizeof(double));
+    need[3] = std::max(need[3], B * parts * sizeof(int));
     if (S.plan.bins == SPREAD_X) need[6] = std::max(need[6], bins_bytes_x(S.G.s, S.moving->m, S.plan.B));
     else if (S.plan.bins > SPREAD_BOX)
         need[6] = std::max(need[6], bins_bytes(S.G.s, S.G.dim, S.moving->m, S.plan.B, S.plan.bins));
@@ -962,12 +966,17 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             int nparts = 0;
             r.part_score = S.ps;
             r.part_idx = S.pi;
+            // k_r > 1: each block keeps its K >= k_r best (K a power of two, <= 16)
+            const int K = S.k_r <= 1 ? 1 : (S.k_r <= 2 ? 2 : (S.k_r <= 4 ? 4 : (S.k_r <= 8 ? 8 : 16)));
+            const int mode = K == 1 ? ROW_INV_ARGMAX
+                                    : (K == 2 ? ROW_INV_TOPK2 : (K == 4 ? ROW_INV_TOPK4 : (K == 8 ? ROW_INV_TOPK8 : ROW_INV_TOPK16)));
             {
                 PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
-                CK(ctx, launch_rows<T>(ROW_INV_ARGMAX, r, b, &nparts, s));
+                CK(ctx, launch_rows<T>(mode, r, b, &nparts, s));
             }
             PassTimer pt(ctx, SD_PASS_REDUCE, s, timed);
-            CK(ctx, launch_reduce_argmax(S.ps, S.pi, nparts, b, r0, S.out, s));
+            if (K == 1) CK(ctx, launch_reduce_argmax(S.ps, S.pi, nparts, b, r0, S.out, s));
+            else CK(ctx, launch_reduce_topk(S.ps, S.pi, nparts, K, S.k_r, b, r0, S.out, s));
         }
     }
     return SD_OK;
@@ -1056,9 +1065,10 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
 // captured graph when the "graph" option is on).
 template <typename T>
 static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,
-                      const sd_grid* g, void* out, int maps, cudaStream_t st) {
+                      const sd_grid* g, void* out, int maps, cudaStream_t st, int k_r = 1) {
     Search<T> S;
     CKI(search_setup<T>(ctx, fixed, moving, quats, n_r, g, out, maps, st, &S));
+    S.k_r = k_r;
     if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) CKI(autotune<T>(ctx, &S, st));
     size_t need[8] = {};
     search_need(S, need);
@@ -1067,9 +1077,9 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
 
     if (ctx->opt_graph && !ctx->opt_plain && st != nullptr) {
         char key[256];
-        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d|%d|%d", (const void*)fixed,
+        snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d|%d|%d|%d", (const void*)fixed,
                  (const void*)moving, (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B,
-                 S.plan.bins, (int)S.pruned, ctx->opt_timing);
+                 S.plan.bins, (int)S.pruned, ctx->opt_timing, S.k_r);
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
@@ -1360,7 +1370,7 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
         (e = pool_alloc((void**)&perm_b, (size_t)n_b * sizeof(int32_t), st)) != cudaSuccess ||
         (e = pool_alloc((void**)&bnd_s, (size_t)n_b * sizeof(vec4<T>), st)) != cudaSuccess ||
         (e = pool_alloc((void**)&nrm_s, (size_t)n_b * sizeof(vec4<T>), st)) != cudaSuccess ||
-        (e = pool_alloc((void**)&tbox, (size_t)n_tiles * 6 * sizeof(float), st)) != cudaSuccess)
+        (e = pool_alloc((void**)&tbox, (size_t)n_tiles * (1 + SDF_TILE / 32) * 6 * sizeof(float), st)) != cudaSuccess)
         return fail_free(SD_ERR_OOM, "allocation failed", e);
     // bounding radii of the queries and of the boundary samples
     double r2[2] = {0.0, 0.0};
@@ -1405,6 +1415,7 @@ static int sdf_build_t(sd_ctx* ctx, const void* bnd, const void* nrm, const void
     a.pos_out = (vec4<T>*)s->pos;
     a.perm_q = perm_q;
     a.tile_box = ctx->opt_sdf_cull ? tbox : nullptr;
+    a.sub_box = ctx->opt_sdf_cull >= 2 ? tbox + n_tiles * 6 : nullptr;
     a.n_tiles = n_tiles;
     e = launch_sdf<T>(a, ctx->p.dim, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1521,12 +1532,12 @@ int sd_score_rotations(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movin
     if (n_r < 0 || n_r > (int64_t)INT32_MAX) return fail(ctx, SD_ERR_ARG, "score_rotations: bad rotation count");
     if (n_r == 0) return SD_OK;
     if (!quats || !cand_out) return fail(ctx, SD_ERR_ARG, "score_rotations: NULL pointer");
-    if (k_r != 1) return fail(ctx, SD_ERR_UNIMPLEMENTED, "score_rotations: only k_r = 1 is supported");
+    if (k_r < 1 || k_r > 16) return fail(ctx, SD_ERR_ARG, "score_rotations: k_r must be in [1, 16] (got %d)", k_r);
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (ctx->p.precision == SD_F64)
-        return run_search<double>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st);
-    return run_search<float>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st);
+        return run_search<double>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st, k_r);
+    return run_search<float>(ctx, fixed, moving, quats, n_r, g, cand_out, 0, st, k_r);
 }
 
 int sd_score_maps(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving, const double* quats, int64_t n_r,

@@ -41,10 +41,13 @@ struct SdfArgs {
     vec4<T>* pos_out;     // m: copy of the query points for the shape (processing order)
     const int32_t* perm_q;  // processing order of the queries (caller index), or null
     const float* tile_box;  // boundary tile boxes (n_tiles x 6: lo, hi), or null
+    const float* sub_box;   // boxes of 32-sample sub-tiles (n_tiles * SDF_TILE / 32 x 6), or null
     int64_t n_tiles;        // boundary tiles of SDF_TILE samples
 };
 // Boundary samples gathered into Morton order: positions, normals with the
-// area in .w, and the bounding box of every tile of SDF_TILE samples.
+// area in .w, the bounding box of every tile of SDF_TILE samples (tile_box,
+// n_tiles x 6) followed by those of its 32-sample sub-tiles
+// (n_tiles * SDF_TILE / 32 x 6 more floats).
 template <typename T>
 cudaError_t launch_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T* area, const int32_t* perm,
                                   int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box,
@@ -111,7 +114,11 @@ cudaError_t launch_spread_x(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, 
 // *_P modes are the pruned forward passes of the search: the sub-box is read
 // unshifted (cell a at position a, a < s <= n/2; the shift is a phase folded
 // into W, see launch_wshift), and only the N = n/2 central modes are computed.
-enum RowMode { ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3, ROW_FWD_P = 4 };
+// ROW_INV_TOPK*: inverse x keeping each block's 2 / 4 / 8 / 16 best translations.
+enum RowMode {
+    ROW_FWD = 0, ROW_INV_ARGMAX = 1, ROW_INV_MAP = 2, ROW_EXPAND = 3, ROW_FWD_P = 4,
+    ROW_INV_TOPK2 = 8, ROW_INV_TOPK4 = 9, ROW_INV_TOPK8 = 10, ROW_INV_TOPK16 = 11
+};
 enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FUSED = 2, COL_EXPAND = 3, COL_FWD_P = 4, COL_FUSED_P = 5 };
 
 // Whether the pruned passes serve an oversampled length n (a host-side copy of
@@ -178,6 +185,11 @@ cudaError_t launch_wtable(const cplx<T>* B1, const double* D, int N, int dim, do
 // forward passes read the sub-box unshifted (the *_P modes).
 template <typename T>
 cudaError_t launch_wshift(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out, cudaStream_t st);
+
+// top-K partials (K per block, K in {2, 4, 8, 16}) -> the k_r <= K best
+// candidates of each rotation (score descending, index ascending)
+cudaError_t launch_reduce_topk(const double* part_score, const int* part_idx, int nparts, int K, int k_r, int batch,
+                               int64_t rot0, void* cand, cudaStream_t st);
 
 // argmax partials -> one candidate per rotation
 cudaError_t launch_reduce_argmax(const double* part_score, const int* part_idx, int nparts, int batch,

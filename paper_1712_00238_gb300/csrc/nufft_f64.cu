@@ -1,6 +1,7 @@
 // FP64 instantiation of the nonuniform-FFT passes, plus the FP64 tables and the
 // per-rotation argmax reduction shared by both precisions.
 #include "nufft_impl.cuh"
+#include "topk.cuh"
 SD_INSTANTIATE_NUFFT(double)
 
 namespace sd {
@@ -85,6 +86,44 @@ cudaError_t launch_reduce_argmax(const double* ps, const int* pi, int nparts, in
                                  void* cand, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     k_reduce_argmax<<<batch, 256, 0, st>>>(ps, pi, nparts, rot0, reinterpret_cast<CandRec*>(cand));
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int K>
+__global__ void k_reduce_topk(const double* ps, const int* pi, int nparts, int k_r, int64_t rot0, CandRec* cand) {
+    extern __shared__ __align__(16) unsigned char rk_raw[];
+    double* sv = reinterpret_cast<double*>(rk_raw);
+    int* si = reinterpret_cast<int*>(sv + blockDim.x * K);
+    __shared__ double wv[32], bestv[K];
+    __shared__ int wi[32], besti[K];
+    const int b = blockIdx.x;
+    TopK<double, K> top;
+    top.init();
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) top.push(ps[(int64_t)b * nparts + p], pi[(int64_t)b * nparts + p]);
+    block_topk_merge<double, K>(top, sv, si, wv, wi, bestv, besti);
+    if (threadIdx.x < k_r) {
+        CandRec c;
+        const bool real = besti[threadIdx.x] != INT_MAX;
+        c.score = real ? bestv[threadIdx.x] : -INFINITY;
+        c.rot = (int32_t)(rot0 + b);
+        c.idx = real ? besti[threadIdx.x] : -1;
+        cand[(rot0 + b) * (int64_t)k_r + threadIdx.x] = c;
+    }
+}
+
+cudaError_t launch_reduce_topk(const double* ps, const int* pi, int nparts, int K, int k_r, int batch, int64_t rot0,
+                               void* cand, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    CandRec* c = reinterpret_cast<CandRec*>(cand);
+    const size_t smem = (size_t)128 * K * (sizeof(double) + sizeof(int));
+    switch (K) {
+        case 2: k_reduce_topk<2><<<batch, 128, smem, st>>>(ps, pi, nparts, k_r, rot0, c); break;
+        case 4: k_reduce_topk<4><<<batch, 128, smem, st>>>(ps, pi, nparts, k_r, rot0, c); break;
+        case 8: k_reduce_topk<8><<<batch, 128, smem, st>>>(ps, pi, nparts, k_r, rot0, c); break;
+        case 16: k_reduce_topk<16><<<batch, 128, smem, st>>>(ps, pi, nparts, k_r, rot0, c); break;
+        default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }

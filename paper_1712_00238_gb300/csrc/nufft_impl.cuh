@@ -26,6 +26,7 @@
 #include "fft.cuh"
 #include "fftp.cuh"
 #include "kernels.cuh"
+#include "topk.cuh"
 
 namespace sd {
 
@@ -1382,6 +1383,51 @@ __global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_p(RowArgs<T>
     rows_inv_p_body<T, LEN, MODE>(a);
 }
 
+// Inverse x of rows of N points keeping each block's K best translations of the
+// real part (score descending, index ascending): a sorted list per thread, merged
+// through shared memory after the transform; partials are K per block.
+template <typename T, int LEN, int K>
+__device__ __forceinline__ void rows_inv_topk_body(const RowArgs<T>& a) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int NT = cta_threads<T, LEN>();
+    constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int PL = LEN / plan_last_radix(LEN);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + TR * LD;
+    T* sv = reinterpret_cast<T*>(tw + NTW);
+    int* si = reinterpret_cast<int*>(sv + NT * K);
+    __shared__ T wv[32], bestv[K];
+    __shared__ int wi[32], besti[K];
+    const int row0 = blockIdx.x * TR;
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
+    __syncthreads();
+    const C* in = a.in + (int64_t)blockIdx.y * a.in_rot_stride + (int64_t)row0 * LEN;
+    const int nrows = a.nrows - row0;
+    const C zero = mk(T(0), T(0));
+    auto load = [&](int line, int i, int r) -> C { return line < nrows ? in[line * LEN + i + r * NB1] : zero; };
+    TopK<T, K> top;
+    top.init();
+    auto emit = [&](int line, int i, int r, C v) {
+        if (line < nrows) top.push(v.x, (row0 + line) * LEN + i + r * PL);
+    };
+    fftp_lines<C, LEN, true, TR, NT, LAY_ROW, true, false, false>(buf, LD, tw, load, emit);
+    block_topk_merge<T, K>(top, sv, si, wv, wi, bestv, besti);
+    if (threadIdx.x < K) {
+        const int64_t o = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * K + threadIdx.x;
+        a.part_score[o] = (double)bestv[threadIdx.x];
+        a.part_idx[o] = besti[threadIdx.x];
+    }
+}
+
+template <typename T, int LEN, int K>
+__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_topk(RowArgs<T> a) {
+    rows_inv_topk_body<T, LEN, K>(a);
+}
+
 // Resident CTAs per SM the pruned passes are compiled for (0: the compiler's choice).
 // 512-point FP32 lines (256 threads, two butterflies each) take 2 (at most 128
 // registers; 146 otherwise); 384-point ones 3 (384 threads: at most 56).
@@ -1561,8 +1607,42 @@ static cudaError_t cols_inv_p_impl(const ColArgs<T>& a, int batch, cudaStream_t 
     return cudaGetLastError();
 }
 
+template <typename T, int LEN, int K>
+static cudaError_t rows_inv_topk_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    using C = cplx<T>;
+    constexpr int TR = lines_per_cta<T, LEN>();
+    constexpr int NT = cta_threads<T, LEN>();
+    const int nb = (a.nrows + TR - 1) / TR;
+    if (nparts) *nparts = nb * K;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    if (a.in_row_stride != LEN) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(TR * line_pitch(LEN) + tw_count(LEN)) * sizeof(C) + (size_t)NT * K * (sizeof(T) + sizeof(int));
+    auto kern = k_rows_inv_topk<T, LEN, K>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, batch), NT, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_rows_t(int mode, const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    if (mode >= ROW_INV_TOPK2 && mode <= ROW_INV_TOPK16) {
+        switch (a.N) {
+#define SD_ROWK_CASE(L)                                                                         \
+    case L:                                                                                     \
+        switch (mode) {                                                                         \
+            case ROW_INV_TOPK2: return rows_inv_topk_impl<T, L, 2>(a, batch, nparts, st);       \
+            case ROW_INV_TOPK4: return rows_inv_topk_impl<T, L, 4>(a, batch, nparts, st);       \
+            case ROW_INV_TOPK8: return rows_inv_topk_impl<T, L, 8>(a, batch, nparts, st);       \
+            default: return rows_inv_topk_impl<T, L, 16>(a, batch, nparts, st);                 \
+        }
+            SD_ROWK_CASE(8) SD_ROWK_CASE(16) SD_ROWK_CASE(24) SD_ROWK_CASE(32) SD_ROWK_CASE(48) SD_ROWK_CASE(64)
+            SD_ROWK_CASE(96) SD_ROWK_CASE(128) SD_ROWK_CASE(192) SD_ROWK_CASE(256)
+#undef SD_ROWK_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
     if (mode == ROW_INV_ARGMAX || mode == ROW_INV_MAP) {
         switch (a.N) {
 #define SD_ROWI_CASE(L)                                                                                    \

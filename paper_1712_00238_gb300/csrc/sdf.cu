@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a, int tiles_pe
     __shared__ vec4<T> sn[SDF_TILE];
     __shared__ float wred[SDF_TILE / 32][7];
     __shared__ float box[7];  // lo[3], hi[3], reach
+    float wbox[7] = {0, 0, 0, 0, 0, 0, 0};  // the warp's lo[3], hi[3], reach
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.m;
     const int64_t src = live ? (a.perm_q ? (int64_t)a.perm_q[i] : i) : 0;
@@ -143,6 +144,9 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a, int tiles_pe
         }
         if ((threadIdx.x & 31) == 0)
             for (int d = 0; d < 7; ++d) wred[threadIdx.x >> 5][d] = v[d];
+        // this warp's own box and reach, for the sub-tile test
+        for (int d = 0; d < 7; ++d) wbox[d] = __shfl_sync(0xffffffffu, v[d], 0);
+        wbox[6] = wbox[6] * (1.f + (float)a.eps) * (1.f + 1e-4f) + 1e-6f;
         __syncthreads();
         if (threadIdx.x < 7) {
             float r = wred[0][threadIdx.x];
@@ -183,6 +187,17 @@ __global__ void __launch_bounds__(SDF_TILE) k_sdf_sum(SdfArgs<T> a, int tiles_pe
         __syncthreads();
         const int cnt = (int)min((int64_t)SDF_TILE, a.n_b - t0);
         for (int k = 0; k < cnt; ++k) {
+            if (cull && a.sub_box && (k & 31) == 0) {
+                // skip the 32-sample sub-tile when it lies beyond this warp's reach
+                const float* sb = a.sub_box + (tile * (SDF_TILE / 32) + (k >> 5)) * 6;
+                const float g0 = fmaxf(0.f, fmaxf(sb[0] - wbox[3], wbox[0] - sb[3]));
+                const float g1 = fmaxf(0.f, fmaxf(sb[1] - wbox[4], wbox[1] - sb[4]));
+                const float g2 = (D == 3) ? fmaxf(0.f, fmaxf(sb[2] - wbox[5], wbox[2] - sb[5])) : 0.f;
+                if (g0 * g0 + g1 * g1 + g2 * g2 > wbox[6] * wbox[6]) {  // same in every lane of the warp
+                    k += 31;
+                    continue;
+                }
+            }
             const vec4<T> q = sq[k];
             const T dx = p.x - q.x, dy = p.y - q.y, dz = (D == 3) ? p.z - q.z : T(0);
             const T d2 = dx * dx + dy * dy + dz * dz;
@@ -237,7 +252,8 @@ __global__ void k_sdf_sum_finish(SdfArgs<T> a, int splits, const cplx<T>* part) 
 
 template <typename T>
 __global__ void k_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T* area, const int32_t* perm,
-                                 int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box) {
+                                 int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box,
+                                 float* sub_box) {
     __shared__ float wred[SDF_TILE / 32][6];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
@@ -256,8 +272,15 @@ __global__ void k_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const T
         for (int d = 0; d < 3; ++d) v[d] = fminf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
         for (int d = 3; d < 6; ++d) v[d] = fmaxf(v[d], __shfl_down_sync(0xffffffffu, v[d], off));
     }
-    if ((threadIdx.x & 31) == 0)
+    if ((threadIdx.x & 31) == 0) {
         for (int d = 0; d < 6; ++d) wred[threadIdx.x >> 5][d] = v[d];
+        // the box of this warp's 32 samples (a sub-tile), widened like the tile's
+        float* sb = sub_box + ((int64_t)blockIdx.x * (SDF_TILE / 32) + (threadIdx.x >> 5)) * 6;
+        for (int d = 0; d < 6; ++d) {
+            const float m = 1e-6f * (fabsf(v[d]) + 1.f);
+            sb[d] = v[d] == FLT_MAX || v[d] == -FLT_MAX ? v[d] : (d < 3 ? v[d] - m : v[d] + m);
+        }
+    }
     __syncthreads();
     if (threadIdx.x < 6) {
         float r = wred[0][threadIdx.x];
@@ -274,8 +297,9 @@ cudaError_t launch_boundary_order(const vec4<T>* bnd, const vec4<T>* nrm, const 
                                   int64_t n_b, int dim, vec4<T>* bnd_s, vec4<T>* nrm_s, float* tile_box,
                                   cudaStream_t st) {
     if (n_b == 0) return cudaSuccess;
-    k_boundary_order<T><<<(unsigned)((n_b + SDF_TILE - 1) / SDF_TILE), SDF_TILE, 0, st>>>(bnd, nrm, area, perm, n_b,
-                                                                                        dim, bnd_s, nrm_s, tile_box);
+    const int64_t n_tiles = (n_b + SDF_TILE - 1) / SDF_TILE;
+    k_boundary_order<T><<<(unsigned)n_tiles, SDF_TILE, 0, st>>>(bnd, nrm, area, perm, n_b, dim, bnd_s, nrm_s, tile_box,
+                                                                tile_box + n_tiles * 6);
     note_launch();
     return cudaGetLastError();
 }

@@ -160,6 +160,13 @@ def _sphere_shape(name, n_spheres, seed, per_sphere=40, band=2.0, density=2.0):
 
 
 @functools.lru_cache(maxsize=None)
+def large_sphere_shape(n_spheres: int = 5000, seed: int = 4) -> ShapeInput:
+    """One shape at the top of the uneven batch's size range (5,000 spheres:
+    ~2e5 SDF samples against ~2e5 boundary samples), built by the same rules."""
+    return _sphere_shape(f"spheres{n_spheres}", n_spheres, seed * 1000 + 999)
+
+
+@functools.lru_cache(maxsize=None)
 def docking_pair(n_rec: int = 2000, n_lig: int = 500, seed: int = 2) -> tuple[ShapeInput, ShapeInput]:
     return _sphere_shape("receptor", n_rec, seed), _sphere_shape("ligand", n_lig, seed)
 

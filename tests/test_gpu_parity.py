@@ -628,9 +628,10 @@ def test_argument_errors_are_reported():
     with pytest.raises(sd.SdError) as e:
         ctx.score_rotations(fx, mv, q, sd.Grid(100, w.L))
     assert e.value.code == sd.SD_ERR_ARG
-    with pytest.raises(sd.SdError) as e:
-        ctx.score_rotations(fx, mv, q, grid_of(w), k_r=2)
-    assert e.value.code == sd.SD_ERR_UNIMPLEMENTED
+    for bad_k in (0, 17):
+        with pytest.raises(sd.SdError) as e:
+            ctx.score_rotations(fx, mv, q, grid_of(w), k_r=bad_k)
+        assert e.value.code == sd.SD_ERR_ARG
     with pytest.raises(sd.SdError):
         ctx.score_rotations(fx, mv, q, sd.Grid(32, -1.0))
     other = make_ctx(w)
@@ -737,3 +738,71 @@ def test_alu_peak_probe_rates_are_plausible():
     import ctypes as ct
     v = ct.c_double()
     assert lib.sd_alu_peak(0, 9, ct.byref(v)) == sd.SD_ERR_ARG
+
+
+def test_sdf_cull_levels_agree_on_a_large_shape():
+    # the eps-neighbour restriction of the SDF sums (boundary tiles beyond the
+    # truncation radius of a block's queries, 32-sample sub-tiles beyond a warp's)
+    # skips only pairs that Eq. 17t drops: the sums are the same to the bit, at
+    # the top of the uneven batch's size range (~2e5 queries x ~3e5 samples)
+    s = configs.large_sphere_shape()
+    w = configs.docking_2000_500()
+    ctx = make_ctx(w)
+    rhos = {}
+    for level in (2, 1, 0):
+        ctx.set_option("sdf_cull", level)
+        _, rho = gpu_shape(ctx, s, return_rho=True)
+        rhos[level] = rho.cpu().numpy()
+    assert np.array_equal(rhos[2], rhos[1]) and np.array_equal(rhos[2], rhos[0])
+    rng = np.random.default_rng(5)
+    sel = rng.choice(s.query.m, 200, replace=False)
+    b = s.boundary
+    ref = osdf.sdf_rho(s.query.pos[sel], b.pos, b.normal, b.area, **w.sdf_params())
+    assert rel_err(rhos[2][sel, 0] + 1j * rhos[2][sel, 1], ref) < 1e-4
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,prec,N,k_r", [("tiny_3d", "f32", 16, 5), ("tiny_3d", "f32", 48, 16),
+                                             ("tiny_2d", "f64", 32, 3), ("tiny_2d", "f32", 8, 12)])
+def test_several_candidates_per_rotation(name, prec, N, k_r):
+    # k_r > 1: the k_r best translations of every rotation, score descending then
+    # index ascending, against the same maps and the oracle's
+    w = getattr(configs, name)()
+    p1, c1, p2, c2 = oracle_weights(name)
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    maps = ctx.score_maps(fx, mv, q, g).cpu().numpy().real
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g).real
+    s, rot, idx = (t.cpu().numpy().reshape(w.n_rot, k_r) for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g,
+                                                                                                      k_r=k_r)))
+    run_tol = 1e-12 if prec == "f64" else 1e-6
+    for r in range(w.n_rot):
+        assert np.all(rot[r] == r)
+        order = np.lexsort((np.arange(maps[r].size), -maps[r]))[:k_r]
+        scale = np.abs(maps[r]).max()
+        # the scores are the map's k_r largest, in order
+        assert np.all(np.diff(s[r]) <= 0)
+        assert np.allclose(s[r], maps[r][order], rtol=0, atol=run_tol * scale)
+        # the same translations wherever consecutive values are separated
+        srt = maps[r][order]
+        gaps = -np.diff(np.append(srt, np.sort(maps[r])[::-1][k_r]))
+        for k in range(k_r):
+            if gaps[k] > 10 * run_tol * scale and (k == 0 or gaps[k - 1] > 10 * run_tol * scale):
+                assert idx[r, k] == order[k], (r, k)
+        # and the oracle's, where its margins exceed the path's tolerance
+        ro = np.lexsort((np.arange(ref[r].size), -ref[r]))[:k_r + 1]
+        rs = ref[r][ro]
+        tol = TOL[prec] * np.abs(ref[r]).max()
+        for k in range(k_r):
+            if rs[k] - rs[k + 1] > 2 * tol and (k == 0 or rs[k - 1] - rs[k] > 2 * tol):
+                assert idx[r, k] == ro[k], (r, k)
+    # the global top-k over all of them
+    cand = ctx.score_rotations(fx, mv, q, g, k_r=k_r)
+    s2, rot2, idx2 = (t.cpu().numpy() for t in sd.decode_cands(cand))
+    poses = ctx.top_k_poses(cand, 4, fx, mv, q, g, rescore_fp64=False)
+    flat = np.lexsort((idx2, rot2, -s2))[:4]
+    assert [(p["rot"], p["idx"]) for p in poses] == [(int(rot2[i]), int(idx2[i])) for i in flat]
+    ctx.close()
