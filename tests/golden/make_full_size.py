@@ -125,7 +125,7 @@ def peg(pool):
                 t = oscore.translation_of_index(i, w.N, w.L, 3)
                 t0 = time.time()
                 fc = f_c(p1, c1, p2, c2, w.quats[r], t, w.sigma_g, pool)
-                f.write(f"{k} {r} {i} {s!r} {fc.real!r} {fc.imag!r}\n")
+                f.write(f"{k} {r} {i} {float(s)!r} {float(fc.real)!r} {float(fc.imag)!r}\n")
                 f.flush()
                 print(f"f_c rank {k}: {time.time() - t0:.0f} s", flush=True)
 
