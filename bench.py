@@ -69,8 +69,11 @@ def parse_args():
                          "forward x transform there (3D FP32)")
     ap.add_argument("--spread-box", type=int, default=0,
                     help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
+    ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="forward-pass FFT plan: -1 the autotuner's (or the pruned default), 0 full, 1 pruned, "
+                         "2 pruned with narrow column CTAs")
     ap.add_argument("--autotune", type=int, default=1,
-                    help="1: the library times candidate plans (batch, spreading) once per geometry")
+                    help="1: the library times candidate plans (batch, spreading, FFT plan) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
     ap.add_argument("--workload", choices=["peg_in_bore_3d", "peg_in_hole_2d", "docking_2000_500", "refine_256",
                                            "uneven_batch", "multistart_2d", "sdf_large"],
@@ -258,6 +261,7 @@ def run_ours(args):
     ctx.set_option("spread_direct", args.spread_direct)
     ctx.set_option("spread_fused", args.spread_fused)
     ctx.set_option("spread_box", args.spread_box)
+    ctx.set_option("fft_plan", args.fft_plan)
     ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
     plan_used = {}
@@ -414,6 +418,7 @@ def run_ours(args):
                               if plan_used.get("spread_bins") == 2 else
                               f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
                               if plan_used.get("spread_bins") else "global vector atomics"),
+                   "fft_plan": FFT_PLAN_TEXT.get(plan_used.get("fft_plan")),
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -488,6 +493,13 @@ def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
 # sub-box side, N, rotations per launch); a launch of another shape reports
 # null.  Docking pair: one 20-rotation launch of the pruned fused pass, whose
 # product table is read from DRAM once per launch (its other rotations hit L2).
+# the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW)
+FFT_PLAN_TEXT = {
+    0: "full: shifted sub-box padded to n, every output of each line",
+    1: "pruned: zero upper half skipped, only the N kept modes; shift as a phase in W",
+    2: "pruned, half the columns per CTA in the forward y and fused z passes",
+}
+
 TRAFFIC_PER_LAUNCH: dict = {
     ("fused", 156, 192, 20): 976803840 + 1081333248,
 }

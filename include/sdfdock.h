@@ -138,7 +138,10 @@ const char* sd_last_error(const sd_ctx* ctx);
  * shared memory first), "pruned" (1, the default: the forward FFT passes of the
  * search read the spread sub-box unshifted and compute only the kept modes, with
  * the shift applied as a phase in the product table; 0: the shifted sub-box and
- * every mode; results are the same up to FP rounding), "spread_box" (1: each
+ * every mode; results are the same up to FP rounding), "fft_plan" (-1, the
+ * default: the autotuner's choice, else SD_FFT_PRUNED where the pruned passes
+ * apply; 0..2: that SD_FFT_* plan wherever it applies, never tuned),
+ * "spread_box" (1: each
  * CTA spreads a block of Morton-consecutive samples into a shared box of the
  * sub-box and adds the box's nonzero cells with 16-byte atomics; FP32, w 4-7;
  * default 0), "spread_fused" (1: in
@@ -156,7 +159,9 @@ const char* sd_last_error(const sd_ctx* ctx);
  * bins of 8, 12 or 16 cells, or
  * (pruned 3D FP32 searches with w = 6) spreading fused with the forward x
  * transform -- on its first
- * rotations and keep the fastest; the choice is cached per precision, grid,
+ * rotations and keep the fastest, then time the other forward-pass FFT plans
+ * (SD_FFT_*) under that choice and keep the fastest of those; the choice is
+ * cached per precision, grid,
  * sub-box size and sample-count octave; ignored when "batch" or "plain" is
  * set; results do not depend on the plan beyond FP32 rounding). */
 int sd_set_option(sd_ctx* ctx, const char* key, int64_t value);
@@ -290,6 +295,7 @@ typedef struct sd_pair_stat {
                              2: shared boxes of sample blocks */
     int32_t n;            /* oversampled grid size per axis */
     int32_t s;            /* sub-box side of its moving shape */
+    int32_t fft_plan;     /* forward-pass plan of its search (SD_FFT_*) */
 } sd_pair_stat;
 
 /* Score many shape pairs, each on its own grid and rotation list, in one
@@ -311,17 +317,31 @@ typedef struct sd_pair_stat {
 int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair_stat* stats,
                    void* stream);
 
+/* Forward-pass FFT plans of a search (Section 5's transform over the
+ * translations, computed axis by axis):
+ *   SD_FFT_FULL           every pass reads the shifted sub-box padded to n and
+ *                         computes all n outputs of each line
+ *   SD_FFT_PRUNED         the passes skip the zero upper half of each line and
+ *                         compute only the N kept modes; the sub-box shift is a
+ *                         phase folded into the product table
+ *   SD_FFT_PRUNED_NARROW  as PRUNED, with half the columns per CTA in the
+ *                         forward y and fused last-axis passes (FP32, n >= 128) */
+#define SD_FFT_FULL 0
+#define SD_FFT_PRUNED 1
+#define SD_FFT_PRUNED_NARROW 2
+
 /* The plan a search of n_r rotations of `moving` on grid g would run with now:
- * rotations per batch and the bin side of binned spreading (0: direct; 1:
+ * rotations per batch, the bin side of binned spreading (0: direct; 1:
  * spreading fused with the forward x transform; 2: shared boxes of sample
- * blocks).  With the
+ * blocks) and the forward-pass FFT plan (SD_FFT_*).  Each output pointer may
+ * be NULL.  With the
  * "autotune" option it is the cached choice for this geometry if there is one
  * (the first search of a geometry makes it), else the default.  No device work. */
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
-                   int32_t* spread_bins);
+                   int32_t* spread_bins, int32_t* fft_plan);
 
 /* The autotuner's cached plans as JSON text,
- *   {"sdfdock_plans": 1, "plans": [{"key": K, "batch": B, "spread_bins": S}, ...]}
+ *   {"sdfdock_plans": 1, "plans": [{"key": K, "batch": B, "spread_bins": S, "fft": F}, ...]}
  * (K: precision|dim|N|n|sub-box/16|log2 of the moving sample count).  *len
  * receives the size including the terminating NUL; with buf NULL only the size
  * is returned; a smaller cap is SD_ERR_ARG. */
@@ -329,9 +349,11 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
 
 /* Add the plans of a JSON text written by sd_tune_export to this context's
  * cache (entries with a key already present are replaced), so searches of those
- * geometries skip the timing trials.  A text that is not such a table, or an
- * entry with batch outside [1, 64] or spread_bins not 0, 1, 2, 8, 12 or 16, is SD_ERR_ARG and
- * leaves the cache unchanged. */
+ * geometries skip the timing trials (an entry without "fft" takes
+ * SD_FFT_PRUNED; a plan that does not apply to a job is replaced by the job's
+ * default there).  A text that is not such a table, or an entry with batch
+ * outside [1, 64], spread_bins not 0, 1, 2, 8, 12 or 16, or fft not 0, 1 or 2,
+ * is SD_ERR_ARG and leaves the cache unchanged. */
 int sd_tune_import(sd_ctx* ctx, const char* json);
 
 /* Global top-k over per-rotation candidates, ordered by score descending,

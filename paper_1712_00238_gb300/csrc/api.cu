@@ -58,6 +58,7 @@ struct Plan {      // launch plan of one scoring job
     int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct,
                    // 1: spreading fused with the forward x transform (SPREAD_X),
                    // 2: shared boxes of sample blocks (SPREAD_BOX)
+    int fft = SD_FFT_PRUNED;  // forward-pass plan (SD_FFT_FULL / _PRUNED / _PRUNED_NARROW)
 };
 
 struct sd_ctx {
@@ -75,6 +76,7 @@ struct sd_ctx {
     int opt_plain = 0;
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
+    int opt_fft_plan = -1;      // >= 0: this SD_FFT_* plan wherever it applies (not tuned)
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
     int opt_sdf_cull = 2;       // 0: SDF sums over every boundary tile; 1: skip far tiles; 2: and far sub-tiles per warp
@@ -447,8 +449,9 @@ static cudaError_t pass_x_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
 // y pass (3D): (s,s,N) -> (s,N,N)
 template <typename T>
 static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
-                              int64_t out_rs, int batch, cudaStream_t st, int mode = COL_FWD) {
+                              int64_t out_rs, int batch, cudaStream_t st, int mode = COL_FWD, int narrow = 0) {
     ColArgs<T> c{};
+    c.narrow = narrow;
     c.in = in;
     c.out = out;
     c.in_rot_stride = in_rs;
@@ -469,8 +472,10 @@ static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
 // last axis (z in 3D, y in 2D): FWD (modes) or FUSED (product with W, inverse)
 template <typename T>
 static cudaError_t pass_last(int mode, const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs,
-                             cplx<T>* out, int64_t out_rs, const cplx<T>* W, int batch, cudaStream_t st) {
+                             cplx<T>* out, int64_t out_rs, const cplx<T>* W, int batch, cudaStream_t st,
+                             int narrow = 0) {
     ColArgs<T> c{};
+    c.narrow = narrow;
     c.in = in;
     c.out = out;
     c.in_rot_stride = in_rs;
@@ -788,7 +793,9 @@ struct Search {
     void* out = nullptr;
     int maps = 0;
     Plan plan{};
-    bool pruned = false;  // pruned forward passes with the shifted table W'
+    bool prunable = false;          // pruned forward passes apply (sub-box in the low half of a line)
+    bool narrowable = false;        // and their narrow column plan exists (FP32, n >= 128)
+    const cplx<T>* Wsh = nullptr;   // the shifted table W' of the pruned passes
     int k_r = 1;          // candidates per rotation (argmax output)
     int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
     cplx<T>* b0 = nullptr;
@@ -802,7 +809,23 @@ struct Search {
 // Spreading fused with the x transform: pruned 3D FP32 searches with w = 6.
 template <typename T>
 static bool spread_x_ok(const sd_ctx* ctx, const Search<T>& S) {
-    return sizeof(T) == 4 && S.G.dim == 3 && ctx->p.w == 6 && S.pruned;
+    return sizeof(T) == 4 && S.G.dim == 3 && ctx->p.w == 6 && S.plan.fft != SD_FFT_FULL;
+}
+
+// The forward-pass plans a job can run: FULL always, the pruned ones where the
+// sub-box fits.
+template <typename T>
+static bool fft_plan_ok(const Search<T>& S, int fft) {
+    return fft == SD_FFT_FULL || (fft == SD_FFT_PRUNED && S.prunable) ||
+           (fft == SD_FFT_PRUNED_NARROW && S.narrowable);
+}
+
+// The plan a job starts from: the forced one if it applies, else pruned where
+// possible.
+template <typename T>
+static int fft_plan_default(const sd_ctx* ctx, const Search<T>& S) {
+    if (ctx->opt_fft_plan >= 0 && fft_plan_ok(S, ctx->opt_fft_plan)) return ctx->opt_fft_plan;
+    return S.prunable ? SD_FFT_PRUNED : SD_FFT_FULL;
 }
 
 // Fixed-shape tables, geometry, twiddles and the default plan of a job (may
@@ -826,8 +849,9 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     S->rows_last = (S->G.dim == 2) ? S->G.N : (int64_t)S->G.N * S->G.N;
     S->Nd = (S->G.dim == 2) ? (int64_t)S->G.N * S->G.N : (int64_t)S->G.N * S->G.N * S->G.N;
     // pruned forward passes: the sub-box must fit in the low half of a line
-    S->pruned = ctx->opt_pruned && pruned_len_ok(S->G.n) && S->G.s <= S->G.N;
-    if (S->pruned) {
+    S->prunable = ctx->opt_pruned && pruned_len_ok(S->G.n) && S->G.s <= S->G.N;
+    S->narrowable = S->prunable && sizeof(T) == 4 && S->G.n >= 128;
+    if (S->prunable) {
         void* ws = nullptr;
         for (auto& w : prep->Wsh)
             if (w.first == S->G.s_h) ws = w.second;
@@ -836,8 +860,9 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
             CK(ctx, launch_wshift<T>((const cplx<T>*)prep->W, S->G.N, S->G.dim, S->G.n, S->G.s_h, (cplx<T>*)ws, st));
             prep->Wsh.emplace_back(S->G.s_h, ws);
         }
-        S->W = (const cplx<T>*)ws;
+        S->Wsh = (const cplx<T>*)ws;
     }
+    S->plan.fft = fft_plan_default(ctx, *S);
     if (ctx->opt_spread_box && bins_supported(ctx)) S->plan.bins = SPREAD_BOX;
     if (ctx->opt_spread_fused && spread_x_ok(ctx, *S)) S->plan.bins = SPREAD_X;
     return SD_OK;
@@ -907,9 +932,12 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         sa.out = S.b0;
         sa.out_rot_stride = S.e0;
         sa.n_full = G.n;
-        const int mx = S.pruned ? ROW_FWD_P : ROW_FWD;
-        const int my = S.pruned ? COL_FWD_P : COL_FWD;
-        const int mf = S.pruned ? COL_FUSED_P : COL_FUSED;
+        const bool pruned = S.plan.fft != SD_FFT_FULL;
+        const int narrow = S.plan.fft == SD_FFT_PRUNED_NARROW;
+        const int mx = pruned ? ROW_FWD_P : ROW_FWD;
+        const int my = pruned ? COL_FWD_P : COL_FWD;
+        const int mf = pruned ? COL_FUSED_P : COL_FUSED;
+        const C* Wp = pruned ? S.Wsh : S.W;
         if (fused_x) {
             // spreading and the forward x transform in one pass: no sub-box
             PassTimer pt(ctx, SD_PASS_SPREAD_X, s, timed);
@@ -929,11 +957,11 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         if (G.dim == 3) {
             {
                 PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
-                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s, my));
+                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s, my, narrow));
             }
             {
                 PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, S.W, b, s));
+                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, narrow));
             }
             {
                 PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
@@ -943,7 +971,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             fin_rs = S.e1;
         } else {
             PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, S.W, b, s));
+            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, Wp, b, s, narrow));
             fin = S.b0;
             fin_rs = S.e0;
         }
@@ -984,7 +1012,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
 
 // ---------------------------------------------------------------------------
 // autotuner: per job geometry, the plan (rotations per launch, spreading
-// variant) with the lowest measured time per rotation
+// variant, forward-pass FFT plan) with the lowest measured time per rotation
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -1007,9 +1035,12 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     if (it != ctx->tuned.end()) {
         S->plan.B = (int)std::min<int64_t>(it->second.B, std::max<int64_t>(S->n_r, 1));
         S->plan.bins = it->second.bins;
+        if (ctx->opt_fft_plan < 0 && fft_plan_ok(*S, it->second.fft)) S->plan.fft = it->second.fft;
         return SD_OK;
     }
-    const int b0 = S->plan.B;
+    // first stage: batch x spreading under the job's default FFT plan; second
+    // stage: the other FFT plans under the best of the first
+    const int b0 = S->plan.B, f0 = S->plan.fft;
     std::vector<Plan> cand;
     for (int B : {b0 / 4, b0 / 2, b0, 2 * b0}) {
         if (B < 1 || B > 64 || (B > S->n_r && B != b0)) continue;
@@ -1017,7 +1048,7 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
             if (bins == SPREAD_X ? !spread_x_ok(ctx, *S) : (bins && !bins_supported(ctx))) continue;
             bool dup = false;
             for (auto& c : cand) dup |= (c.B == B && c.bins == bins);
-            if (!dup) cand.push_back(Plan{B, bins});
+            if (!dup) cand.push_back(Plan{B, bins, f0});
         }
     }
     int most = 1;
@@ -1029,28 +1060,38 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
     Plan best = S->plan;
     double best_ms = INFINITY;
     int rc = SD_OK;
-    for (auto& c : cand) {
+    auto trial = [&](const Plan& c) -> int {
         Search<T> t = *S;
         t.plan = c;
         size_t need[8] = {};
         search_need(t, need);
-        if ((rc = ws_reserve(ctx, need)) != SD_OK) break;
+        CKI(ws_reserve(ctx, need));
         search_bind(ctx, &t);
-        if ((rc = search_enqueue(ctx, t, 0, std::min<int64_t>(n_trial, c.B), st, false)) != SD_OK) break;
+        CKI(search_enqueue(ctx, t, 0, std::min<int64_t>(n_trial, c.B), st, false));
         cudaEventRecord(e0, st);
-        if ((rc = search_enqueue(ctx, t, 0, n_trial, st, false)) != SD_OK) break;
+        CKI(search_enqueue(ctx, t, 0, n_trial, st, false));
         cudaEventRecord(e1, st);
         float ms = 0.f;
         cudaError_t e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            rc = fail(ctx, SD_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
-            break;
-        }
+        if (e != cudaSuccess) return fail(ctx, SD_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
         const double per = ms / (double)n_trial;
         if (per < best_ms) {
             best_ms = per;
             best = c;
+        }
+        return SD_OK;
+    };
+    for (auto& c : cand)
+        if ((rc = trial(c)) != SD_OK) break;
+    if (rc == SD_OK && ctx->opt_fft_plan < 0) {
+        const Plan first = best;
+        for (int f : {SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_FULL}) {
+            Plan c = first;
+            c.fft = f;
+            // spreading fused with the x pass exists only under the pruned plans
+            if (f == first.fft || !fft_plan_ok(*S, f) || (f == SD_FFT_FULL && c.bins == SPREAD_X)) continue;
+            if ((rc = trial(c)) != SD_OK) break;
         }
     }
     cudaEventDestroy(e0);
@@ -1079,7 +1120,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
         char key[256];
         snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d|%d|%d|%d", (const void*)fixed,
                  (const void*)moving, (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B,
-                 S.plan.bins, (int)S.pruned, ctx->opt_timing, S.k_r);
+                 S.plan.bins, S.plan.fft, ctx->opt_timing, S.k_r);
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
@@ -1143,9 +1184,9 @@ static int run_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pa
         CKI(search_setup<T>(ctx, J.fixed, J.moving, J.quats, J.n_r, &J.grid, J.cand_out, 0, st, &S[j]));
         if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) CKI(autotune<T>(ctx, &S[j], st));
         char part[256];
-        snprintf(part, sizeof part, "|%p,%p,%p,%lld,%d,%.17g,%p,%d,%d", (const void*)J.fixed, (const void*)J.moving,
-                 (const void*)J.quats, (long long)J.n_r, J.grid.N, J.grid.L, (void*)J.cand_out, S[j].plan.B,
-                 S[j].plan.bins);
+        snprintf(part, sizeof part, "|%p,%p,%p,%lld,%d,%.17g,%p,%d,%d,%d", (const void*)J.fixed,
+                 (const void*)J.moving, (const void*)J.quats, (long long)J.n_r, J.grid.N, J.grid.L,
+                 (void*)J.cand_out, S[j].plan.B, S[j].plan.bins, S[j].plan.fft);
         k += part;
     }
     char tail[64];
@@ -1223,6 +1264,7 @@ static int run_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pa
             stats[j].ms = ms;
             stats[j].batch = S[j].plan.B;
             stats[j].spread_bins = S[j].plan.bins;
+            stats[j].fft_plan = S[j].plan.fft;
             stats[j].n = S[j].G.n;
             stats[j].s = S[j].G.s;
         }
@@ -1323,6 +1365,10 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
+    else if (!strcmp(key, "fft_plan")) {
+        if (value < -1 || value > SD_FFT_PRUNED_NARROW) return fail(ctx, SD_ERR_ARG, "fft_plan: -1, 0, 1 or 2");
+        ctx->opt_fft_plan = (int)value;
+    }
     else if (!strcmp(key, "spread_fused")) ctx->opt_spread_fused = (int)value;
     else if (!strcmp(key, "spread_box")) ctx->opt_spread_box = (int)value;
     else if (!strcmp(key, "sdf_cull")) ctx->opt_sdf_cull = (int)value;
@@ -1559,8 +1605,8 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len) {
     bool first = true;
     for (const auto& kv : ctx->tuned) {
         char e[256];
-        snprintf(e, sizeof e, "%s{\"key\": \"%s\", \"batch\": %d, \"spread_bins\": %d}", first ? "" : ", ",
-                 kv.first.c_str(), kv.second.B, kv.second.bins);
+        snprintf(e, sizeof e, "%s{\"key\": \"%s\", \"batch\": %d, \"spread_bins\": %d, \"fft\": %d}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.B, kv.second.bins, kv.second.fft);
         js += e;
         first = false;
     }
@@ -1584,11 +1630,13 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         const char* q = strchr(p, '"');
         if (!q || q - p > 120) return fail(ctx, SD_ERR_ARG, "tune_import: malformed key");
         std::string key(p, (size_t)(q - p));
-        int B = 0, bins = -1;
-        if (sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d}", &B, &bins) != 2 || B < 1 || B > 64 ||
-            (bins != 0 && bins != SPREAD_X && bins != SPREAD_BOX && bins != 8 && bins != 12 && bins != 16))
+        int B = 0, bins = -1, fft = SD_FFT_PRUNED;
+        const int nf = sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d, \"fft\": %d}", &B, &bins, &fft);
+        if (nf < 2 || B < 1 || B > 64 ||
+            (bins != 0 && bins != SPREAD_X && bins != SPREAD_BOX && bins != 8 && bins != 12 && bins != 16) ||
+            fft < SD_FFT_FULL || fft > SD_FFT_PRUNED_NARROW)
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
-        got[key] = Plan{B, bins};
+        got[key] = Plan{B, bins, fft};
         p = q;
     }
     for (auto& kv : got) ctx->tuned[kv.first] = kv.second;
@@ -1596,7 +1644,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
 }
 
 int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_t n_r, int32_t* batch,
-                   int32_t* spread_bins) {
+                   int32_t* spread_bins, int32_t* fft_plan) {
     if (!ctx) return SD_ERR_ARG;
     if (!moving || moving->ctx != ctx) return fail(ctx, SD_ERR_ARG, "search_plan: bad moving shape");
     if (n_r < 1) return fail(ctx, SD_ERR_ARG, "search_plan: bad rotation count");
@@ -1608,7 +1656,9 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
         S.n_r = n_r;
         S.plan.B = choose_batch<T>(ctx, S.G, n_r);
         S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
-        S.pruned = ctx->opt_pruned && pruned_len_ok(S.G.n) && S.G.s <= S.G.N;
+        S.prunable = ctx->opt_pruned && pruned_len_ok(S.G.n) && S.G.s <= S.G.N;
+        S.narrowable = S.prunable && sizeof(T) == 4 && S.G.n >= 128;
+        S.plan.fft = fft_plan_default(ctx, S);
         if (ctx->opt_spread_box && bins_supported(ctx)) S.plan.bins = SPREAD_BOX;
         if (ctx->opt_spread_fused && spread_x_ok(ctx, S)) S.plan.bins = SPREAD_X;
         if (ctx->opt_autotune && !ctx->opt_plain && ctx->opt_batch <= 0) {
@@ -1616,10 +1666,12 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
             if (it != ctx->tuned.end()) {
                 S.plan.B = (int)std::min<int64_t>(it->second.B, n_r);
                 S.plan.bins = it->second.bins;
+                if (ctx->opt_fft_plan < 0 && fft_plan_ok(S, it->second.fft)) S.plan.fft = it->second.fft;
             }
         }
         if (batch) *batch = S.plan.B;
         if (spread_bins) *spread_bins = S.plan.bins;
+        if (fft_plan) *fft_plan = S.plan.fft;
         return SD_OK;
     };
     if (ctx->p.precision == SD_F64) return plan(double{});

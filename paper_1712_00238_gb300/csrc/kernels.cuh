@@ -162,6 +162,7 @@ struct ColArgs {
     const cplx<T>* twI;                 // twiddles of N (inverse)
     const cplx<T>* W;                   // COL_FUSED: N x ncols table
     int rot_fastest;                    // COL_FUSED: grid (batch, column blocks), W reused from L2
+    int narrow;                         // COL_FWD_P / COL_FUSED_P: half the columns per CTA
 };
 template <typename T> cudaError_t launch_cols(int mode, const ColArgs<T>& a, int batch, cudaStream_t st);
 

@@ -46,15 +46,20 @@ __host__ __device__ constexpr int lines_per_cta() {
 // warps, at least 64.  Wider than 384 butterflies (512-point lines) the CTA
 // keeps 256 threads with two butterflies each: registers would otherwise allow
 // only one CTA per SM.
-template <typename T, int LEN>
-__host__ __device__ constexpr int cta_threads() {
+template <int LEN>
+__host__ __device__ constexpr int cta_threads_for(int lines) {
     int most = 0;
     for (int s = 0; plan_radix(LEN, s) != 0; ++s) {
-        const int nb = lines_per_cta<T, LEN>() * (LEN / plan_radix(LEN, s));
+        const int nb = lines * (LEN / plan_radix(LEN, s));
         most = nb > most ? nb : most;
     }
     most = (most + 31) / 32 * 32;
     return most < 64 ? 64 : (most > 384 ? 256 : most);
+}
+
+template <typename T, int LEN>
+__host__ __device__ constexpr int cta_threads() {
+    return cta_threads_for<LEN>(lines_per_cta<T, LEN>());
 }
 
 // Resident CTAs per SM that a pass's register allocation is bounded for, 0 for
@@ -1216,12 +1221,12 @@ __global__ void __launch_bounds__(cta_threads<T, LEN>(), MB) k_rows_fwd_p(RowArg
     rows_fwd_p_body<T, LEN>(a);
 }
 
-// y pass (3D): columns (one per kept x mode) of each z plane -> N modes.
-template <typename T, int LEN>
+// y pass (3D): columns (one per kept x mode) of each z plane -> N modes, TC
+// columns per CTA.
+template <typename T, int LEN, int TC>
 __device__ __forceinline__ void cols_fwd_p_body(const ColArgs<T>& a) {
     using C = cplx<T>;
-    constexpr int TC = lines_per_cta<T, LEN>();
-    constexpr int NT = cta_threads<T, LEN>();
+    constexpr int NT = cta_threads_for<LEN>(TC);
     constexpr int LD = col_pitch(LEN);
     constexpr int NTW = tw_count(LEN);
     constexpr int NB1 = LEN / plan_radix(LEN, 0);
@@ -1247,19 +1252,19 @@ __device__ __forceinline__ void cols_fwd_p_body(const ColArgs<T>& a) {
     fftp_lines<C, LEN, false, TC, NT, LAY_COL, false, false, true>(buf, LD, tw, load, emit);
 }
 
-template <typename T, int LEN, int MB>
-__global__ void __launch_bounds__(cta_threads<T, LEN>(), MB) k_cols_fwd_p(ColArgs<T> a) {
-    cols_fwd_p_body<T, LEN>(a);
+template <typename T, int LEN, int MB, int TC>
+__global__ void __launch_bounds__(cta_threads_for<LEN>(TC), MB) k_cols_fwd_p(ColArgs<T> a) {
+    cols_fwd_p_body<T, LEN, TC>(a);
 }
 
 // Last axis: pruned forward FFT of length LENF, times the shifted product table
-// W' (N x ncols), inverse FFT of length LENF/2 in the same block.
-template <typename T, int LENF>
+// W' (N x ncols), inverse FFT of length LENF/2 in the same block; TC columns
+// per CTA.
+template <typename T, int LENF, int TC>
 __device__ __forceinline__ void cols_fused_p_body(const ColArgs<T>& a) {
     using C = cplx<T>;
     constexpr int LENI = LENF / 2;
-    constexpr int TC = lines_per_cta<T, LENF>();
-    constexpr int NT = cta_threads<T, LENF>();
+    constexpr int NT = cta_threads_for<LENF>(TC);
     constexpr int LD = col_pitch(LENF);
     constexpr int NTWF = tw_count(LENF);
     constexpr int NTWI = tw_count(LENI);
@@ -1300,9 +1305,9 @@ __device__ __forceinline__ void cols_fused_p_body(const ColArgs<T>& a) {
     fftp_lines<C, LENI, true, TC, NT, LAY_COL, false, true, false>(buf, LD, twI, load, emit_out);
 }
 
-template <typename T, int LENF, int MB>
-__global__ void __launch_bounds__(cta_threads<T, LENF>(), MB) k_cols_fused_p(ColArgs<T> a) {
-    cols_fused_p_body<T, LENF>(a);
+template <typename T, int LENF, int MB, int TC>
+__global__ void __launch_bounds__(cta_threads_for<LENF>(TC), MB) k_cols_fused_p(ColArgs<T> a) {
+    cols_fused_p_body<T, LENF, TC>(a);
 }
 
 // Inverse y (3D), in place: columns of N points, full input and output.  Each
@@ -1436,6 +1441,23 @@ __host__ __device__ constexpr int pruned_min_ctas() {
     return sizeof(T) != 4 ? 0 : (LEN == 512 ? 2 : (LEN == 384 ? 3 : 0));
 }
 
+// The narrow plan of the pruned column passes (forward y and the fused last
+// axis): half the columns per CTA, so twice the CTAs of half the shared memory,
+// for FP32 lines of 128 points and more.  Its register bound keeps the
+// per-thread cap of the standard plan.
+template <typename T, int LEN>
+__host__ __device__ constexpr bool narrow_cols_ok() {
+    return sizeof(T) == 4 && LEN >= 128;
+}
+template <typename T, int LEN>
+__host__ __device__ constexpr int narrow_lines() {
+    return lines_per_cta<T, LEN>() / 2;
+}
+template <typename T, int LEN, int KIND>
+__host__ __device__ constexpr int narrow_min_ctas() {
+    return pruned_min_ctas<T, LEN, KIND>() * cta_threads<T, LEN>() / cta_threads_for<LEN>(narrow_lines<T, LEN>());
+}
+
 // W' = W exp(2 pi i s_h (kx + ky [+ kz]) / n) with kappa signed (modes at kappa mod N).
 template <typename T>
 __global__ void k_wshift(const cplx<T>* W, int N, int dim, int n, int s_h, cplx<T>* out) {
@@ -1539,40 +1561,56 @@ static cudaError_t rows_fwd_p_impl(const RowArgs<T>& a, int batch, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <typename T, int LEN>
-static cudaError_t cols_fwd_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+template <typename T, int LEN, int TC, int MB>
+static cudaError_t cols_fwd_p_launch(const ColArgs<T>& a, int batch, cudaStream_t st) {
     using C = cplx<T>;
-    static_assert(prunable_len(LEN), "length not prunable");
-    constexpr int TC = lines_per_cta<T, LEN>();
     const int nb = (a.ncols + TC - 1) / TC;
     if (nb == 0 || batch == 0 || a.nouter == 0) return cudaSuccess;
     const size_t smem = (size_t)(TC * col_pitch(LEN) + tw_count(LEN)) * sizeof(C);
-    auto kern = k_cols_fwd_p<T, LEN, pruned_min_ctas<T, LEN, 1>()>;
+    auto kern = k_cols_fwd_p<T, LEN, MB, TC>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(nb, a.nouter, batch), cta_threads<T, LEN>(), smem, st>>>(a);
+    kern<<<dim3(nb, a.nouter, batch), cta_threads_for<LEN>(TC), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int LEN>
+static cudaError_t cols_fwd_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    static_assert(prunable_len(LEN), "length not prunable");
+    if constexpr (narrow_cols_ok<T, LEN>())
+        if (a.narrow)
+            return cols_fwd_p_launch<T, LEN, narrow_lines<T, LEN>(), narrow_min_ctas<T, LEN, 1>()>(a, batch, st);
+    if (a.narrow) return cudaErrorInvalidValue;
+    return cols_fwd_p_launch<T, LEN, lines_per_cta<T, LEN>(), pruned_min_ctas<T, LEN, 1>()>(a, batch, st);
+}
+
+template <typename T, int LENF, int TC, int MB>
+static cudaError_t cols_fused_p_launch(const ColArgs<T>& a, int batch, cudaStream_t st) {
+    using C = cplx<T>;
+    const int nb = (a.ncols + TC - 1) / TC;
+    if (nb == 0 || batch == 0) return cudaSuccess;
+    if (a.nouter != 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(TC * col_pitch(LENF) + tw_count(LENF) + tw_count(LENF / 2)) * sizeof(C);
+    auto kern = k_cols_fused_p<T, LENF, MB, TC>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const bool rf = a.rot_fastest;
+    if (rf && nb > 65535) return cudaErrorInvalidValue;
+    const dim3 grid = rf ? dim3(batch, nb, 1) : dim3(nb, 1, batch);
+    kern<<<grid, cta_threads_for<LENF>(TC), smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename T, int LENF>
 static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
-    using C = cplx<T>;
     static_assert(prunable_len(LENF), "length not prunable");
-    constexpr int TC = lines_per_cta<T, LENF>();
-    const int nb = (a.ncols + TC - 1) / TC;
-    if (nb == 0 || batch == 0) return cudaSuccess;
-    if (a.nouter != 1) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(TC * col_pitch(LENF) + tw_count(LENF) + tw_count(LENF / 2)) * sizeof(C);
-    auto kern = k_cols_fused_p<T, LENF, pruned_min_ctas<T, LENF, 2>()>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    const bool rf = a.rot_fastest;
-    if (rf && nb > 65535) return cudaErrorInvalidValue;
-    const dim3 grid = rf ? dim3(batch, nb, 1) : dim3(nb, 1, batch);
-    kern<<<grid, cta_threads<T, LENF>(), smem, st>>>(a);
-    note_launch();
-    return cudaGetLastError();
+    if constexpr (narrow_cols_ok<T, LENF>())
+        if (a.narrow)
+            return cols_fused_p_launch<T, LENF, narrow_lines<T, LENF>(), narrow_min_ctas<T, LENF, 2>()>(a, batch, st);
+    if (a.narrow) return cudaErrorInvalidValue;
+    return cols_fused_p_launch<T, LENF, lines_per_cta<T, LENF>(), pruned_min_ctas<T, LENF, 2>()>(a, batch, st);
 }
 
 template <typename T, int LEN, int MODE>

@@ -73,7 +73,7 @@ class sd_pair_job(ct.Structure):
 
 class sd_pair_stat(ct.Structure):
     _fields_ = [("ms", ct.c_double), ("batch", ct.c_int32), ("spread_bins", ct.c_int32), ("n", ct.c_int32),
-                ("s", ct.c_int32)]
+                ("s", ct.c_int32), ("fft_plan", ct.c_int32)]
 
 
 class sd_refine_params(ct.Structure):
@@ -107,7 +107,7 @@ _SIGS = {
     "sd_score_pairs": (ct.c_int, [ct.c_void_p, ct.POINTER(sd_pair_job), ct.c_int64, ct.POINTER(sd_pair_stat),
                                   ct.c_void_p]),
     "sd_search_plan": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(sd_grid), ct.c_int64,
-                                  ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+                                  ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
     "sd_tune_export": (ct.c_int, [ct.c_void_p, ct.c_char_p, ct.c_int64, ct.POINTER(ct.c_int64)]),
     "sd_tune_import": (ct.c_int, [ct.c_void_p, ct.c_char_p]),
     "sd_top_k_poses": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_int, ct.c_void_p,
@@ -368,12 +368,13 @@ class Context:
         self._check(self.lib.sd_tune_import(self.handle, text.encode()))
 
     def search_plan(self, moving: Shape, grid: Grid, n_r: int) -> dict:
-        """The plan a search would use now: rotations per batch and binned (1) or direct spreading."""
-        b, s = ct.c_int32(), ct.c_int32()
+        """The plan a search would use now: rotations per batch, the spreading variant
+        (spread_bins, as sd_search_plan) and the forward-pass FFT plan (FFT_PLANS index)."""
+        b, s, f = ct.c_int32(), ct.c_int32(), ct.c_int32()
         g = grid.c()
         self._check(self.lib.sd_search_plan(self.handle, moving.handle, ct.byref(g), n_r, ct.byref(b),
-                                            ct.byref(s)))
-        return {"batch": b.value, "spread_bins": s.value}
+                                            ct.byref(s), ct.byref(f)))
+        return {"batch": b.value, "spread_bins": s.value, "fft_plan": f.value}
 
     def score_pairs(self, jobs, outs: list | None = None, stats: bool = True):
         """Score many (fixed, moving, quats, grid) jobs in one launch sequence (a captured
@@ -397,7 +398,8 @@ class Context:
         self._check(self.lib.sd_score_pairs(self.handle, arr, n, st, _stream(self.device)))
         if not stats:
             return outs, None
-        return outs, [dict(ms=x.ms, batch=x.batch, spread_bins=x.spread_bins, n=x.n, s=x.s) for x in st]
+        return outs, [dict(ms=x.ms, batch=x.batch, spread_bins=x.spread_bins, n=x.n, s=x.s,
+                           fft_plan=x.fft_plan) for x in st]
 
     def top_k_poses(self, cand: torch.Tensor, k: int, fixed: Shape = None, moving: Shape = None,
                     quats: torch.Tensor = None, grid: Grid = None, rescore_fp64: bool = True) -> list[dict]:

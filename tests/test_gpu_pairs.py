@@ -123,6 +123,7 @@ def test_tuned_plans_export_and_import():
     table = json.loads(text)
     assert table["sdfdock_plans"] == 1 and len(table["plans"]) == 1
     assert table["plans"][0]["batch"] >= 1 and table["plans"][0]["spread_bins"] in (0, 1, 2, 8, 12, 16)
+    assert table["plans"][0]["fft"] == plan["fft_plan"] and plan["fft_plan"] in (0, 1, 2)
 
     ctx2 = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
     fx2, mv2, _, _, _ = _jobs(ctx2)[2]
@@ -132,11 +133,15 @@ def test_tuned_plans_export_and_import():
     assert ctx2.search_plan(mv2, g, qd.shape[0]) == plan
     assert json.loads(ctx2.tune_export()) == table
     # malformed tables are refused and leave the cache as it was
-    for bad in ("{}", re.sub(r'"batch": \d+', '"batch": 0', text), re.sub(r'"spread_bins": \d+', '"spread_bins": 7', text)):
+    for bad in ("{}", re.sub(r'"batch": \d+', '"batch": 0', text), re.sub(r'"spread_bins": \d+', '"spread_bins": 7', text),
+                re.sub(r'"fft": \d+', '"fft": 3', text)):
         with pytest.raises(sd.SdError) as e:
             ctx2.tune_import(bad)
         assert e.value.code == sd.SD_ERR_ARG
     assert json.loads(ctx2.tune_export()) == table
     assert isinstance(before["batch"], int)
+    # a table without the FFT plan (older exports) takes the pruned plan
+    ctx2.tune_import(re.sub(r', "fft": \d+', '', text))
+    assert ctx2.search_plan(mv2, g, qd.shape[0])["fft_plan"] in (1, plan["fft_plan"])
     ctx.close()
     ctx2.close()

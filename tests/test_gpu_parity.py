@@ -215,9 +215,11 @@ def _sub_box(radius, N, L, w):
 def test_pruned_and_full_forward_passes_agree(name, prec, N):
     # The pruned forward passes read the sub-box unshifted and compute only the
     # kept modes, applying the shift as a phase in the product table; the full
-    # passes read the shifted sub-box and compute every mode.  Same maps, and
-    # both equal the oracle's.  (tiny_3d at N = 48 has s = N exactly, the largest
-    # sub-box the pruned path takes; n = 96 ends with radix 12, n = 64 / 128 with 8.)
+    # passes read the shifted sub-box and compute every mode; the narrow plan is
+    # the pruned one with half the columns per CTA (FP32, n >= 128).  Same maps,
+    # and all equal the oracle's.  (tiny_3d at N = 48 has s = N exactly, the
+    # largest sub-box the pruned path takes; n = 96 ends with radix 12, n = 64 /
+    # 128 with 8.)
     w = getattr(configs, name)()
     p1, c1, p2, c2 = oracle_weights(name)
     s = _sub_box(float(np.linalg.norm(p2, axis=1).max()), N, w.L, w.w)
@@ -227,13 +229,18 @@ def test_pruned_and_full_forward_passes_agree(name, prec, N):
     mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
     q = quats_dev(w.quats)
     g = grid_of(w, N)
+    narrow = prec == "f32" and 2 * N >= 128
     got = {}
-    for pruned in (1, 0):
-        ctx.set_option("pruned", pruned)
-        got[pruned] = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    for plan in (1, 0, 2):
+        ctx.set_option("fft_plan", plan)
+        # a plan that does not apply falls back to the pruned default
+        assert ctx.search_plan(mv, g, w.n_rot)["fft_plan"] == (plan if plan != 2 or narrow else 1)
+        got[plan] = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+    ctx.set_option("fft_plan", -1)
     ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
     for r in range(w.n_rot):
         assert rel_err(got[1][r], got[0][r]) < (1e-12 if prec == "f64" else 2e-6), r
+        assert rel_err(got[2][r], got[1][r]) < (1e-12 if prec == "f64" else 2e-6), r
         assert rel_err(got[1][r], ref[r]) < TOL[prec], r
     ctx.close()
 
