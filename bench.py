@@ -64,14 +64,16 @@ def parse_args():
     ap.add_argument("--plain", type=int, default=0, help="one rotation per launch sequence, no graph")
     ap.add_argument("--spread-direct", type=int, default=1,
                     help="with --autotune 0: 1 global vector atomics, 0 spread by bins")
+    ap.add_argument("--spread-bin-side", type=int, default=16, choices=[8, 12, 16],
+                    help="with --autotune 0 --spread-direct 0: the bin side of binned spreading")
     ap.add_argument("--spread-fused", type=int, default=0,
                     help="with --autotune 0: 1 spreads straight into rows held in shared memory and runs the "
                          "forward x transform there (3D FP32)")
     ap.add_argument("--spread-box", type=int, default=0,
                     help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
-    ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2],
+    ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="forward-pass FFT plan: -1 the autotuner's (or the pruned default), 0 full, 1 pruned, "
-                         "2 pruned with narrow column CTAs")
+                         "2 pruned with narrow column CTAs, 3 pruned with wide column CTAs")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library times candidate plans (batch, spreading, FFT plan) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
@@ -261,6 +263,7 @@ def run_ours(args):
     ctx.set_option("spread_direct", args.spread_direct)
     ctx.set_option("spread_fused", args.spread_fused)
     ctx.set_option("spread_box", args.spread_box)
+    ctx.set_option("spread_bin_side", args.spread_bin_side)
     ctx.set_option("fft_plan", args.fft_plan)
     ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
@@ -493,11 +496,12 @@ def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
 # sub-box side, N, rotations per launch); a launch of another shape reports
 # null.  Docking pair: one 20-rotation launch of the pruned fused pass, whose
 # product table is read from DRAM once per launch (its other rotations hit L2).
-# the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW)
+# the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE)
 FFT_PLAN_TEXT = {
     0: "full: shifted sub-box padded to n, every output of each line",
     1: "pruned: zero upper half skipped, only the N kept modes; shift as a phase in W",
     2: "pruned, half the columns per CTA in the forward y and fused z passes",
+    3: "pruned, twice the columns per CTA in the forward y and fused z passes",
 }
 
 TRAFFIC_PER_LAUNCH: dict = {

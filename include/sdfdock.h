@@ -135,12 +135,14 @@ const char* sd_last_error(const sd_ctx* ctx);
  * graph), "timing" (1: CUDA-event timing of every pass, see sd_pass_times),
  * "spread_direct" (1, the default: spread with global vector atomics per kernel
  * row; 0: sort the samples into 16^d-cell bins and accumulate each bin's taps in
- * shared memory first), "pruned" (1, the default: the forward FFT passes of the
+ * shared memory first), "spread_bin_side" (8, 12 or 16, default 16: the bin
+ * side of binned spreading when the autotuner does not choose it), "pruned"
+ * (1, the default: the forward FFT passes of the
  * search read the spread sub-box unshifted and compute only the kept modes, with
  * the shift applied as a phase in the product table; 0: the shifted sub-box and
  * every mode; results are the same up to FP rounding), "fft_plan" (-1, the
  * default: the autotuner's choice, else SD_FFT_PRUNED where the pruned passes
- * apply; 0..2: that SD_FFT_* plan wherever it applies, never tuned),
+ * apply; 0..3: that SD_FFT_* plan wherever it applies, never tuned),
  * "spread_box" (1: each
  * CTA spreads a block of Morton-consecutive samples into a shared box of the
  * sub-box and adds the box's nonzero cells with 16-byte atomics; FP32, w 4-7;
@@ -325,10 +327,13 @@ int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair
  *                         compute only the N kept modes; the sub-box shift is a
  *                         phase folded into the product table
  *   SD_FFT_PRUNED_NARROW  as PRUNED, with half the columns per CTA in the
- *                         forward y and fused last-axis passes (FP32, n >= 128) */
+ *                         forward y and fused last-axis passes (FP32, n 128..384)
+ *   SD_FFT_PRUNED_WIDE    as PRUNED, with twice the columns per CTA there
+ *                         (FP32, n 128..384) */
 #define SD_FFT_FULL 0
 #define SD_FFT_PRUNED 1
 #define SD_FFT_PRUNED_NARROW 2
+#define SD_FFT_PRUNED_WIDE 3
 
 /* The plan a search of n_r rotations of `moving` on grid g would run with now:
  * rotations per batch, the bin side of binned spreading (0: direct; 1:
@@ -352,7 +357,7 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
  * geometries skip the timing trials (an entry without "fft" takes
  * SD_FFT_PRUNED; a plan that does not apply to a job is replaced by the job's
  * default there).  A text that is not such a table, or an entry with batch
- * outside [1, 64], spread_bins not 0, 1, 2, 8, 12 or 16, or fft not 0, 1 or 2,
+ * outside [1, 64], spread_bins not 0, 1, 2, 8, 12 or 16, or fft not 0 to 3,
  * is SD_ERR_ARG and leaves the cache unchanged. */
 int sd_tune_import(sd_ctx* ctx, const char* json);
 
@@ -466,18 +471,23 @@ int sd_host_line_fft(int len, int inverse, const double* in, double* out);
 
 /* Probe of an arithmetic rate of this GPU, for the rooflines of the kernels
  * bound by arithmetic rather than memory (the SDF sums: FP32 FMA and the
- * special-function unit; the FP64 re-score: FP64 FMA).  The paper has no
- * counterpart.  Runs a probe kernel (eight independent dependency chains per
- * thread, eight CTAs of 256 threads per SM) on `device` for a few to tens of
- * milliseconds, synchronously on the legacy default stream, and stores the best
- * of three timed launches in *ops_per_s: floating-point operations per second
- * for the FMA kinds (two per FMA), instructions per second for the others.
- * Allocates 4 bytes of device memory for the duration of the call.  SD_ERR_ARG
- * for an unknown kind or device, SD_ERR_CUDA if a CUDA call fails. */
+ * special-function unit; the FP64 re-score: FP64 FMA) or by shared-memory
+ * atomics (the spreading tiles).  The paper has no counterpart.  Runs a probe
+ * kernel (eight independent dependency chains per thread, or for the atomic
+ * kinds each lane adding to its own shared word, so that the lanes of a warp
+ * hit distinct banks; eight CTAs of 256 threads per SM) on `device` for a few
+ * to tens of milliseconds, synchronously on the legacy default stream, and
+ * stores the best of three timed launches in *ops_per_s: floating-point
+ * operations per second for the FMA kinds (two per FMA), instructions (atomic
+ * adds) per second for the others.  Allocates 4 bytes of device memory for the
+ * duration of the call.  SD_ERR_ARG for an unknown kind or device, SD_ERR_CUDA
+ * if a CUDA call fails. */
 #define SD_PEAK_FP32_FMA 0
 #define SD_PEAK_FP64_FMA 1
-#define SD_PEAK_SFU_EX2 2   /* ex2.approx.f32 (the exponential's special-function step) */
-#define SD_PEAK_SFU_RSQRT 3 /* rsqrt.approx.f32 */
+#define SD_PEAK_SFU_EX2 2    /* ex2.approx.f32 (the exponential's special-function step) */
+#define SD_PEAK_SFU_RSQRT 3  /* rsqrt.approx.f32 */
+#define SD_PEAK_SHARED_ADD32 4 /* 32-bit integer atomic add to shared memory */
+#define SD_PEAK_SHARED_ADD64 5 /* 64-bit integer atomic add to shared memory */
 int sd_alu_peak(int device, int kind, double* ops_per_s);
 
 /* Library version string (static storage). */

@@ -53,12 +53,15 @@ struct GraphEntry {
     long long kernels = 0;            // kernel launches captured (counted again at every replay)
 };
 
+// Bin side of binned spreading when it is asked for without the autotuner.
+constexpr int DEFAULT_BIN = 16;
+
 struct Plan {      // launch plan of one scoring job
     int B = 1;     // rotations per launch sequence
     int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct,
                    // 1: spreading fused with the forward x transform (SPREAD_X),
                    // 2: shared boxes of sample blocks (SPREAD_BOX)
-    int fft = SD_FFT_PRUNED;  // forward-pass plan (SD_FFT_FULL / _PRUNED / _PRUNED_NARROW)
+    int fft = SD_FFT_PRUNED;  // forward-pass plan (SD_FFT_FULL / _PRUNED / _PRUNED_NARROW / _PRUNED_WIDE)
 };
 
 struct sd_ctx {
@@ -77,6 +80,7 @@ struct sd_ctx {
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_fft_plan = -1;      // >= 0: this SD_FFT_* plan wherever it applies (not tuned)
+    int opt_bin_side = DEFAULT_BIN;  // bin side of binned spreading when it is not tuned
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
     int opt_sdf_cull = 2;       // 0: SDF sums over every boundary tile; 1: skip far tiles; 2: and far sub-tiles per warp
@@ -449,9 +453,9 @@ static cudaError_t pass_x_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
 // y pass (3D): (s,s,N) -> (s,N,N)
 template <typename T>
 static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs, cplx<T>* out,
-                              int64_t out_rs, int batch, cudaStream_t st, int mode = COL_FWD, int narrow = 0) {
+                              int64_t out_rs, int batch, cudaStream_t st, int mode = COL_FWD, int lines = LINES_STD) {
     ColArgs<T> c{};
-    c.narrow = narrow;
+    c.lines = lines;
     c.in = in;
     c.out = out;
     c.in_rot_stride = in_rs;
@@ -473,9 +477,9 @@ static cudaError_t pass_y_fwd(const Geo& G, const Tw<T>& tw, const cplx<T>* in, 
 template <typename T>
 static cudaError_t pass_last(int mode, const Geo& G, const Tw<T>& tw, const cplx<T>* in, int64_t in_rs,
                              cplx<T>* out, int64_t out_rs, const cplx<T>* W, int batch, cudaStream_t st,
-                             int narrow = 0) {
+                             int lines = LINES_STD) {
     ColArgs<T> c{};
-    c.narrow = narrow;
+    c.lines = lines;
     c.in = in;
     c.out = out;
     c.in_rot_stride = in_rs;
@@ -554,8 +558,6 @@ static int bins_for(sd_ctx* ctx, int s, int dim, int64_t m, int batch, int tb, B
     return SD_OK;
 }
 
-// Bin side of binned spreading when it is asked for without the autotuner.
-constexpr int DEFAULT_BIN = 16;
 // Plan.bins value of spreading fused with the forward x transform.
 constexpr int SPREAD_X = 1;
 // Plan.bins value of spreading by blocks of Morton-consecutive samples.
@@ -794,7 +796,7 @@ struct Search {
     int maps = 0;
     Plan plan{};
     bool prunable = false;          // pruned forward passes apply (sub-box in the low half of a line)
-    bool narrowable = false;        // and their narrow column plan exists (FP32, n >= 128)
+    bool alt_cols = false;          // and their narrow / wide column plans exist (FP32, n 128..384)
     const cplx<T>* Wsh = nullptr;   // the shifted table W' of the pruned passes
     int k_r = 1;          // candidates per rotation (argmax output)
     int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
@@ -817,7 +819,7 @@ static bool spread_x_ok(const sd_ctx* ctx, const Search<T>& S) {
 template <typename T>
 static bool fft_plan_ok(const Search<T>& S, int fft) {
     return fft == SD_FFT_FULL || (fft == SD_FFT_PRUNED && S.prunable) ||
-           (fft == SD_FFT_PRUNED_NARROW && S.narrowable);
+           ((fft == SD_FFT_PRUNED_NARROW || fft == SD_FFT_PRUNED_WIDE) && S.alt_cols);
 }
 
 // The plan a job starts from: the forced one if it applies, else pruned where
@@ -844,13 +846,13 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
     S->out = out;
     S->maps = maps;
     S->plan.B = choose_batch<T>(ctx, S->G, n_r);
-    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
+    S->plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? ctx->opt_bin_side : 0;
     per_rot_elems<T>(S->G, &S->e0, &S->e1);
     S->rows_last = (S->G.dim == 2) ? S->G.N : (int64_t)S->G.N * S->G.N;
     S->Nd = (S->G.dim == 2) ? (int64_t)S->G.N * S->G.N : (int64_t)S->G.N * S->G.N * S->G.N;
     // pruned forward passes: the sub-box must fit in the low half of a line
     S->prunable = ctx->opt_pruned && pruned_len_ok(S->G.n) && S->G.s <= S->G.N;
-    S->narrowable = S->prunable && sizeof(T) == 4 && S->G.n >= 128;
+    S->alt_cols = S->prunable && sizeof(T) == 4 && S->G.n >= 128 && S->G.n <= 384;
     if (S->prunable) {
         void* ws = nullptr;
         for (auto& w : prep->Wsh)
@@ -933,7 +935,8 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         sa.out_rot_stride = S.e0;
         sa.n_full = G.n;
         const bool pruned = S.plan.fft != SD_FFT_FULL;
-        const int narrow = S.plan.fft == SD_FFT_PRUNED_NARROW;
+        const int lines = S.plan.fft == SD_FFT_PRUNED_NARROW ? LINES_NARROW
+                          : (S.plan.fft == SD_FFT_PRUNED_WIDE ? LINES_WIDE : LINES_STD);
         const int mx = pruned ? ROW_FWD_P : ROW_FWD;
         const int my = pruned ? COL_FWD_P : COL_FWD;
         const int mf = pruned ? COL_FUSED_P : COL_FUSED;
@@ -957,11 +960,11 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         if (G.dim == 3) {
             {
                 PassTimer pt(ctx, SD_PASS_FWD_Y, s, timed);
-                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s, my, narrow));
+                CK(ctx, pass_y_fwd<T>(G, S.tw, S.b1, S.e1, S.b0, S.e0, b, s, my, lines));
             }
             {
                 PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, narrow));
+                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, lines));
             }
             {
                 PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
@@ -971,7 +974,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             fin_rs = S.e1;
         } else {
             PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, Wp, b, s, narrow));
+            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, Wp, b, s, lines));
             fin = S.b0;
             fin_rs = S.e0;
         }
@@ -1086,7 +1089,7 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
         if ((rc = trial(c)) != SD_OK) break;
     if (rc == SD_OK && ctx->opt_fft_plan < 0) {
         const Plan first = best;
-        for (int f : {SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_FULL}) {
+        for (int f : {SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE, SD_FFT_FULL}) {
             Plan c = first;
             c.fft = f;
             // spreading fused with the x pass exists only under the pruned plans
@@ -1365,8 +1368,11 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
-    else if (!strcmp(key, "fft_plan")) {
-        if (value < -1 || value > SD_FFT_PRUNED_NARROW) return fail(ctx, SD_ERR_ARG, "fft_plan: -1, 0, 1 or 2");
+    else if (!strcmp(key, "spread_bin_side")) {
+        if (value != 8 && value != 12 && value != 16) return fail(ctx, SD_ERR_ARG, "spread_bin_side: 8, 12 or 16");
+        ctx->opt_bin_side = (int)value;
+    } else if (!strcmp(key, "fft_plan")) {
+        if (value < -1 || value > SD_FFT_PRUNED_WIDE) return fail(ctx, SD_ERR_ARG, "fft_plan: -1 to 3");
         ctx->opt_fft_plan = (int)value;
     }
     else if (!strcmp(key, "spread_fused")) ctx->opt_spread_fused = (int)value;
@@ -1634,7 +1640,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         const int nf = sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d, \"fft\": %d}", &B, &bins, &fft);
         if (nf < 2 || B < 1 || B > 64 ||
             (bins != 0 && bins != SPREAD_X && bins != SPREAD_BOX && bins != 8 && bins != 12 && bins != 16) ||
-            fft < SD_FFT_FULL || fft > SD_FFT_PRUNED_NARROW)
+            fft < SD_FFT_FULL || fft > SD_FFT_PRUNED_WIDE)
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
         got[key] = Plan{B, bins, fft};
         p = q;
@@ -1655,9 +1661,9 @@ int sd_search_plan(sd_ctx* ctx, const sd_shape* moving, const sd_grid* g, int64_
         S.moving = moving;
         S.n_r = n_r;
         S.plan.B = choose_batch<T>(ctx, S.G, n_r);
-        S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? DEFAULT_BIN : 0;
+        S.plan.bins = (!ctx->opt_spread_direct && bins_supported(ctx)) ? ctx->opt_bin_side : 0;
         S.prunable = ctx->opt_pruned && pruned_len_ok(S.G.n) && S.G.s <= S.G.N;
-        S.narrowable = S.prunable && sizeof(T) == 4 && S.G.n >= 128;
+        S.alt_cols = S.prunable && sizeof(T) == 4 && S.G.n >= 128 && S.G.n <= 384;
         S.plan.fft = fft_plan_default(ctx, S);
         if (ctx->opt_spread_box && bins_supported(ctx)) S.plan.bins = SPREAD_BOX;
         if (ctx->opt_spread_fused && spread_x_ok(ctx, S)) S.plan.bins = SPREAD_X;

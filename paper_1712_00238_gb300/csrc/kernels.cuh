@@ -162,8 +162,9 @@ struct ColArgs {
     const cplx<T>* twI;                 // twiddles of N (inverse)
     const cplx<T>* W;                   // COL_FUSED: N x ncols table
     int rot_fastest;                    // COL_FUSED: grid (batch, column blocks), W reused from L2
-    int narrow;                         // COL_FWD_P / COL_FUSED_P: half the columns per CTA
+    int lines;                          // COL_FWD_P / COL_FUSED_P: columns per CTA (LINES_*)
 };
+enum { LINES_STD = 0, LINES_NARROW = 1, LINES_WIDE = 2 };  // standard, half, twice
 template <typename T> cudaError_t launch_cols(int mode, const ColArgs<T>& a, int batch, cudaStream_t st);
 
 // twiddles exp(-2 pi i j / len), computed in FP64

@@ -324,12 +324,34 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t m, BinArgs bn) {
     bn.sorted[(int64_t)b * m + pos] = (int32_t)j;
 }
 
+// Pitches (y, z) of the tile kernel's shared planes, PS = TB + W - 1 cells a
+// side.  Lanes take the taps of a sample whose offsets kx + PY ky + PZ kz are
+// distinct mod 32, so each atomic instruction touches 32 distinct banks; these
+// pitches (the smallest, up to 15 % more cells than dense, found by exhaustive
+// search over PY mod 32 and PZ mod 32) let every W^D tap box be covered in the
+// minimum ceil(W^D / 32) such rounds, each round's taps lying on rows whose
+// staged products c wy wz are read in one shared wavefront.
+__host__ __device__ constexpr int tile_pitch(int D, int W, int TB, int axis) {
+    // {PY, PZ} per (W, TB); 2D uses PY only
+    constexpr int p2[4][3] = {{12, 18, 19}, {13, 19, 26}, {13, 18, 21}, {14, 18, 23}};
+    constexpr int p3[4][3][2] = {{{12, 136}, {16, 244}, {20, 392}},
+                                 {{13, 165}, {19, 311}, {23, 461}},
+                                 {{13, 169}, {18, 314}, {23, 486}},
+                                 {{14, 199}, {18, 327}, {23, 510}}};
+    const int wi = W - 4, ti = TB == 8 ? 0 : (TB == 12 ? 1 : 2);
+    return D == 2 ? (axis == 0 ? p2[wi][ti] : 0) : p3[wi][ti][axis];
+}
+
 // Shared-memory layout of the tile kernel: two fixed-point planes of the tile
 // (real, imaginary), then the staged sample records.
 template <int D, int W, int TB>
 struct TileShape {
+    static_assert(W >= 4 && W <= 7 && (TB == 8 || TB == 12 || TB == 16), "tile shape not tabulated");
     static constexpr int PS = TB + W - 1;                         // tile side
-    static constexpr int CELLS = (D == 3) ? PS * PS * PS : PS * PS;
+    static constexpr int PY = tile_pitch(D, W, TB, 0);            // y pitch of the planes
+    static constexpr int PZ = tile_pitch(D, W, TB, 1);            // z pitch (3D)
+    static_assert(PY >= PS && (D == 2 || PZ >= PY * PS), "pitch below the tile side");
+    static constexpr int CELLS = (D == 3) ? PZ * PS : PY * PS;
     static constexpr int ROWS = (D == 3) ? W * W : W;             // (ky, kz) rows of a tap box
     static constexpr int TAPS = ROWS * W;
     static constexpr int CHUNK = 64;                              // samples staged at a time
@@ -337,7 +359,43 @@ struct TileShape {
     static constexpr int O_C = 3 * W, O_BASE = 3 * W + 2, O_ORG = 3 * W + 3, O_ROW = (3 * W + 4 + 1) & ~1;
     static constexpr int REC = (O_ROW + 2 * ROWS + 1) & ~1;
     static constexpr size_t smem = (size_t)2 * CELLS * sizeof(int) + (size_t)CHUNK * REC * sizeof(float);
+    static constexpr int offset(int tap) {
+        return tap % W + PY * ((tap / W) % W) + (D == 3 ? PZ * (tap / (W * W)) : 0);
+    }
+    // rounds: the most taps whose offsets share a residue mod 32
+    static constexpr int rounds() {
+        int most = 0;
+        for (int r = 0; r < 32; ++r) {
+            int n = 0;
+            for (int t = 0; t < TAPS; ++t) n += (offset(t) & 31) == r;
+            most = n > most ? n : most;
+        }
+        return most;
+    }
+    static constexpr int ROUNDS = rounds();
+    static_assert(ROUNDS == (TAPS + 31) / 32, "pitches leave a bank conflict");
 };
+
+// The tap of each (round, lane) of the tile kernel, -1 for an idle lane: the
+// q-th tap (in tap order) whose offset is congruent to the lane mod 32.
+template <int D, int W, int TB>
+struct TapRounds {
+    short tap[TileShape<D, W, TB>::ROUNDS * 32];
+};
+template <int D, int W, int TB>
+constexpr TapRounds<D, W, TB> make_tap_rounds() {
+    using TS = TileShape<D, W, TB>;
+    TapRounds<D, W, TB> t{};
+    for (int i = 0; i < TS::ROUNDS * 32; ++i) t.tap[i] = -1;
+    int used[32] = {};
+    for (int k = 0; k < TS::TAPS; ++k) {
+        const int r = TS::offset(k) & 31;
+        t.tap[used[r]++ * 32 + r] = (short)k;
+    }
+    return t;
+}
+template <int D, int W, int TB>
+__device__ const TapRounds<D, W, TB> kTapRounds = make_tap_rounds<D, W, TB>();
 
 // One CTA per (bin, rotation).  The CTA stages CHUNK of the bin's samples at a
 // time: one thread per sample evaluates its kernel weights and tile offset, then
@@ -356,8 +414,8 @@ struct TileShape {
 template <int D, int W, int TB>
 __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
     using TS = TileShape<D, W, TB>;
-    constexpr int PS = TS::PS, PS2 = PS * PS, CELLS = TS::CELLS, ROWS = TS::ROWS, TAPS = TS::TAPS;
-    constexpr int ROUNDS = (TAPS + 31) / 32;
+    constexpr int PS = TS::PS, PS2 = PS * PS, PY = TS::PY, PZ = TS::PZ, CELLS = TS::CELLS, ROWS = TS::ROWS, TAPS = TS::TAPS;
+    constexpr int ROUNDS = TS::ROUNDS;
     constexpr int CHUNK = TS::CHUNK, REC = TS::REC;
     constexpr int NWARP = 8;
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
@@ -414,16 +472,20 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
     const int nb = bn.nb, s = a.s;
     const int org0[3] = {(t % nb) * TB, ((t / nb) % nb) * TB, (D == 3) ? (t / (nb * nb)) * TB : 0};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this lane's tap in each round: x weight, row of c * wy * wz, tile offset
+    // this lane's tap in each round (the lanes of a round on distinct banks): x
+    // weight, row of c * wy * wz, tile offset; bit q of `live`: a tap in round q
     int kx_of[ROUNDS], row_of[ROUNDS], cell_of[ROUNDS];
+    unsigned live = 0;
 #pragma unroll
     for (int q = 0; q < ROUNDS; ++q) {
-        const int tap = min(q * 32 + lane, TAPS - 1);
+        const int tap0 = kTapRounds<D, W, TB>.tap[q * 32 + lane];
+        live |= (tap0 >= 0 ? 1u : 0u) << q;
+        const int tap = max(tap0, 0);
         const int kx = tap % W, row = tap / W;
         const int ky = row % W, kz = (D == 3) ? row / W : 0;
         kx_of[q] = kx;
         row_of[q] = TS::O_ROW + 2 * row;
-        cell_of[q] = kx + PS * ky + PS2 * kz;
+        cell_of[q] = kx + PY * ky + PZ * kz;
     }
     float2* out = a.out + (int64_t)b * a.out_rot_stride;
     for (int p0 = lo; p0 < hi; p0 += CHUNK) {
@@ -435,13 +497,12 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
             float2 c;
             sample_taps<float, D, W>(a, Rm, sorted[p0 + threadIdx.x], org, wt, c);
             bool inside = true;
-            int base = 0, mul = 1, packed = 0;
+            int base = 0, packed = 0;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const int l = org[d] - org0[d];
                 inside &= (l >= 0 && l < TB);
-                base += l * mul;
-                mul *= PS;
+                base += l * (d == 0 ? 1 : (d == 1 ? PY : PZ));
                 packed |= org[d] << (10 * d);
             }
             float* r = stage + threadIdx.x * REC;
@@ -474,7 +535,7 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
             if (base >= 0) {  // uniform over the warp
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
-                    if (TAPS % 32 == 0 || q * 32 + lane < TAPS) {
+                    if ((live >> q) & 1u) {
                         const float wx = r[kx_of[q]];
                         const float2 cw = *reinterpret_cast<const float2*>(r + row_of[q]);
                         const int cell = base + cell_of[q];
@@ -513,7 +574,7 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
     for (int i = threadIdx.x; i < PAIRS; i += blockDim.x) {
         const int xp = i % XP, row = i / XP;  // row = y + PS z
         const int x = 2 * xp;
-        const int li = row * PS + x;
+        const int li = (row % PS) * PY + (D == 3 ? (row / PS) * PZ : 0) + x;
         const int r0 = tre[li], i0 = tim[li];
         const int r1 = (x + 1 < PS) ? tre[li + 1] : 0, i1 = (x + 1 < PS) ? tim[li + 1] : 0;
         if ((r0 | i0 | r1 | i1) == 0) continue;
@@ -1441,21 +1502,22 @@ __host__ __device__ constexpr int pruned_min_ctas() {
     return sizeof(T) != 4 ? 0 : (LEN == 512 ? 2 : (LEN == 384 ? 3 : 0));
 }
 
-// The narrow plan of the pruned column passes (forward y and the fused last
-// axis): half the columns per CTA, so twice the CTAs of half the shared memory,
-// for FP32 lines of 128 points and more.  Its register bound keeps the
-// per-thread cap of the standard plan.
+// Other widths of the pruned column passes (forward y and the fused last axis)
+// for FP32 lines of 128 to 384 points: the narrow plan takes half the columns
+// per CTA (twice the CTAs, half the shared memory each, 64-byte row segments),
+// the wide plan twice (256-byte row segments, up to 99 KB of shared memory).
+// Their register bound keeps the per-thread cap of the standard plan.
 template <typename T, int LEN>
-__host__ __device__ constexpr bool narrow_cols_ok() {
-    return sizeof(T) == 4 && LEN >= 128;
+__host__ __device__ constexpr bool alt_cols_ok() {
+    return sizeof(T) == 4 && LEN >= 128 && LEN <= 384;
 }
-template <typename T, int LEN>
-__host__ __device__ constexpr int narrow_lines() {
-    return lines_per_cta<T, LEN>() / 2;
+template <typename T, int LEN, int WIDE>
+__host__ __device__ constexpr int alt_lines() {
+    return WIDE ? 2 * lines_per_cta<T, LEN>() : lines_per_cta<T, LEN>() / 2;
 }
-template <typename T, int LEN, int KIND>
-__host__ __device__ constexpr int narrow_min_ctas() {
-    return pruned_min_ctas<T, LEN, KIND>() * cta_threads<T, LEN>() / cta_threads_for<LEN>(narrow_lines<T, LEN>());
+template <typename T, int LEN, int KIND, int WIDE>
+__host__ __device__ constexpr int alt_min_ctas() {
+    return pruned_min_ctas<T, LEN, KIND>() * cta_threads<T, LEN>() / cta_threads_for<LEN>(alt_lines<T, LEN, WIDE>());
 }
 
 // W' = W exp(2 pi i s_h (kx + ky [+ kz]) / n) with kappa signed (modes at kappa mod N).
@@ -1578,10 +1640,13 @@ static cudaError_t cols_fwd_p_launch(const ColArgs<T>& a, int batch, cudaStream_
 template <typename T, int LEN>
 static cudaError_t cols_fwd_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     static_assert(prunable_len(LEN), "length not prunable");
-    if constexpr (narrow_cols_ok<T, LEN>())
-        if (a.narrow)
-            return cols_fwd_p_launch<T, LEN, narrow_lines<T, LEN>(), narrow_min_ctas<T, LEN, 1>()>(a, batch, st);
-    if (a.narrow) return cudaErrorInvalidValue;
+    if constexpr (alt_cols_ok<T, LEN>()) {
+        if (a.lines == LINES_NARROW)
+            return cols_fwd_p_launch<T, LEN, alt_lines<T, LEN, 0>(), alt_min_ctas<T, LEN, 1, 0>()>(a, batch, st);
+        if (a.lines == LINES_WIDE)
+            return cols_fwd_p_launch<T, LEN, alt_lines<T, LEN, 1>(), alt_min_ctas<T, LEN, 1, 1>()>(a, batch, st);
+    }
+    if (a.lines != LINES_STD) return cudaErrorInvalidValue;
     return cols_fwd_p_launch<T, LEN, lines_per_cta<T, LEN>(), pruned_min_ctas<T, LEN, 1>()>(a, batch, st);
 }
 
@@ -1606,10 +1671,13 @@ static cudaError_t cols_fused_p_launch(const ColArgs<T>& a, int batch, cudaStrea
 template <typename T, int LENF>
 static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     static_assert(prunable_len(LENF), "length not prunable");
-    if constexpr (narrow_cols_ok<T, LENF>())
-        if (a.narrow)
-            return cols_fused_p_launch<T, LENF, narrow_lines<T, LENF>(), narrow_min_ctas<T, LENF, 2>()>(a, batch, st);
-    if (a.narrow) return cudaErrorInvalidValue;
+    if constexpr (alt_cols_ok<T, LENF>()) {
+        if (a.lines == LINES_NARROW)
+            return cols_fused_p_launch<T, LENF, alt_lines<T, LENF, 0>(), alt_min_ctas<T, LENF, 2, 0>()>(a, batch, st);
+        if (a.lines == LINES_WIDE)
+            return cols_fused_p_launch<T, LENF, alt_lines<T, LENF, 1>(), alt_min_ctas<T, LENF, 2, 1>()>(a, batch, st);
+    }
+    if (a.lines != LINES_STD) return cudaErrorInvalidValue;
     return cols_fused_p_launch<T, LENF, lines_per_cta<T, LENF>(), pruned_min_ctas<T, LENF, 2>()>(a, batch, st);
 }
 

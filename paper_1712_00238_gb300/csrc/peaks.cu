@@ -1,10 +1,14 @@
 // ALU throughput probes: the rates that bound the kernels that are limited by
 // arithmetic rather than memory (the SDF sums: FP32 FMA and the special-function
-// unit; the FP64 re-score: FP64 FMA), measured on the device they run on.  Each
-// thread runs eight independent dependency chains of one instruction class, long
-// enough to hide its latency, over several waves of CTAs; the rate is the best
-// of three timed launches after one untimed one.
+// unit; the FP64 re-score: FP64 FMA) or by shared-memory atomics (the spreading
+// tiles), measured on the device they run on.  Each thread runs eight
+// independent dependency chains of one instruction class, long enough to hide
+// its latency (the atomic kinds: eight adds per iteration to the thread's own
+// shared word, the lanes of a warp on distinct banks), over several waves of
+// CTAs; the rate is the best of three timed launches after one untimed one.
 #include <math.h>
+
+#include <type_traits>
 
 #include "../../include/sdfdock.h"
 #include "kernels.cuh"
@@ -17,7 +21,19 @@ constexpr int kThreads = 256;
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_peak(float* sink, int iters) {
     const float seed = 1e-3f * (float)(threadIdx.x & 31);
-    if constexpr (KIND == SD_PEAK_FP64_FMA) {
+    if constexpr (KIND == SD_PEAK_SHARED_ADD32 || KIND == SD_PEAK_SHARED_ADD64) {
+        // each thread adds to its own word (consecutive lanes, consecutive words)
+        using W = std::conditional_t<KIND == SD_PEAK_SHARED_ADD32, unsigned int, unsigned long long>;
+        __shared__ W acc[kThreads];
+        acc[threadIdx.x] = 0;
+        __syncthreads();
+        const W step = (W)(threadIdx.x & 7) + 1;
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) atomicAdd(acc + threadIdx.x, step + (W)k);
+        __syncthreads();
+        if (acc[threadIdx.x] == (W)1) sink[0] = 1.f;  // never true: keeps the adds
+    } else if constexpr (KIND == SD_PEAK_FP64_FMA) {
         double v[kChains];
 #pragma unroll
         for (int k = 0; k < kChains; ++k) v[k] = 0.5 + seed + 0.01 * k;
@@ -57,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_peak(float* sink, int iters) {
 }  // namespace
 
 int sd_alu_peak(int device, int kind, double* ops_per_s) {
-    if (!ops_per_s || kind < 0 || kind > SD_PEAK_SFU_RSQRT) return SD_ERR_ARG;
+    if (!ops_per_s || kind < 0 || kind > SD_PEAK_SHARED_ADD64) return SD_ERR_ARG;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return SD_ERR_CUDA;
     if (cudaSetDevice(device) != cudaSuccess) return SD_ERR_ARG;
@@ -66,10 +82,12 @@ int sd_alu_peak(int device, int kind, double* ops_per_s) {
     const int blocks = 8 * (sms > 0 ? sms : 1);
     // enough iterations for a launch of a few to tens of milliseconds
     const int iters = (kind == SD_PEAK_FP64_FMA) ? 2048 : (kind == SD_PEAK_FP32_FMA ? 65536 : 8192);
-    void (*kern)(float*, int) = kind == SD_PEAK_FP32_FMA   ? k_peak<SD_PEAK_FP32_FMA>
-                                : kind == SD_PEAK_FP64_FMA ? k_peak<SD_PEAK_FP64_FMA>
-                                : kind == SD_PEAK_SFU_EX2  ? k_peak<SD_PEAK_SFU_EX2>
-                                                           : k_peak<SD_PEAK_SFU_RSQRT>;
+    void (*kern)(float*, int) = kind == SD_PEAK_FP32_FMA       ? k_peak<SD_PEAK_FP32_FMA>
+                                : kind == SD_PEAK_FP64_FMA     ? k_peak<SD_PEAK_FP64_FMA>
+                                : kind == SD_PEAK_SFU_EX2      ? k_peak<SD_PEAK_SFU_EX2>
+                                : kind == SD_PEAK_SFU_RSQRT    ? k_peak<SD_PEAK_SFU_RSQRT>
+                                : kind == SD_PEAK_SHARED_ADD32 ? k_peak<SD_PEAK_SHARED_ADD32>
+                                                               : k_peak<SD_PEAK_SHARED_ADD64>;
     float* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = SD_OK;

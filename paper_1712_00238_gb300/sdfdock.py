@@ -530,7 +530,7 @@ class Octree:
             pass
 
 
-PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "sfu_ex2": 2, "sfu_rsqrt": 3}
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "sfu_ex2": 2, "sfu_rsqrt": 3, "shared_add32": 4, "shared_add64": 5}
 
 
 def alu_peak(kind: str, device: int = 0) -> float:
