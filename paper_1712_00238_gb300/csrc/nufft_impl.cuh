@@ -221,29 +221,31 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
 
 // Tap-box origin (sub-box coordinates, wrapped when the sub-box is the whole
 // periodic grid) and kernel weights of sample j under rotation Rm.
+// One axis of it: the rotated coordinate d of p, the axis's tap origin and
+// its W kernel weights.
+template <typename T, int W>
+__device__ __forceinline__ int axis_taps(const SpreadArgs<T>& a, const T* Rm, const vec4<T>& p, int d, T wt[W]) {
+    const T y = a.sign * (Rm[3 * d] * p.x + Rm[3 * d + 1] * p.y + Rm[3 * d + 2] * p.z);
+    const T half = T(W) * T(0.5);
+    const T inv_half = T(2) / T(W);
+    const T g = y * a.inv_h;
+    const int u0 = (int)ceil(g - half);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const T z = (T(u0 + k) - g) * inv_half;
+        const T z2 = z * z;
+        wt[k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
+    }
+    return wrap_index(u0 + a.s_h, a.s);
+}
+
 template <typename T, int D, int W>
 __device__ __forceinline__ void sample_taps(const SpreadArgs<T>& a, const T* Rm, int64_t j, int org[D], T wt[D][W],
                                             cplx<T>& c) {
     const vec4<T> p = a.pos[j];
     c = a.c[j];
-    T y[3];
-    y[0] = a.sign * (Rm[0] * p.x + Rm[1] * p.y + Rm[2] * p.z);
-    y[1] = a.sign * (Rm[3] * p.x + Rm[4] * p.y + Rm[5] * p.z);
-    y[2] = a.sign * (Rm[6] * p.x + Rm[7] * p.y + Rm[8] * p.z);
-    const T half = T(W) * T(0.5);
-    const T inv_half = T(2) / T(W);
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        const T g = y[d] * a.inv_h;
-        const int u0 = (int)ceil(g - half);
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const T z = (T(u0 + k) - g) * inv_half;
-            const T z2 = z * z;
-            wt[d][k] = (z2 <= T(1)) ? exp(a.beta * (sqrt(T(1) - z2) - T(1))) : T(0);
-        }
-        org[d] = wrap_index(u0 + a.s_h, a.s);
-    }
+    for (int d = 0; d < D; ++d) org[d] = axis_taps<T, W>(a, Rm, p, d, wt[d]);
 }
 
 // The tap-box origin alone (the same arithmetic as sample_taps).
@@ -359,11 +361,11 @@ struct TileShape {
     static constexpr int O_C = 3 * W, O_BASE = 3 * W + 2, O_ORG = 3 * W + 3, O_ROW = (3 * W + 4 + 1) & ~1;
     static constexpr int REC = (O_ROW + 2 * ROWS + 1) & ~1;
     static constexpr size_t smem = (size_t)2 * CELLS * sizeof(int) + (size_t)CHUNK * REC * sizeof(float);
-    static constexpr int offset(int tap) {
+    __host__ __device__ static constexpr int offset(int tap) {
         return tap % W + PY * ((tap / W) % W) + (D == 3 ? PZ * (tap / (W * W)) : 0);
     }
     // rounds: the most taps whose offsets share a residue mod 32
-    static constexpr int rounds() {
+    __host__ __device__ static constexpr int rounds() {
         int most = 0;
         for (int r = 0; r < 32; ++r) {
             int n = 0;
@@ -383,7 +385,7 @@ struct TapRounds {
     short tap[TileShape<D, W, TB>::ROUNDS * 32];
 };
 template <int D, int W, int TB>
-constexpr TapRounds<D, W, TB> make_tap_rounds() {
+__host__ __device__ constexpr TapRounds<D, W, TB> make_tap_rounds() {
     using TS = TileShape<D, W, TB>;
     TapRounds<D, W, TB> t{};
     for (int i = 0; i < TS::ROUNDS * 32; ++i) t.tap[i] = -1;
@@ -396,6 +398,18 @@ constexpr TapRounds<D, W, TB> make_tap_rounds() {
 }
 template <int D, int W, int TB>
 __device__ const TapRounds<D, W, TB> kTapRounds = make_tap_rounds<D, W, TB>();
+// Bit q: every lane has a tap in round q.
+template <int D, int W, int TB>
+__host__ __device__ constexpr unsigned full_rounds_mask() {
+    const TapRounds<D, W, TB> t = make_tap_rounds<D, W, TB>();
+    unsigned mask = 0;
+    for (int q = 0; q < TileShape<D, W, TB>::ROUNDS; ++q) {
+        bool full = true;
+        for (int l = 0; l < 32; ++l) full = full && t.tap[q * 32 + l] >= 0;
+        mask |= (full ? 1u : 0u) << q;
+    }
+    return mask;
+}
 
 // One CTA per (bin, rotation).  The CTA stages CHUNK of the bin's samples at a
 // time: one thread per sample evaluates its kernel weights and tile offset, then
@@ -412,11 +426,13 @@ __device__ const TapRounds<D, W, TB> kTapRounds = make_tap_rounds<D, W, TB>();
 // counting pass and this one agree, as they evaluate the same function) is
 // added with global atomics instead.
 template <int D, int W, int TB>
-__global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
+__global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, BinArgs bn) {
     using TS = TileShape<D, W, TB>;
     constexpr int PS = TS::PS, PS2 = PS * PS, PY = TS::PY, PZ = TS::PZ, CELLS = TS::CELLS, ROWS = TS::ROWS, TAPS = TS::TAPS;
     constexpr int ROUNDS = TS::ROUNDS;
     constexpr int CHUNK = TS::CHUNK, REC = TS::REC;
+    static_assert(4 * CHUNK == 256, "four threads per staged sample");
+    constexpr unsigned FULL = full_rounds_mask<D, W, TB>();
     constexpr int NWARP = 8;
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
     constexpr int MAGIC_BITS = 0x4B400000;
@@ -490,42 +506,57 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
     float2* out = a.out + (int64_t)b * a.out_rot_stride;
     for (int p0 = lo; p0 < hi; p0 += CHUNK) {
         const int nj = min(CHUNK, hi - p0);
-        // (1) one thread per sample: weights, weight value, tile offset
-        if ((int)threadIdx.x < nj) {
-            int org[D];
-            float wt[D][W];
-            float2 c;
-            sample_taps<float, D, W>(a, Rm, sorted[p0 + threadIdx.x], org, wt, c);
-            bool inside = true;
-            int base = 0, packed = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const int l = org[d] - org0[d];
-                inside &= (l >= 0 && l < TB);
-                base += l * (d == 0 ? 1 : (d == 1 ? PY : PZ));
-                packed |= org[d] << (10 * d);
-            }
-            float* r = stage + threadIdx.x * REC;
-#pragma unroll
-            for (int d = 0; d < D; ++d)
-#pragma unroll
-                for (int k = 0; k < W; ++k) r[d * W + k] = wt[d][k];
-            if (D == 2)
-#pragma unroll
-                for (int k = 0; k < W; ++k) r[2 * W + k] = 1.f;
-            r[TS::O_C] = c.x * scale;
-            r[TS::O_C + 1] = c.y * scale;
-            r[TS::O_BASE] = __int_as_float(inside ? base : -1);
-            r[TS::O_ORG] = __int_as_float(packed);
-        }
-        __syncthreads();
-        // (2) c * scale * wy * wz for every row of every staged sample
-        for (int i = threadIdx.x; i < nj * ROWS; i += blockDim.x) {
-            const int j = i / ROWS, row = i - j * ROWS;
+        // (1) four threads per sample, lanes 4i..4i+3 of one warp: the kernel
+        // weights of one axis each (the fourth: the scaled c), then each forms
+        // c * scale * wy * wz for a quarter of the sample's rows
+        {
+            const int j = (int)threadIdx.x >> 2, part = (int)threadIdx.x & 3;
+            const bool act = j < nj;
             float* r = stage + j * REC;
-            const float wyz = r[W + row % W] * r[2 * W + row / W];
-            r[TS::O_ROW + 2 * row] = r[TS::O_C] * wyz;
-            r[TS::O_ROW + 2 * row + 1] = r[TS::O_C + 1] * wyz;
+            int contrib = 0, ok = 1, packed = 0;
+            float cx = 0.f, cy = 0.f;
+            if (act) {
+                const int64_t js = sorted[p0 + j];
+                if (part < D) {
+                    float wt[W];
+                    const int o = axis_taps<float, W>(a, Rm, a.pos[js], part, wt);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) r[part * W + k] = wt[k];
+                    const int l = o - (part == 0 ? org0[0] : (part == 1 ? org0[1] : org0[2]));
+                    ok = (l >= 0 && l < TB);
+                    contrib = l * (part == 0 ? 1 : (part == 1 ? PY : PZ));
+                    packed = o << (10 * part);
+                } else if (part == 3) {
+                    const float2 c = a.c[js];
+                    cx = c.x * scale;
+                    cy = c.y * scale;
+                } else {  // 2D: unit z weights
+#pragma unroll
+                    for (int k = 0; k < W; ++k) r[2 * W + k] = 1.f;
+                }
+            }
+            // combine the four lanes of the sample (every lane of the warp takes part)
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+                ok &= __shfl_xor_sync(0xffffffffu, ok, o);
+                packed |= __shfl_xor_sync(0xffffffffu, packed, o);
+            }
+            cx = __shfl_sync(0xffffffffu, cx, (lane & ~3) | 3);
+            cy = __shfl_sync(0xffffffffu, cy, (lane & ~3) | 3);
+            __syncwarp();  // the weights of the sample's other lanes are in shared memory
+            if (act) {
+                if (part == 0) {
+                    r[TS::O_BASE] = __int_as_float(ok ? contrib : -1);
+                    r[TS::O_ORG] = __int_as_float(packed);
+                    r[TS::O_C] = cx;
+                    r[TS::O_C + 1] = cy;
+                }
+                for (int row = part; row < ROWS; row += 4) {
+                    const float wyz = r[W + row % W] * r[2 * W + row / W];
+                    *reinterpret_cast<float2*>(r + TS::O_ROW + 2 * row) = make_float2(cx * wyz, cy * wyz);
+                }
+            }
         }
         __syncthreads();
         // (3) the warps add the staged samples round-robin, one at a time
@@ -535,7 +566,7 @@ __global__ void __launch_bounds__(256, 2) k_spread_tiles(SpreadArgs<float> a, Bi
             if (base >= 0) {  // uniform over the warp
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
-                    if ((live >> q) & 1u) {
+                    if (((FULL >> q) & 1u) || ((live >> q) & 1u)) {
                         const float wx = r[kx_of[q]];
                         const float2 cw = *reinterpret_cast<const float2*>(r + row_of[q]);
                         const int cell = base + cell_of[q];
