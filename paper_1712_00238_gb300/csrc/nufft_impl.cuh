@@ -357,9 +357,9 @@ struct TileShape {
     static constexpr int ROWS = (D == 3) ? W * W : W;             // (ky, kz) rows of a tap box
     static constexpr int TAPS = ROWS * W;
     static constexpr int CHUNK = 64;                              // samples staged at a time
-    // record: wx[W] wy[W] wz[W] | c.x c.y | base | origin | c * wy * wz per row (pairs)
-    static constexpr int O_C = 3 * W, O_BASE = 3 * W + 2, O_ORG = 3 * W + 3, O_ROW = (3 * W + 4 + 1) & ~1;
-    static constexpr int REC = (O_ROW + 2 * ROWS + 1) & ~1;
+    // record: wx[W] | c.x c.y (scaled) | base | origin | wy * wz per row
+    static constexpr int O_C = W, O_BASE = W + 2, O_ORG = W + 3, O_ROW = W + 4;
+    static constexpr int REC = O_ROW + ROWS;
     static constexpr size_t smem = (size_t)2 * CELLS * sizeof(int) + (size_t)CHUNK * REC * sizeof(float);
     __host__ __device__ static constexpr int offset(int tap) {
         return tap % W + PY * ((tap / W) % W) + (D == 3 ? PZ * (tap / (W * W)) : 0);
@@ -500,39 +500,39 @@ __global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, Bi
         const int kx = tap % W, row = tap / W;
         const int ky = row % W, kz = (D == 3) ? row / W : 0;
         kx_of[q] = kx;
-        row_of[q] = TS::O_ROW + 2 * row;
+        row_of[q] = TS::O_ROW + row;
         cell_of[q] = kx + PY * ky + PZ * kz;
     }
     float2* out = a.out + (int64_t)b * a.out_rot_stride;
     for (int p0 = lo; p0 < hi; p0 += CHUNK) {
         const int nj = min(CHUNK, hi - p0);
         // (1) four threads per sample, lanes 4i..4i+3 of one warp: the kernel
-        // weights of one axis each (the fourth: the scaled c), then each forms
-        // c * scale * wy * wz for a quarter of the sample's rows
+        // weights of one axis each (the fourth: the scaled c); the y and z
+        // weights go to the sample's four lanes by shuffles, and each lane stores
+        // the products wy * wz of the rows whose kz is its index mod 4
         {
             const int j = (int)threadIdx.x >> 2, part = (int)threadIdx.x & 3;
             const bool act = j < nj;
             float* r = stage + j * REC;
             int contrib = 0, ok = 1, packed = 0;
-            float cx = 0.f, cy = 0.f;
+            float wt[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) wt[k] = 1.f;  // 2D: unit z weights in lane 2
             if (act) {
                 const int64_t js = sorted[p0 + j];
                 if (part < D) {
-                    float wt[W];
                     const int o = axis_taps<float, W>(a, Rm, a.pos[js], part, wt);
-#pragma unroll
-                    for (int k = 0; k < W; ++k) r[part * W + k] = wt[k];
                     const int l = o - (part == 0 ? org0[0] : (part == 1 ? org0[1] : org0[2]));
                     ok = (l >= 0 && l < TB);
                     contrib = l * (part == 0 ? 1 : (part == 1 ? PY : PZ));
                     packed = o << (10 * part);
+                    if (part == 0)
+#pragma unroll
+                        for (int k = 0; k < W; ++k) r[k] = wt[k];
                 } else if (part == 3) {
                     const float2 c = a.c[js];
-                    cx = c.x * scale;
-                    cy = c.y * scale;
-                } else {  // 2D: unit z weights
-#pragma unroll
-                    for (int k = 0; k < W; ++k) r[2 * W + k] = 1.f;
+                    r[TS::O_C] = c.x * scale;
+                    r[TS::O_C + 1] = c.y * scale;
                 }
             }
             // combine the four lanes of the sample (every lane of the warp takes part)
@@ -542,36 +542,38 @@ __global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, Bi
                 ok &= __shfl_xor_sync(0xffffffffu, ok, o);
                 packed |= __shfl_xor_sync(0xffffffffu, packed, o);
             }
-            cx = __shfl_sync(0xffffffffu, cx, (lane & ~3) | 3);
-            cy = __shfl_sync(0xffffffffu, cy, (lane & ~3) | 3);
-            __syncwarp();  // the weights of the sample's other lanes are in shared memory
+            float wy[W], wz[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                wy[k] = __shfl_sync(0xffffffffu, wt[k], (lane & ~3) | 1);
+                wz[k] = __shfl_sync(0xffffffffu, wt[k], (lane & ~3) | 2);
+            }
             if (act) {
                 if (part == 0) {
                     r[TS::O_BASE] = __int_as_float(ok ? contrib : -1);
                     r[TS::O_ORG] = __int_as_float(packed);
-                    r[TS::O_C] = cx;
-                    r[TS::O_C + 1] = cy;
                 }
-                for (int row = part; row < ROWS; row += 4) {
-                    const float wyz = r[W + row % W] * r[2 * W + row / W];
-                    *reinterpret_cast<float2*>(r + TS::O_ROW + 2 * row) = make_float2(cx * wyz, cy * wyz);
-                }
+#pragma unroll
+                for (int kz = 0; kz < ROWS / W; ++kz)
+                    if ((kz & 3) == part)
+#pragma unroll
+                        for (int ky = 0; ky < W; ++ky) r[TS::O_ROW + ky + W * kz] = wy[ky] * wz[kz];
             }
         }
         __syncthreads();
-        // (3) the warps add the staged samples round-robin, one at a time
+        // (2) the warps add the staged samples round-robin, one at a time
         for (int j = warp; j < nj; j += NWARP) {
             const float* r = stage + j * REC;
             const int base = __float_as_int(r[TS::O_BASE]);
             if (base >= 0) {  // uniform over the warp
+                const float cx = r[TS::O_C], cy = r[TS::O_C + 1];
 #pragma unroll
                 for (int q = 0; q < ROUNDS; ++q) {
                     if (((FULL >> q) & 1u) || ((live >> q) & 1u)) {
-                        const float wx = r[kx_of[q]];
-                        const float2 cw = *reinterpret_cast<const float2*>(r + row_of[q]);
+                        const float w = r[kx_of[q]] * r[row_of[q]];
                         const int cell = base + cell_of[q];
-                        atomicAdd(tre + cell, __float_as_int(fmaf(cw.x, wx, MAGIC)) - MAGIC_BITS);
-                        atomicAdd(tim + cell, __float_as_int(fmaf(cw.y, wx, MAGIC)) - MAGIC_BITS);
+                        atomicAdd(tre + cell, __float_as_int(fmaf(cx, w, MAGIC)) - MAGIC_BITS);
+                        atomicAdd(tim + cell, __float_as_int(fmaf(cy, w, MAGIC)) - MAGIC_BITS);
                     }
                 }
             } else {  // safety net (a tap box outside the tile): global atomics on the sub-box
@@ -582,13 +584,10 @@ __global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, Bi
                     const int tap = q * 32 + lane;
                     if (tap < TAPS) {
                         const int kx = tap % W, ky = (tap / W) % W, kz = (D == 3) ? tap / (W * W) : 0;
-                        float w = r[kx] * r[W + ky];
+                        const float w = r[kx] * r[TS::O_ROW + tap / W];
                         int64_t o = (int64_t)wrap_index(((packed >> 10) & 1023) + ky, s) * s +
                                     wrap_index((packed & 1023) + kx, s);
-                        if (D == 3) {
-                            w *= r[2 * W + kz];
-                            o += (int64_t)wrap_index(((packed >> 20) & 1023) + kz, s) * s * s;
-                        }
+                        if (D == 3) o += (int64_t)wrap_index(((packed >> 20) & 1023) + kz, s) * s * s;
                         atomic_cadd(out + o, make_float2(cx * w, cy * w));
                     }
                 }
