@@ -401,7 +401,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "peak_source": src,
                     "algorithmic_bytes_per_launch": int(per_launch),
-                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, s, w.N, plan_used.get("batch"))),
+                    "traffic": traffic_per_launch(dom, s, w.N, plan_used.get("batch")),
                     "avg_launch_us": round(avg_s * 1e6, 2)}
     search_ms = None
     if passes:
@@ -415,7 +415,7 @@ def run_ours(args):
                    "rotations": n_rot, "translations": w.N ** w.dim, "sub_box": s,
                    "batch": plan_used.get("batch"), "autotune": bool(args.autotune),
                    "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": ("fused with the forward x transform (8x6 row bins, shared fixed-point tile)"
+                   "spread": ("fused with the forward x transform (5x6 row bins, shared fixed-point tile)"
                               if plan_used.get("spread_bins") == 1 else
                               "shared boxes of 128 Morton-consecutive samples, 16-byte pair atomics"
                               if plan_used.get("spread_bins") == 2 else
@@ -492,10 +492,6 @@ def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# search passes from one ncu capture of the current kernels, keyed by (pass,
-# sub-box side, N, rotations per launch); a launch of another shape reports
-# null.  Docking pair: one 20-rotation launch of the pruned fused pass, whose
-# product table is read from DRAM once per launch (its other rotations hit L2).
 # the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE)
 FFT_PLAN_TEXT = {
     0: "full: shifted sub-box padded to n, every output of each line",
@@ -504,9 +500,23 @@ FFT_PLAN_TEXT = {
     3: "pruned, twice the columns per CTA in the forward y and fused z passes",
 }
 
-TRAFFIC_PER_LAUNCH: dict = {
-    ("fused", 156, 192, 20): 976803840 + 1081333248,
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# search passes from one ncu capture, keyed by (pass, sub-box side, N): bytes per
+# rotation of the launch and bytes once per launch.  Docking pair: one
+# 20-rotation launch of the pruned fused pass read 976,803,840 B and wrote
+# 1,081,333,248 B; its product table W' (N^3 complex, 56,623,104 B) is read from
+# DRAM once per launch (the launch's other rotations hit L2), the rest scales
+# with the rotations.  A pass of another shape reports null.
+TRAFFIC_MODEL: dict = {
+    ("fused", 156, 192): ((976803840 - 56623104 + 1081333248) / 20, 56623104),
 }
+
+
+def traffic_per_launch(dom, s, N, batch):
+    m = TRAFFIC_MODEL.get((dom, s, N))
+    if m is None or not batch:
+        return None
+    return int(round(m[0] * batch + m[1]))
 
 
 # ---------------------------------------------------------------------------

@@ -831,7 +831,9 @@ __global__ void __launch_bounds__(BOX_SPC) k_spread_box(SpreadArgs<float> a) {
 // from the tile and writes the N kept modes of each row.  No sub-box is stored,
 // cleared or re-read, and no global atomic is issued.
 
-constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 8, SX_NT = 256, SX_CHUNK = 64;
+constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 6, SX_NT = 256, SX_CHUNK = 64;
+static_assert(SX_TY >= SX_W - 1 && SX_TZ >= SX_W - 1, "a tap box must meet at most two bins per axis");
+static_assert((SX_TY * SX_TZ) % SX_TR == 0, "rows per FFT group must divide the rows of a bin");
 // staged record: w[axis][W] | origin[3] | c * scale (pair)
 constexpr int SX_O_ORG = 3 * SX_W, SX_O_C = 3 * SX_W + 4;
 constexpr int SX_REC = SX_O_C + 2;

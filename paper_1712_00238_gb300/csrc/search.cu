@@ -8,6 +8,7 @@
 // FP64 (the continuous score of Eq. 8 for Gaussian-represented SDFs).  Pairs
 // are screened in FP32 against a cutoff of 8 sigma_g sqrt 2 (with a margin), and
 // CTA / tile bounding boxes skip whole blocks of far pairs.
+#include <algorithm>
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -274,7 +275,11 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
             }
         }
     };
-    for (int tile = 0; tile < ntiles; ++tile) {
+    // this CTA's share of the moving tiles (grid z splits them, so that the few
+    // fixed blocks near the contact are spread over more CTAs)
+    const int per = (ntiles + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int t_lo = (int)blockIdx.z * per, t_hi = min(ntiles, t_lo + per);
+    for (int tile = t_lo; tile < t_hi; ++tile) {
         const float* tb = tbase + tile * 6;
         const float g0 = fmaxf(0.f, fmaxf(tb[0] - bhi0, blo0 - tb[3]));
         const float g1 = fmaxf(0.f, fmaxf(tb[1] - bhi1, blo1 - tb[4]));
@@ -357,7 +362,19 @@ cudaError_t launch_rescore(const RescoreArgs<T>& a, cudaStream_t st) {
     const unsigned ntiles = (unsigned)((a.m2 + RS_TILE - 1) / RS_TILE);
     k_rescore_move<T><<<dim3(ntiles, a.k), RS_TILE, 0, st>>>(a);
     note_launch();
-    const dim3 grid((unsigned)((a.m1 + RS_TILE - 1) / RS_TILE), a.k);
+    // split the moving tiles over grid z until there are about 64 CTAs per SM
+    // (most CTAs find their fixed block beyond reach of the pose and return)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    const int64_t fixed_tiles = (a.m1 + RS_TILE - 1) / RS_TILE;
+    const int64_t want = ((int64_t)64 * sms + fixed_tiles * a.k - 1) / (fixed_tiles * a.k);
+    const unsigned groups = (unsigned)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)ntiles, 16}));
+    const dim3 grid((unsigned)fixed_tiles, a.k, groups);
     k_rescore<T><<<grid, RS_TILE, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
