@@ -71,6 +71,8 @@ def parse_args():
                          "forward x transform there (3D FP32)")
     ap.add_argument("--spread-box", type=int, default=0,
                     help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
+    ap.add_argument("--inverse-cluster", type=int, default=1, choices=[0, 1],
+                    help="1: inverse y and x of each z-plane in one cluster kernel (3D FP32); 0: two passes")
     ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="forward-pass FFT plan: -1 the autotuner's (or the pruned default), 0 full, 1 pruned, "
                          "2 pruned with narrow column CTAs, 3 pruned with wide column CTAs")
@@ -227,6 +229,7 @@ def algorithmic_bytes_per_rotation(s: int, N: int, m_moving: int, dim: int = 3, 
         "fused": (s * N * N + 2 * N ** 3) * c,
         "inv_y": 2 * N ** 3 * c,
         "inv_x": N ** 3 * c,
+        "inv_yx": N ** 3 * c,
         "reduce": 0,
     }
 
@@ -265,6 +268,7 @@ def run_ours(args):
     ctx.set_option("spread_box", args.spread_box)
     ctx.set_option("spread_bin_side", args.spread_bin_side)
     ctx.set_option("fft_plan", args.fft_plan)
+    ctx.set_option("inverse_cluster", args.inverse_cluster)
     ctx.set_option("autotune", args.autotune)
     grid = sd.Grid(w.N, w.L)
     plan_used = {}
@@ -398,10 +402,13 @@ def run_ours(args):
         avg_s = t * 1e-3 / n
         peak, src = measured_peak()
         ach = per_launch / avg_s / 1e9
+        traffic = traffic_per_launch(dom, s, w.N, plan_used.get("batch"))
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "peak_source": src,
                     "algorithmic_bytes_per_launch": int(per_launch),
-                    "traffic": traffic_per_launch(dom, s, w.N, plan_used.get("batch")),
+                    "traffic": traffic,
+                    # the same launch time against the DRAM bytes it actually moves
+                    "frac_dram_actual": (round(traffic / avg_s / 1e9 / peak, 4) if traffic else None),
                     "avg_launch_us": round(avg_s * 1e6, 2)}
     search_ms = None
     if passes:
@@ -422,6 +429,8 @@ def run_ours(args):
                               f"binned shared-memory tiles ({plan_used['spread_bins']}^3-cell bins)"
                               if plan_used.get("spread_bins") else "global vector atomics"),
                    "fft_plan": FFT_PLAN_TEXT.get(plan_used.get("fft_plan")),
+                   "inverse": ("y and x of each z-plane in one kernel, clusters of 8 CTAs sharing the plane"
+                               if "inv_yx" in passes else "two passes (y, then x with argmax)"),
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -143,6 +143,11 @@ const char* sd_last_error(const sd_ctx* ctx);
  * every mode; results are the same up to FP rounding), "fft_plan" (-1, the
  * default: the autotuner's choice, else SD_FFT_PRUNED where the pruned passes
  * apply; 0..3: that SD_FFT_* plan wherever it applies, never tuned),
+ * "inverse_cluster" (1, the default: in 3D FP32 searches with N in {32, 48, 64,
+ * 96, 128, 192, 256} returning maps or one candidate per rotation, the inverse
+ * y and x transforms of each z-plane run in one kernel, a cluster of 8 CTAs
+ * per plane holding the plane in distributed shared memory between the two
+ * axes; 0: two passes through device memory; same results up to FP rounding),
  * "spread_box" (1: each
  * CTA spreads a block of Morton-consecutive samples into a shared box of the
  * sub-box and adds the box's nonzero cells with 16-byte atomics; FP32, w 4-7;
@@ -507,7 +512,8 @@ int64_t sd_launch_count(void);
 #define SD_PASS_REDUCE 7  /* per-rotation argmax reduction                    */
 #define SD_PASS_GRAPH 8   /* one replay of a captured search graph            */
 #define SD_PASS_SPREAD_X 9  /* rotate + spread fused with the forward x FFT   */
-#define SD_PASS_COUNT 10
+#define SD_PASS_INV_YX 10   /* inverse y and x of whole z-planes in clusters  */
+#define SD_PASS_COUNT 11
 
 /* With the context option "timing" = 1, every pass launch of the search is
  * bracketed by CUDA events on its stream; a search replayed from a captured

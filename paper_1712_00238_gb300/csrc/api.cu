@@ -80,6 +80,7 @@ struct sd_ctx {
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_fft_plan = -1;      // >= 0: this SD_FFT_* plan wherever it applies (not tuned)
+    int opt_inv_cluster = 1;    // 1: inverse y and x of whole z-planes in thread-block clusters (3D FP32)
     int opt_bin_side = DEFAULT_BIN;  // bin side of binned spreading when it is not tuned
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
@@ -798,6 +799,7 @@ struct Search {
     bool prunable = false;          // pruned forward passes apply (sub-box in the low half of a line)
     bool alt_cols = false;          // and their narrow / wide column plans exist (FP32, n 128..384)
     const cplx<T>* Wsh = nullptr;   // the shifted table W' of the pruned passes
+    bool iyx = false;               // inverse y + x in clusters (maps, or one candidate per rotation)
     int k_r = 1;          // candidates per rotation (argmax output)
     int64_t e0 = 0, e1 = 0, rows_last = 0, Nd = 0;
     cplx<T>* b0 = nullptr;
@@ -865,6 +867,7 @@ static int search_setup(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* movi
         S->Wsh = (const cplx<T>*)ws;
     }
     S->plan.fft = fft_plan_default(ctx, *S);
+    S->iyx = ctx->opt_inv_cluster && sizeof(T) == 4 && S->G.dim == 3 && inv_yx_supported(S->G.N);
     if (ctx->opt_spread_box && bins_supported(ctx)) S->plan.bins = SPREAD_BOX;
     if (ctx->opt_spread_fused && spread_x_ok(ctx, *S)) S->plan.bins = SPREAD_X;
     return SD_OK;
@@ -913,6 +916,8 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
     const Geo& G = S.G;
     const int B = S.plan.B;
     const bool fused_x = S.plan.bins == SPREAD_X;
+    // the cluster inverse ends with one candidate per rotation (or the map)
+    const bool iyx = S.iyx && (S.maps || S.k_r <= 1);
     for (int64_t r0 = r_lo; r0 < r_hi; r0 += B) {
         const int b = (int)std::min<int64_t>(B, r_hi - r0);
         if (!fused_x) {
@@ -966,7 +971,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
                 PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
                 CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, lines));
             }
-            {
+            if (!iyx) {
                 PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
                 CK(ctx, pass_y_inv<T>(G, S.tw, S.b1, S.e1, b, s));
             }
@@ -991,8 +996,9 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         if (S.maps) {
             r.out = (C*)S.out + r0 * S.Nd;
             r.out_rot_stride = S.Nd;
-            PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
-            CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
+            PassTimer pt(ctx, iyx ? SD_PASS_INV_YX : SD_PASS_INV_X, s, timed);
+            if (iyx) CK(ctx, launch_inv_yx<T>(ROW_INV_MAP, r, b, nullptr, s));
+            else CK(ctx, launch_rows<T>(ROW_INV_MAP, r, b, nullptr, s));
         } else {
             int nparts = 0;
             r.part_score = S.ps;
@@ -1002,8 +1008,9 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             const int mode = K == 1 ? ROW_INV_ARGMAX
                                     : (K == 2 ? ROW_INV_TOPK2 : (K == 4 ? ROW_INV_TOPK4 : (K == 8 ? ROW_INV_TOPK8 : ROW_INV_TOPK16)));
             {
-                PassTimer pt(ctx, SD_PASS_INV_X, s, timed);
-                CK(ctx, launch_rows<T>(mode, r, b, &nparts, s));
+                PassTimer pt(ctx, iyx ? SD_PASS_INV_YX : SD_PASS_INV_X, s, timed);
+                if (iyx) CK(ctx, launch_inv_yx<T>(mode, r, b, &nparts, s));
+                else CK(ctx, launch_rows<T>(mode, r, b, &nparts, s));
             }
             PassTimer pt(ctx, SD_PASS_REDUCE, s, timed);
             if (K == 1) CK(ctx, launch_reduce_argmax(S.ps, S.pi, nparts, b, r0, S.out, s));
@@ -1123,7 +1130,7 @@ static int run_search(sd_ctx* ctx, const sd_shape* fixed, const sd_shape* moving
         char key[256];
         snprintf(key, sizeof key, "%p|%p|%p|%lld|%d|%.17g|%p|%d|%p|%d|%d|%d|%d|%d", (const void*)fixed,
                  (const void*)moving, (const void*)quats, (long long)n_r, g->N, g->L, out, maps, (void*)st, S.plan.B,
-                 S.plan.bins, S.plan.fft, ctx->opt_timing, S.k_r);
+                 S.plan.bins, S.plan.fft, ctx->opt_timing, S.k_r * 2 + (int)S.iyx);
         std::string k(key);
         auto it = ctx->graphs.find(k);
         if (it == ctx->graphs.end()) {
@@ -1189,7 +1196,7 @@ static int run_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pa
         char part[256];
         snprintf(part, sizeof part, "|%p,%p,%p,%lld,%d,%.17g,%p,%d,%d,%d", (const void*)J.fixed,
                  (const void*)J.moving, (const void*)J.quats, (long long)J.n_r, J.grid.N, J.grid.L,
-                 (void*)J.cand_out, S[j].plan.B, S[j].plan.bins, S[j].plan.fft);
+                 (void*)J.cand_out, S[j].plan.B, S[j].plan.bins, S[j].plan.fft * 2 + (int)S[j].iyx);
         k += part;
     }
     char tail[64];
@@ -1368,6 +1375,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
     else if (!strcmp(key, "timing")) ctx->opt_timing = (int)value;
     else if (!strcmp(key, "spread_direct")) ctx->opt_spread_direct = (int)value;
     else if (!strcmp(key, "pruned")) ctx->opt_pruned = (int)value;
+    else if (!strcmp(key, "inverse_cluster")) ctx->opt_inv_cluster = (int)value;
     else if (!strcmp(key, "spread_bin_side")) {
         if (value != 8 && value != 12 && value != 16) return fail(ctx, SD_ERR_ARG, "spread_bin_side: 8, 12 or 16");
         ctx->opt_bin_side = (int)value;

@@ -148,6 +148,15 @@ struct RowArgs {
 };
 template <typename T> cudaError_t launch_rows(int mode, const RowArgs<T>& a, int batch, int* nparts,
                                               cudaStream_t st);
+// Inverse y and x of whole z-planes in thread-block clusters (3D, FP32, modes
+// ROW_INV_ARGMAX / ROW_INV_MAP): a.in is the rotation's N^3 volume (z, ky, kx)
+// after the last-axis pass, a.nrows = N^2, row strides N; *nparts receives the
+// argmax partials per rotation (N times the cluster size).
+template <typename T> cudaError_t launch_inv_yx(int mode, const RowArgs<T>& a, int batch, int* nparts,
+                                                cudaStream_t st);
+inline bool inv_yx_supported(int N) {
+    return N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 192 || N == 256;
+}
 
 template <typename T>
 struct ColArgs {

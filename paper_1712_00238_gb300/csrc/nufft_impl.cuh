@@ -1481,6 +1481,89 @@ __global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_p(RowArgs<T>
     rows_inv_p_body<T, LEN, MODE>(a);
 }
 
+// ---------------------------------------------------------------------------
+// inverse y and x of whole z-planes in thread-block clusters (3D search)
+// ---------------------------------------------------------------------------
+//
+// The N x N plane (ky, kx) of one rotation at one z is shared by the IYX_CS CTAs
+// of a cluster.  CTA q first runs the inverse y transform of the N / IYX_CS
+// columns kx in [q N / IYX_CS, (q + 1) N / IYX_CS), leaving them in its shared
+// memory; after a cluster barrier it runs the inverse x transform of the rows y
+// in the same range, the first stage reading each row's inputs from the CTAs
+// that hold them (distributed shared memory); a second barrier, after those
+// reads, lets every CTA reuse its buffer for the remaining stages.  The
+// plane's intermediate never returns to device memory: one read of N^3 per
+// rotation instead of a read, a write and a read.  Output as the inverse x pass:
+// the map's rows, or each CTA's (max Re, lowest index) partial.
+
+constexpr int IYX_CS = 8;  // CTAs per cluster (the portable maximum)
+
+template <typename T, int LEN>
+__host__ __device__ constexpr int iyx_lines() { return LEN / IYX_CS; }
+template <typename T, int LEN>
+__host__ __device__ constexpr int iyx_threads() { return cta_threads_for<LEN>(iyx_lines<T, LEN>()); }
+template <typename T, int LEN>
+__host__ __device__ constexpr int iyx_pitch() {
+    return col_pitch(LEN) > line_pitch(LEN) ? col_pitch(LEN) : line_pitch(LEN);
+}
+// The register cap of three CTAs per SM where that leaves room for a radix-24
+// stage (0: the compiler's choice).
+template <typename T, int LEN>
+__host__ __device__ constexpr int iyx_min_ctas() {
+    return (sizeof(T) == 4 && iyx_threads<T, LEN>() == 384) ? 3 : 0;
+}
+
+template <typename T, int LEN, int MODE>
+__global__ void __cluster_dims__(IYX_CS, 1, 1) __launch_bounds__(iyx_threads<T, LEN>(), iyx_min_ctas<T, LEN>())
+    k_inv_yx(RowArgs<T> a) {
+    using C = cplx<T>;
+    constexpr int NL = iyx_lines<T, LEN>();  // columns, then rows, of this CTA
+    constexpr int NT = iyx_threads<T, LEN>();
+    constexpr int LDA = col_pitch(LEN);      // y transform: buf[column * LDA + y]
+    constexpr int LDB = line_pitch(LEN);     // x transform: padded rows
+    constexpr int NTW = tw_count(LEN);
+    constexpr int NB1 = LEN / plan_radix(LEN, 0);
+    constexpr int PL = LEN / plan_last_radix(LEN);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* tw = buf + NL * iyx_pitch<T, LEN>();
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const int q = (int)cl.block_rank();
+    const int z = (int)blockIdx.x / IYX_CS;
+    const int c0 = q * NL;  // this CTA's first column, then first row
+    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
+    __syncthreads();
+    const C* plane = a.in + (int64_t)blockIdx.y * a.in_rot_stride + (int64_t)z * LEN * LEN;  // [ky][kx]
+    // inverse y of columns c0 .. c0 + NL - 1 (lanes across columns: coalesced)
+    auto load_y = [&](int line, int i, int r) -> C { return plane[(int64_t)(i + r * NB1) * LEN + c0 + line]; };
+    auto emit_y = [&](int line, int i, int r, C v) { buf[line * LDA + i + r * PL] = v; };
+    fftp_lines<C, LEN, true, NL, NT, LAY_COL, false, false, false>(buf, LDA, tw, load_y, emit_y);
+    cl.sync();  // every column of the plane is transformed
+    // inverse x of rows c0 .. c0 + NL - 1: input kx of row y sits in CTA kx / NL
+    auto load_x = [&](int line, int i, int r) -> C {
+        const int kx = i + r * NB1;
+        const C* src = cl.map_shared_rank(buf, kx / NL);
+        return src[(kx % NL) * LDA + c0 + line];
+    };
+    T best = -INFINITY;
+    int bidx = INT_MAX;
+    const int64_t row0 = (int64_t)z * LEN + c0;  // row (z, y) of the rotation's map
+    C* out = (MODE == ROW_INV_MAP) ? a.out + (int64_t)blockIdx.y * a.out_rot_stride + row0 * LEN : nullptr;
+    auto emit_x = [&](int line, int i, int r, C v) {
+        if constexpr (MODE == ROW_INV_ARGMAX) argmax_merge(best, bidx, v.x, (int)((row0 + line) * LEN) + i + r * PL);
+        else out[line * LEN + i + r * PL] = v;
+    };
+    fftp_lines<C, LEN, true, NL, NT, LAY_ROW, true, false, false, 0, 1, 1>(buf, LDB, tw, load_x, emit_x);
+    if constexpr (MODE == ROW_INV_ARGMAX) {
+        block_argmax(best, bidx);
+        if (threadIdx.x == 0) {
+            const int64_t o = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+            a.part_score[o] = (double)best;
+            a.part_idx[o] = bidx;
+        }
+    }
+}
+
 // Inverse x of rows of N points keeping each block's K best translations of the
 // real part (score descending, index ascending): a sorted list per thread, merged
 // through shared memory after the transform; partials are K per block.
@@ -1728,6 +1811,46 @@ static cudaError_t rows_inv_p_impl(const RowArgs<T>& a, int batch, int* nparts, 
     kern<<<dim3(nb, batch), cta_threads<T, LEN>(), smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
+}
+
+// Plane lengths the cluster inverse is built for (FP32; N a multiple of IYX_CS;
+// the same list as inv_yx_supported).
+#define SD_FOR_EACH_IYX(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+
+template <typename T, int LEN, int MODE>
+static cudaError_t inv_yx_impl(const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    using C = cplx<T>;
+    static_assert(LEN % IYX_CS == 0, "plane length not a multiple of the cluster size");
+    const int nb = IYX_CS * LEN;  // one cluster per z-plane
+    if (nparts) *nparts = nb;
+    if (batch == 0) return cudaSuccess;
+    if (a.in_row_stride != LEN || (MODE == ROW_INV_MAP && a.out_row_stride != LEN) || a.nrows != LEN * LEN)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(iyx_lines<T, LEN>() * iyx_pitch<T, LEN>() + tw_count(LEN)) * sizeof(C);
+    auto kern = k_inv_yx<T, LEN, MODE>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(nb, batch), iyx_threads<T, LEN>(), smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inv_yx_t(int mode, const RowArgs<T>& a, int batch, int* nparts, cudaStream_t st) {
+    if constexpr (sizeof(T) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (mode != ROW_INV_ARGMAX && mode != ROW_INV_MAP) return cudaErrorInvalidValue;
+        switch (a.N) {
+#define SD_IYX_CASE(L)                                                                       \
+    case L:                                                                                  \
+        return mode == ROW_INV_ARGMAX ? inv_yx_impl<T, L, ROW_INV_ARGMAX>(a, batch, nparts, st) \
+                                      : inv_yx_impl<T, L, ROW_INV_MAP>(a, batch, nparts, st);
+            SD_FOR_EACH_IYX(SD_IYX_CASE)
+#undef SD_IYX_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int LEN>
@@ -2103,6 +2226,9 @@ cudaError_t launch_interleave_t(const cplx<T>* src, cplx<T>* dst, int n, int pn,
     }                                                                                                   \
     template <> cudaError_t launch_rows<T>(int mode, const RowArgs<T>& a, int batch, int* np, cudaStream_t st) { \
         return launch_rows_t<T>(mode, a, batch, np, st);                                                \
+    }                                                                                                   \
+    template <> cudaError_t launch_inv_yx<T>(int mode, const RowArgs<T>& a, int batch, int* np, cudaStream_t st) { \
+        return launch_inv_yx_t<T>(mode, a, batch, np, st);                                              \
     }                                                                                                   \
     template <> cudaError_t launch_cols<T>(int mode, const ColArgs<T>& a, int batch, cudaStream_t st) {   \
         return launch_cols_t<T>(mode, a, batch, st);                                                    \

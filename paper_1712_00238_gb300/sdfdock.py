@@ -134,7 +134,7 @@ _SIGS = {
     "sd_alu_peak": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(ct.c_double)]),
 }
 
-PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph", "spread_x"]
+PASS_NAMES = ["clear", "spread", "fwd_x", "fwd_y", "fused", "inv_y", "inv_x", "reduce", "graph", "spread_x", "inv_yx"]
 
 
 def library_path() -> str:

@@ -278,6 +278,40 @@ def test_fused_spreading_matches_oracle(N):
     ctx.close()
 
 
+@pytest.mark.parametrize("N", [32, 48, 64, 96])
+def test_cluster_inverse_matches_oracle(N):
+    # inverse y and x of each z-plane in one kernel (a cluster of CTAs sharing the
+    # plane through distributed shared memory) against the oracle's maps and the
+    # two-pass inverse; the argmax candidates come from the same kernel
+    w = configs.tiny_3d()
+    p1, c1, p2, c2 = oracle_weights("tiny_3d")
+    ctx = make_ctx(w, "f32")
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    got = {}
+    for on in (1, 0):
+        ctx.set_option("inverse_cluster", on)
+        ctx.set_option("timing", 1)
+        ctx.pass_times(reset=True)
+        maps = ctx.score_maps(fx, mv, q, g).cpu().numpy()
+        cands = [t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g))]
+        t = ctx.pass_times()
+        # the cluster pass ran instead of the inverse y and x passes (and only then)
+        assert (t["inv_yx"][0] > 0) == bool(on) and (t["inv_y"][0] > 0) == (not on)
+        got[on] = (maps, cands)
+    ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
+    maps, (s, rot, idx) = got[1]
+    for r in range(w.n_rot):
+        assert rel_err(maps[r], ref[r]) < TOL["f32"], r
+        assert rel_err(maps[r], got[0][0][r]) < 2e-6, r
+        assert abs(s[r] - maps[r].real.max()) <= 1e-6 * np.abs(maps[r].real).max()
+        if top1_margin_ok(ref[r].real):
+            assert idx[r] == int(np.argmax(ref[r].real)) == got[0][1][2][r]
+    ctx.close()
+
+
 def test_maps_full_size_peg_in_bore():
     # 128^3 translations, n = 256 oversampled grid, ~50,000 samples per shape;
     # weights are seeded synthetic values shared by both sides.
