@@ -71,7 +71,7 @@ def parse_args():
                          "forward x transform there (3D FP32)")
     ap.add_argument("--spread-box", type=int, default=0,
                     help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
-    ap.add_argument("--inverse-cluster", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--inverse-cluster", type=int, default=0, choices=[0, 1],
                     help="1: inverse y and x of each z-plane in one cluster kernel (3D FP32); 0: two passes")
     ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="forward-pass FFT plan: -1 the autotuner's (or the pruned default), 0 full, 1 pruned, "

@@ -143,11 +143,12 @@ const char* sd_last_error(const sd_ctx* ctx);
  * every mode; results are the same up to FP rounding), "fft_plan" (-1, the
  * default: the autotuner's choice, else SD_FFT_PRUNED where the pruned passes
  * apply; 0..3: that SD_FFT_* plan wherever it applies, never tuned),
- * "inverse_cluster" (1, the default: in 3D FP32 searches with N in {32, 48, 64,
- * 96, 128, 192, 256} returning maps or one candidate per rotation, the inverse
- * y and x transforms of each z-plane run in one kernel, a cluster of 8 CTAs
- * per plane holding the plane in distributed shared memory between the two
- * axes; 0: two passes through device memory; same results up to FP rounding),
+ * "inverse_cluster" (1: in 3D FP32 searches with N in {32, 48, 64, 96, 128,
+ * 192, 256} returning maps or one candidate per rotation, the inverse y and x
+ * transforms of each z-plane run in one kernel, a cluster of 8 CTAs per plane
+ * holding the plane in distributed shared memory between the two axes; 0, the
+ * default: two passes through device memory, measured faster; same results up
+ * to FP rounding),
  * "spread_box" (1: each
  * CTA spreads a block of Morton-consecutive samples into a shared box of the
  * sub-box and adds the box's nonzero cells with 16-byte atomics; FP32, w 4-7;

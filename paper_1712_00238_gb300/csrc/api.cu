@@ -80,7 +80,7 @@ struct sd_ctx {
     int opt_spread_direct = 1;  // 0: spread by bins
     int opt_pruned = 1;         // 0: forward passes read the shifted sub-box and compute every mode
     int opt_fft_plan = -1;      // >= 0: this SD_FFT_* plan wherever it applies (not tuned)
-    int opt_inv_cluster = 1;    // 1: inverse y and x of whole z-planes in thread-block clusters (3D FP32)
+    int opt_inv_cluster = 0;    // 1: inverse y and x of whole z-planes in thread-block clusters (3D FP32)
     int opt_bin_side = DEFAULT_BIN;  // bin side of binned spreading when it is not tuned
     int opt_spread_fused = 0;   // 1: spreading fused with the forward x transform where available
     int opt_spread_box = 0;     // 1: spreading by shared boxes of sample blocks
