@@ -1486,15 +1486,17 @@ __global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_p(RowArgs<T>
 // ---------------------------------------------------------------------------
 //
 // The N x N plane (ky, kx) of one rotation at one z is shared by the IYX_CS CTAs
-// of a cluster.  CTA q first runs the inverse y transform of the N / IYX_CS
-// columns kx in [q N / IYX_CS, (q + 1) N / IYX_CS), leaving them in its shared
-// memory; after a cluster barrier it runs the inverse x transform of the rows y
-// in the same range, the first stage reading each row's inputs from the CTAs
-// that hold them (distributed shared memory); a second barrier, after those
-// reads, lets every CTA reuse its buffer for the remaining stages.  The
-// plane's intermediate never returns to device memory: one read of N^3 per
-// rotation instead of a read, a write and a read.  Output as the inverse x pass:
-// the map's rows, or each CTA's (max Re, lowest index) partial.
+// of a cluster.  CTA q runs the inverse y transform of the N / IYX_CS columns kx
+// in [q N / IYX_CS, (q + 1) N / IYX_CS) in its shared memory, then sends each
+// transformed value (y, kx) to the row buffer of the CTA that owns row y
+// (distributed shared memory stores); after one cluster barrier every CTA holds
+// its N / IYX_CS whole rows and runs the inverse x transform on them from its
+// own shared memory.  The plane's intermediate never returns to device memory:
+// one read of N^3 per rotation instead of a read, a write and a read.  Both
+// buffers take an odd pitch (lanes across lines) and the twiddles are read
+// from device memory (L1), which keeps a CTA within a third of an SM's shared
+// memory.  Output as the inverse x pass: the map's rows, or each CTA's (max Re,
+// lowest index) partial.
 
 constexpr int IYX_CS = 8;  // CTAs per cluster (the portable maximum)
 
@@ -1502,10 +1504,6 @@ template <typename T, int LEN>
 __host__ __device__ constexpr int iyx_lines() { return LEN / IYX_CS; }
 template <typename T, int LEN>
 __host__ __device__ constexpr int iyx_threads() { return cta_threads_for<LEN>(iyx_lines<T, LEN>()); }
-template <typename T, int LEN>
-__host__ __device__ constexpr int iyx_pitch() {
-    return col_pitch(LEN) > line_pitch(LEN) ? col_pitch(LEN) : line_pitch(LEN);
-}
 // The register cap of three CTAs per SM where that leaves room for a radix-24
 // stage (0: the compiler's choice).
 template <typename T, int LEN>
@@ -1519,32 +1517,34 @@ __global__ void __cluster_dims__(IYX_CS, 1, 1) __launch_bounds__(iyx_threads<T, 
     using C = cplx<T>;
     constexpr int NL = iyx_lines<T, LEN>();  // columns, then rows, of this CTA
     constexpr int NT = iyx_threads<T, LEN>();
-    constexpr int LDA = col_pitch(LEN);      // y transform: buf[column * LDA + y]
-    constexpr int LDB = line_pitch(LEN);     // x transform: padded rows
-    constexpr int NTW = tw_count(LEN);
+    constexpr int LD = col_pitch(LEN);       // both buffers: line * LD + position
     constexpr int NB1 = LEN / plan_radix(LEN, 0);
     constexpr int PL = LEN / plan_last_radix(LEN);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    C* tw = buf + NL * iyx_pitch<T, LEN>();
+    C* cols = reinterpret_cast<C*>(smem_raw);  // this CTA's columns: cols[c * LD + y]
+    C* rows = cols + NL * LD;                   // this CTA's rows: rows[y_local * LD + kx]
+    const C* tw = a.tw;
     cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    cl.barrier_arrive();  // this CTA runs (its rows may receive remote stores)
     const int q = (int)cl.block_rank();
     const int z = (int)blockIdx.x / IYX_CS;
     const int c0 = q * NL;  // this CTA's first column, then first row
-    for (int j = threadIdx.x; j < NTW; j += blockDim.x) tw[j] = a.tw[j];
-    __syncthreads();
     const C* plane = a.in + (int64_t)blockIdx.y * a.in_rot_stride + (int64_t)z * LEN * LEN;  // [ky][kx]
     // inverse y of columns c0 .. c0 + NL - 1 (lanes across columns: coalesced)
     auto load_y = [&](int line, int i, int r) -> C { return plane[(int64_t)(i + r * NB1) * LEN + c0 + line]; };
-    auto emit_y = [&](int line, int i, int r, C v) { buf[line * LDA + i + r * PL] = v; };
-    fftp_lines<C, LEN, true, NL, NT, LAY_COL, false, false, false>(buf, LDA, tw, load_y, emit_y);
-    cl.sync();  // every column of the plane is transformed
-    // inverse x of rows c0 .. c0 + NL - 1: input kx of row y sits in CTA kx / NL
-    auto load_x = [&](int line, int i, int r) -> C {
-        const int kx = i + r * NB1;
-        const C* src = cl.map_shared_rank(buf, kx / NL);
-        return src[(kx % NL) * LDA + c0 + line];
-    };
+    auto emit_y = [&](int line, int i, int r, C v) { cols[line * LD + i + r * PL] = v; };
+    fftp_lines<C, LEN, true, NL, NT, LAY_COL, false, false, false>(cols, LD, tw, load_y, emit_y);
+    __syncthreads();
+    cl.barrier_wait();  // every CTA of the cluster runs
+    // send (y, c0 + c) to the owner of row y: lanes on consecutive columns of a row
+    for (int e = threadIdx.x; e < NL * LEN; e += NT) {
+        const int y = e / NL, c = e - y * NL;
+        C* dst = cl.map_shared_rank(rows, y / NL);
+        dst[(y % NL) * LD + c0 + c] = cols[c * LD + y];
+    }
+    cl.sync();  // every row is complete
+    // inverse x of rows c0 .. c0 + NL - 1 from this CTA's row buffer
+    auto load_none = [&](int, int, int) -> C { return mk(T(0), T(0)); };
     T best = -INFINITY;
     int bidx = INT_MAX;
     const int64_t row0 = (int64_t)z * LEN + c0;  // row (z, y) of the rotation's map
@@ -1553,7 +1553,7 @@ __global__ void __cluster_dims__(IYX_CS, 1, 1) __launch_bounds__(iyx_threads<T, 
         if constexpr (MODE == ROW_INV_ARGMAX) argmax_merge(best, bidx, v.x, (int)((row0 + line) * LEN) + i + r * PL);
         else out[line * LEN + i + r * PL] = v;
     };
-    fftp_lines<C, LEN, true, NL, NT, LAY_ROW, true, false, false, 0, 1, 1>(buf, LDB, tw, load_x, emit_x);
+    fftp_lines<C, LEN, true, NL, NT, LAY_COL, false, true, false>(rows, LD, tw, load_none, emit_x);
     if constexpr (MODE == ROW_INV_ARGMAX) {
         block_argmax(best, bidx);
         if (threadIdx.x == 0) {
@@ -1826,7 +1826,7 @@ static cudaError_t inv_yx_impl(const RowArgs<T>& a, int batch, int* nparts, cuda
     if (batch == 0) return cudaSuccess;
     if (a.in_row_stride != LEN || (MODE == ROW_INV_MAP && a.out_row_stride != LEN) || a.nrows != LEN * LEN)
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(iyx_lines<T, LEN>() * iyx_pitch<T, LEN>() + tw_count(LEN)) * sizeof(C);
+    const size_t smem = (size_t)2 * iyx_lines<T, LEN>() * col_pitch(LEN) * sizeof(C);
     auto kern = k_inv_yx<T, LEN, MODE>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
