@@ -15,8 +15,6 @@
 // dropped outputs are never computed and kept ones land at constant offsets.
 #pragma once
 
-#include <cooperative_groups.h>
-
 #include "fft.cuh"
 
 namespace sd {
@@ -90,11 +88,8 @@ __device__ __forceinline__ int pidx(int j) {
 // i + r P of the last stage.  PAD: in-line padding of the shared buffer (needed
 // when a warp's lanes walk one line, LAY_ROW); column layouts use an odd pitch
 // and no padding.  SRC_SMEM: the inputs are already in buf.
-// FS = 1: the first stage's loads read other CTAs' shared memory (distributed
-// shared memory of a thread-block cluster), so a cluster barrier separates them
-// from the first writes to this CTA's buf.
 template <typename C, int LEN, bool INV, int NL, int NT, int LAY, bool PAD, bool SRC_SMEM, bool HALF_IN,
-          int S = 0, int P = 1, int FS = 0, typename Load, typename Emit>
+          int S = 0, int P = 1, typename Load, typename Emit>
 __device__ __forceinline__ void fftp_lines(C* buf, int ld, const C* tw, Load& load, Emit& emit) {
     constexpr int R = plan_radix(LEN, S);
     constexpr bool first = (S == 0);
@@ -131,8 +126,7 @@ __device__ __forceinline__ void fftp_lines(C* buf, int ld, const C* tw, Load& lo
             else dft<R, INV>(v[q]);
         }
     }
-    if constexpr (first && FS == 1) cooperative_groups::this_cluster().sync();  // every remote read first
-    else if constexpr (!first || SRC_SMEM) __syncthreads();  // every read of buf before any write
+    if constexpr (!first || SRC_SMEM) __syncthreads();  // every read of buf before any write
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int t = threadIdx.x + q * NT;
@@ -153,7 +147,7 @@ __device__ __forceinline__ void fftp_lines(C* buf, int ld, const C* tw, Load& lo
     }
     if constexpr (!last) {
         __syncthreads();
-        fftp_lines<C, LEN, INV, NL, NT, LAY, PAD, SRC_SMEM, HALF_IN, S + 1, P * R, FS>(buf, ld, tw, load, emit);
+        fftp_lines<C, LEN, INV, NL, NT, LAY, PAD, SRC_SMEM, HALF_IN, S + 1, P * R>(buf, ld, tw, load, emit);
     }
 }
 

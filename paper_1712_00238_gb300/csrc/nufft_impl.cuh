@@ -23,6 +23,8 @@
 #include <set>
 #include <tuple>
 
+#include <cooperative_groups.h>
+
 #include "fft.cuh"
 #include "fftp.cuh"
 #include "kernels.cuh"
