@@ -73,10 +73,9 @@ def parse_args():
                     help="with --autotune 0: 1 spreads each block of Morton-consecutive samples into a shared box")
     ap.add_argument("--inverse-cluster", type=int, default=0, choices=[0, 1],
                     help="1: inverse y and x of each z-plane in one cluster kernel (3D FP32); 0: two passes")
-    ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+    ap.add_argument("--fft-plan", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="forward-pass FFT plan: -1 the autotuner's (or the pruned default), 0 full, 1 pruned, "
-                         "2 pruned with narrow column CTAs, 3 pruned with wide column CTAs, 4 pruned with a "
-                         "prefetching persistent fused pass")
+                         "2 pruned with narrow column CTAs, 3 pruned with wide column CTAs")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library times candidate plans (batch, spreading, FFT plan) once per geometry")
     ap.add_argument("--rotations", type=int, default=0, help="use only the first R rotations (profiling cases)")
@@ -502,14 +501,12 @@ def plain_speedup(args, ctx, sd, torch, dev, stream, w, grid, devin, cand):
 
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE,
-# SD_FFT_PRUNED_PIPE)
+# the forward-pass FFT plans (SD_FFT_FULL, SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE)
 FFT_PLAN_TEXT = {
     0: "full: shifted sub-box padded to n, every output of each line",
     1: "pruned: zero upper half skipped, only the N kept modes; shift as a phase in W",
     2: "pruned, half the columns per CTA in the forward y and fused z passes",
     3: "pruned, twice the columns per CTA in the forward y and fused z passes",
-    4: "pruned; fused z pass by persistent CTAs prefetching their next column block (cp.async)",
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the

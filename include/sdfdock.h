@@ -142,7 +142,7 @@ const char* sd_last_error(const sd_ctx* ctx);
  * the shift applied as a phase in the product table; 0: the shifted sub-box and
  * every mode; results are the same up to FP rounding), "fft_plan" (-1, the
  * default: the autotuner's choice, else SD_FFT_PRUNED where the pruned passes
- * apply; 0..4: that SD_FFT_* plan wherever it applies, never tuned),
+ * apply; 0..3: that SD_FFT_* plan wherever it applies, never tuned),
  * "inverse_cluster" (1: in 3D FP32 searches with N in {32, 48, 64, 96, 128,
  * 192, 256} returning maps or one candidate per rotation, the inverse y and x
  * transforms of each z-plane run in one kernel, a cluster of 8 CTAs per plane
@@ -335,16 +335,11 @@ int sd_score_pairs(sd_ctx* ctx, const sd_pair_job* jobs, int64_t n_jobs, sd_pair
  *   SD_FFT_PRUNED_NARROW  as PRUNED, with half the columns per CTA in the
  *                         forward y and fused last-axis passes (FP32, n 128..384)
  *   SD_FFT_PRUNED_WIDE    as PRUNED, with twice the columns per CTA there
- *                         (FP32, n 128..384)
- *   SD_FFT_PRUNED_PIPE    as PRUNED, with the fused last-axis pass run by
- *                         persistent CTAs that copy their next column block's
- *                         input into shared memory (cp.async) while they
- *                         finish the current one */
+ *                         (FP32, n 128..384) */
 #define SD_FFT_FULL 0
 #define SD_FFT_PRUNED 1
 #define SD_FFT_PRUNED_NARROW 2
 #define SD_FFT_PRUNED_WIDE 3
-#define SD_FFT_PRUNED_PIPE 4
 
 /* The plan a search of n_r rotations of `moving` on grid g would run with now:
  * rotations per batch, the bin side of binned spreading (0: direct; 1:
@@ -368,7 +363,7 @@ int sd_tune_export(sd_ctx* ctx, char* buf, int64_t cap, int64_t* len);
  * geometries skip the timing trials (an entry without "fft" takes
  * SD_FFT_PRUNED; a plan that does not apply to a job is replaced by the job's
  * default there).  A text that is not such a table, or an entry with batch
- * outside [1, 64], spread_bins not 0, 1, 2, 8, 12 or 16, or fft not 0 to 4,
+ * outside [1, 64], spread_bins not 0, 1, 2, 8, 12 or 16, or fft not 0 to 3,
  * is SD_ERR_ARG and leaves the cache unchanged. */
 int sd_tune_import(sd_ctx* ctx, const char* json);
 

@@ -61,7 +61,7 @@ struct Plan {      // launch plan of one scoring job
     int bins = 0;  // bin side (8, 12, 16) of bin-sorted spreading, 0: direct,
                    // 1: spreading fused with the forward x transform (SPREAD_X),
                    // 2: shared boxes of sample blocks (SPREAD_BOX)
-    int fft = SD_FFT_PRUNED;  // forward-pass plan (SD_FFT_*)
+    int fft = SD_FFT_PRUNED;  // forward-pass plan (SD_FFT_FULL / _PRUNED / _PRUNED_NARROW / _PRUNED_WIDE)
 };
 
 struct sd_ctx {
@@ -821,8 +821,7 @@ static bool spread_x_ok(const sd_ctx* ctx, const Search<T>& S) {
 template <typename T>
 static bool fft_plan_ok(const Search<T>& S, int fft) {
     return fft == SD_FFT_FULL || (fft == SD_FFT_PRUNED && S.prunable) ||
-           ((fft == SD_FFT_PRUNED_NARROW || fft == SD_FFT_PRUNED_WIDE) && S.alt_cols) ||
-           (fft == SD_FFT_PRUNED_PIPE && S.prunable);
+           ((fft == SD_FFT_PRUNED_NARROW || fft == SD_FFT_PRUNED_WIDE) && S.alt_cols);
 }
 
 // The plan a job starts from: the forced one if it applies, else pruned where
@@ -943,7 +942,6 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
         const bool pruned = S.plan.fft != SD_FFT_FULL;
         const int lines = S.plan.fft == SD_FFT_PRUNED_NARROW ? LINES_NARROW
                           : (S.plan.fft == SD_FFT_PRUNED_WIDE ? LINES_WIDE : LINES_STD);
-        const int lines_last = S.plan.fft == SD_FFT_PRUNED_PIPE ? LINES_PIPE : lines;
         const int mx = pruned ? ROW_FWD_P : ROW_FWD;
         const int my = pruned ? COL_FWD_P : COL_FWD;
         const int mf = pruned ? COL_FUSED_P : COL_FUSED;
@@ -971,7 +969,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             }
             {
                 PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, lines_last));
+                CK(ctx, pass_last<T>(mf, G, S.tw, S.b0, S.e0, S.b1, S.e1, Wp, b, s, lines));
             }
             if (!iyx) {
                 PassTimer pt(ctx, SD_PASS_INV_Y, s, timed);
@@ -981,7 +979,7 @@ static int search_enqueue(sd_ctx* ctx, const Search<T>& S, int64_t r_lo, int64_t
             fin_rs = S.e1;
         } else {
             PassTimer pt(ctx, SD_PASS_FUSED, s, timed);
-            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, Wp, b, s, lines_last));
+            CK(ctx, pass_last<T>(mf, G, S.tw, S.b1, S.e1, S.b0, S.e0, Wp, b, s, lines));
             fin = S.b0;
             fin_rs = S.e0;
         }
@@ -1098,7 +1096,7 @@ static int autotune(sd_ctx* ctx, Search<T>* S, cudaStream_t st) {
         if ((rc = trial(c)) != SD_OK) break;
     if (rc == SD_OK && ctx->opt_fft_plan < 0) {
         const Plan first = best;
-        for (int f : {SD_FFT_PRUNED, SD_FFT_PRUNED_PIPE, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE, SD_FFT_FULL}) {
+        for (int f : {SD_FFT_PRUNED, SD_FFT_PRUNED_NARROW, SD_FFT_PRUNED_WIDE, SD_FFT_FULL}) {
             Plan c = first;
             c.fft = f;
             // spreading fused with the x pass exists only under the pruned plans
@@ -1382,7 +1380,7 @@ int sd_set_option(sd_ctx* ctx, const char* key, int64_t value) {
         if (value != 8 && value != 12 && value != 16) return fail(ctx, SD_ERR_ARG, "spread_bin_side: 8, 12 or 16");
         ctx->opt_bin_side = (int)value;
     } else if (!strcmp(key, "fft_plan")) {
-        if (value < -1 || value > SD_FFT_PRUNED_PIPE) return fail(ctx, SD_ERR_ARG, "fft_plan: -1 to 4");
+        if (value < -1 || value > SD_FFT_PRUNED_WIDE) return fail(ctx, SD_ERR_ARG, "fft_plan: -1 to 3");
         ctx->opt_fft_plan = (int)value;
     }
     else if (!strcmp(key, "spread_fused")) ctx->opt_spread_fused = (int)value;
@@ -1650,7 +1648,7 @@ int sd_tune_import(sd_ctx* ctx, const char* json) {
         const int nf = sscanf(q, "\", \"batch\": %d, \"spread_bins\": %d, \"fft\": %d}", &B, &bins, &fft);
         if (nf < 2 || B < 1 || B > 64 ||
             (bins != 0 && bins != SPREAD_X && bins != SPREAD_BOX && bins != 8 && bins != 12 && bins != 16) ||
-            fft < SD_FFT_FULL || fft > SD_FFT_PRUNED_PIPE)
+            fft < SD_FFT_FULL || fft > SD_FFT_PRUNED_WIDE)
             return fail(ctx, SD_ERR_ARG, "tune_import: malformed entry for key %s", key.c_str());
         got[key] = Plan{B, bins, fft};
         p = q;

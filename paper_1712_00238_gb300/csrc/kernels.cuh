@@ -175,9 +175,7 @@ struct ColArgs {
     int rot_fastest;                    // COL_FUSED: grid (batch, column blocks), W reused from L2
     int lines;                          // COL_FWD_P / COL_FUSED_P: columns per CTA (LINES_*)
 };
-// standard, half, twice; LINES_PIPE: the fused pass as persistent CTAs prefetching
-// their next column block's input (standard width)
-enum { LINES_STD = 0, LINES_NARROW = 1, LINES_WIDE = 2, LINES_PIPE = 3 };
+enum { LINES_STD = 0, LINES_NARROW = 1, LINES_WIDE = 2 };  // standard, half, twice
 template <typename T> cudaError_t launch_cols(int mode, const ColArgs<T>& a, int batch, cudaStream_t st);
 
 // twiddles exp(-2 pi i j / len), computed in FP64

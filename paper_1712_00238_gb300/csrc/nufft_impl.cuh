@@ -1405,88 +1405,6 @@ __global__ void __launch_bounds__(cta_threads_for<LENF>(TC), MB) k_cols_fused_p(
     cols_fused_p_body<T, LENF, TC>(a);
 }
 
-// The same pass as persistent CTAs that overlap the input of the next column
-// block with the inverse transform of the current one.  A CTA takes work items
-// (column block, rotation) in rotation-fastest order, so the CTAs working at the
-// same time share W' blocks in L2.  It copies the s input rows of its next
-// item's columns into a staging buffer with cp.async as soon as the current
-// item's forward transform has read them, runs the current item's inverse
-// transform meanwhile, and reads the next forward transform's first stage from
-// the staging buffer.  Line buffer, staging buffer and twiddles stay within a
-// third of an SM's shared memory at n = 384 for s <= 164.  Full column blocks
-// only (ncols a multiple of TC).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-template <typename T, int TC>
-__device__ __forceinline__ void fused_stage_rows(const ColArgs<T>& a, cplx<T>* stg, int64_t w, int batch) {
-    using C = cplx<T>;
-    constexpr int CPR = TC * (int)sizeof(C) / 16;  // 16-byte chunks per row of a column block
-    static_assert(TC * sizeof(C) % 16 == 0, "column block rows must be whole 16-byte chunks");
-    const int b = (int)(w % batch);
-    const int64_t col0 = (w / batch) * TC;
-    const C* in = a.in + (int64_t)b * a.in_rot_stride + col0;
-    const int n = a.len_in * CPR;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int pos = k / CPR, part = k - pos * CPR;
-        cp_async16(reinterpret_cast<char*>(stg + pos * TC) + part * 16,
-                   reinterpret_cast<const char*>(in + (int64_t)pos * a.ncols) + part * 16);
-    }
-    cp_async_commit();
-}
-
-template <typename T, int LENF, int MB, int TC>
-__global__ void __launch_bounds__(cta_threads_for<LENF>(TC), MB)
-    k_cols_fused_pp(ColArgs<T> a, int batch, int64_t items) {
-    using C = cplx<T>;
-    constexpr int LENI = LENF / 2;
-    constexpr int NT = cta_threads_for<LENF>(TC);
-    constexpr int LD = col_pitch(LENF);
-    constexpr int NB1 = LENF / plan_radix(LENF, 0);
-    constexpr int PI = LENI / plan_last_radix(LENI);
-    static_assert((TC * LD * sizeof(C)) % 16 == 0, "staging buffer must start 16-byte aligned");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    C* stg = buf + TC * LD;  // the staged input: stg[pos * TC + column], pos < s
-    const int ncols = a.ncols, s = a.len_in;
-    C* twF = stg + (size_t)s * TC;  // twiddles, copied once
-    C* twI = twF + tw_count(LENF);
-    const C zero = mk(T(0), T(0));
-    int64_t w = blockIdx.x;
-    if (w < items) fused_stage_rows<T, TC>(a, stg, w, batch);
-    for (int j = threadIdx.x; j < tw_count(LENF); j += blockDim.x) twF[j] = a.twF[j];
-    for (int j = threadIdx.x; j < tw_count(LENI); j += blockDim.x) twI[j] = a.twI[j];
-#pragma unroll 1
-    for (; w < items; w += gridDim.x) {
-        const int b = (int)(w % batch);
-        const int col0 = (int)(w / batch) * TC;
-        C* out = a.out + (int64_t)b * a.out_rot_stride + col0;
-        const C* Wc = a.W + col0;
-        cp_async_wait_all();
-        __syncthreads();  // staged rows visible; the previous item's reads of buf are done
-        auto load = [&](int line, int i, int r) -> C {
-            const int pos = i + r * NB1;
-            return pos < s ? stg[pos * TC + line] : zero;
-        };
-        auto emit_fwd = [&](int line, int i, int r, C v) {
-            if (kept_out<LENF>(r)) {
-                const int kp = i + kept_slot<LENF>(r);
-                buf[line * LD + kp] = cmul(v, Wc[kp * ncols + line]);
-            }
-        };
-        fftp_lines<C, LENF, false, TC, NT, LAY_COL, false, false, true>(buf, LD, twF, load, emit_fwd);
-        __syncthreads();  // the products are in buf; the staging buffer is free
-        if (w + gridDim.x < items) fused_stage_rows<T, TC>(a, stg, w + gridDim.x, batch);
-        auto emit_out = [&](int line, int i, int r, C v) { out[(i + r * PI) * ncols + line] = v; };
-        fftp_lines<C, LENI, true, TC, NT, LAY_COL, false, true, false>(buf, LD, twI, load, emit_out);
-    }
-    cp_async_wait_all();  // nothing in flight when the CTA exits
-}
-
 // Inverse y (3D), in place: columns of N points, full input and output.  Each
 // CTA reads its columns completely in the first stage before any write.
 template <typename T, int LEN>
@@ -1867,48 +1785,9 @@ static cudaError_t cols_fused_p_launch(const ColArgs<T>& a, int batch, cudaStrea
     return cudaGetLastError();
 }
 
-// Register bound of the persistent fused pass: the compiler's choice would take
-// up to 128 registers a thread; FP32 384-point CTAs (384 threads) take 2 per SM,
-// 512-point ones 1, shorter ones (256 threads at most) 4.
-template <typename T, int LENF>
-__host__ __device__ constexpr int pipe_min_ctas() {
-    return sizeof(T) != 4 ? 0 : (LENF == 512 ? 1 : (LENF == 384 ? 2 : 4));
-}
-
-template <typename T, int LENF, int TC, int MB>
-static cudaError_t cols_fused_pp_launch(const ColArgs<T>& a, int batch, cudaStream_t st) {
-    using C = cplx<T>;
-    if (batch == 0 || a.ncols == 0) return cudaSuccess;
-    if (a.nouter != 1 || a.ncols % TC != 0 || a.len_in > LENF / 2 || a.in_rot_stride % 2 != 0 ||
-        (reinterpret_cast<uintptr_t>(a.in) & 15) != 0)
-        return cudaErrorInvalidValue;
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 1;
-    }
-    const int64_t items = (int64_t)(a.ncols / TC) * batch;
-    const size_t smem =
-        (size_t)(TC * col_pitch(LENF) + (size_t)a.len_in * TC + tw_count(LENF) + tw_count(LENF / 2)) * sizeof(C);
-    auto kern = k_cols_fused_pp<T, LENF, MB, TC>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cta_threads_for<LENF>(TC), smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(items, (int64_t)std::max(per_sm, 1) * sms);
-    kern<<<(unsigned)grid, cta_threads_for<LENF>(TC), smem, st>>>(a, batch, items);
-    note_launch();
-    return cudaGetLastError();
-}
-
 template <typename T, int LENF>
 static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_t st) {
     static_assert(prunable_len(LENF), "length not prunable");
-    if (a.lines == LINES_PIPE)
-        return cols_fused_pp_launch<T, LENF, lines_per_cta<T, LENF>(), pipe_min_ctas<T, LENF>()>(a, batch, st);
     if constexpr (alt_cols_ok<T, LENF>()) {
         if (a.lines == LINES_NARROW)
             return cols_fused_p_launch<T, LENF, alt_lines<T, LENF, 0>(), alt_min_ctas<T, LENF, 2, 0>()>(a, batch, st);

@@ -123,7 +123,7 @@ def test_tuned_plans_export_and_import():
     table = json.loads(text)
     assert table["sdfdock_plans"] == 1 and len(table["plans"]) == 1
     assert table["plans"][0]["batch"] >= 1 and table["plans"][0]["spread_bins"] in (0, 1, 2, 8, 12, 16)
-    assert table["plans"][0]["fft"] == plan["fft_plan"] and plan["fft_plan"] in (0, 1, 2, 3, 4)
+    assert table["plans"][0]["fft"] == plan["fft_plan"] and plan["fft_plan"] in (0, 1, 2, 3)
 
     ctx2 = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
     fx2, mv2, _, _, _ = _jobs(ctx2)[2]
@@ -134,7 +134,7 @@ def test_tuned_plans_export_and_import():
     assert json.loads(ctx2.tune_export()) == table
     # malformed tables are refused and leave the cache as it was
     for bad in ("{}", re.sub(r'"batch": \d+', '"batch": 0', text), re.sub(r'"spread_bins": \d+', '"spread_bins": 7', text),
-                re.sub(r'"fft": \d+', '"fft": 5', text)):
+                re.sub(r'"fft": \d+', '"fft": 4', text)):
         with pytest.raises(sd.SdError) as e:
             ctx2.tune_import(bad)
         assert e.value.code == sd.SD_ERR_ARG

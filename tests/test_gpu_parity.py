@@ -232,16 +232,16 @@ def test_pruned_and_full_forward_passes_agree(name, prec, N):
     g = grid_of(w, N)
     alt = prec == "f32" and 128 <= 2 * N <= 384
     got = {}
-    for plan in (1, 0, 2, 3, 4):
+    for plan in (1, 0, 2, 3):
         ctx.set_option("fft_plan", plan)
         # a plan that does not apply falls back to the pruned default
-        assert ctx.search_plan(mv, g, w.n_rot)["fft_plan"] == (plan if plan in (0, 1, 4) or alt else 1)
+        assert ctx.search_plan(mv, g, w.n_rot)["fft_plan"] == (plan if plan < 2 or alt else 1)
         got[plan] = ctx.score_maps(fx, mv, q, g).cpu().numpy()
     ctx.set_option("fft_plan", -1)
     ref = oracle_maps(p1, c1, p2, c2, w.quats, N, w.L, w.sigma_g)
     for r in range(w.n_rot):
         assert rel_err(got[1][r], got[0][r]) < (1e-12 if prec == "f64" else 2e-6), r
-        for alt_plan in (2, 3, 4):
+        for alt_plan in (2, 3):
             assert rel_err(got[alt_plan][r], got[1][r]) < (1e-12 if prec == "f64" else 2e-6), (alt_plan, r)
         assert rel_err(got[1][r], ref[r]) < TOL[prec], r
     ctx.close()
