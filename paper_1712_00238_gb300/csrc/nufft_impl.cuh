@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(BOX_SPC) k_spread_box(SpreadArgs<float> a) {
 // from the tile and writes the N kept modes of each row.  No sub-box is stored,
 // cleared or re-read, and no global atomic is issued.
 
-constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 10, SX_NT = 256, SX_CHUNK = 64;
+constexpr int SX_W = 6, SX_TY = SPREADX_TY, SX_TZ = SPREADX_TZ, SX_TR = 6, SX_NT = 256, SX_CHUNK = 64;
 static_assert(SX_TY >= SX_W - 1 && SX_TZ >= SX_W - 1, "a tap box must meet at most two bins per axis");
 static_assert((SX_TY * SX_TZ) % SX_TR == 0, "rows per FFT group must divide the rows of a bin");
 // staged record: w[axis][W] | origin[3] | c * scale (pair)
@@ -845,13 +845,13 @@ constexpr int SX_REC = SX_O_C + 2;
 // distinct banks.
 __host__ __device__ inline int spread_x_pitch(int s) { return s + ((6 - s % 32) + 32) % 32; }
 
-// The larger of the staging records and the FFT line buffer (the twiddles are
-// read from device memory, through L1, to keep three CTAs on an SM at n = 384).
 template <int LEN>
 __host__ __device__ constexpr size_t spread_x_smem_fixed() {
-    return (size_t)SX_CHUNK * SX_REC * sizeof(float) > (size_t)SX_TR * line_pitch(LEN) * sizeof(float2)
-               ? (size_t)SX_CHUNK * SX_REC * sizeof(float)
-               : (size_t)SX_TR * line_pitch(LEN) * sizeof(float2);
+    // twiddles + the larger of the staging records and the FFT line buffer
+    return (size_t)tw_count(LEN) * sizeof(float2) +
+           ((size_t)SX_CHUNK * SX_REC * sizeof(float) > (size_t)SX_TR * line_pitch(LEN) * sizeof(float2)
+                ? (size_t)SX_CHUNK * SX_REC * sizeof(float)
+                : (size_t)SX_TR * line_pitch(LEN) * sizeof(float2));
 }
 __host__ inline size_t spread_x_smem(int len, int px) {
     size_t fixed = 0;
@@ -886,6 +886,7 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
     constexpr int W = SX_W, TY = SX_TY, TZ = SX_TZ, TR = SX_TR, NT = SX_NT, CHUNK = SX_CHUNK, REC = SX_REC;
     constexpr int ROWS = TY * TZ;
     constexpr int LD = line_pitch(LEN);
+    constexpr int NTW = tw_count(LEN);
     constexpr int NB1 = LEN / plan_radix(LEN, 0);
     constexpr int NH = LEN / 2;
     constexpr int NWARP = NT / 32;
@@ -894,8 +895,9 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
     extern __shared__ __align__(16) unsigned char sx_raw[];
     int* tre = reinterpret_cast<int*>(sx_raw);
     int* tim = tre + ROWS * px;
-    float* stage = reinterpret_cast<float*>(tim + ROWS * px);
-    float2* buf = reinterpret_cast<float2*>(tim + ROWS * px);  // the same memory, after the accumulation
+    float2* tw = reinterpret_cast<float2*>(tim + ROWS * px);
+    float* stage = reinterpret_cast<float*>(tw + NTW);
+    float2* buf = reinterpret_cast<float2*>(tw + NTW);  // the same memory, after the accumulation
     __shared__ float Rm[9];
     __shared__ float wred[NWARP][2];
     __shared__ unsigned char divtab[7][W * W];  // (rho / ny) << 4 | rho % ny
@@ -909,6 +911,7 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
         tre[i] = 0;
         tim[i] = 0;
     }
+    for (int j = tid; j < NTW; j += NT) tw[j] = twg[j];
     for (int i = tid; i < 7 * W * W; i += NT) {
         const int ny = i / (W * W), rho = i % (W * W);
         divtab[ny][rho] = ny ? (unsigned char)(((rho / ny) << 4) | (rho % ny)) : 0;
@@ -1060,7 +1063,7 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
             if (kept_out<LEN>(r) && y < s && z < s)
                 outb[((int64_t)z * s + y) * NH + i + kept_slot<LEN>(r)] = v;
         };
-        fftp_lines<float2, LEN, false, TR, NT, LAY_ROW, true, false, true>(buf, LD, twg, load, emit);
+        fftp_lines<float2, LEN, false, TR, NT, LAY_ROW, true, false, true>(buf, LD, tw, load, emit);
         __syncthreads();  // buf is rewritten by the next group
     }
 }
