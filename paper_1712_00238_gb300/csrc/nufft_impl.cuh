@@ -263,6 +263,20 @@ __device__ __forceinline__ void sample_origin(const SpreadArgs<T>& a, const T* R
     for (int d = 0; d < D; ++d) org[d] = wrap_index((int)ceil(y[d] * a.inv_h - half) + a.s_h, a.s);
 }
 
+// A slot in the sample's bin (bin >= 0; -1 for none): the lanes of a warp with
+// the same bin take consecutive slots from one atomic add by the lowest of them
+// (a shape's samples are in Morton order, so a warp's samples share few bins).
+// Every lane of the warp must call it.
+__device__ __forceinline__ int bin_rank(int* count, int bin) {
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    const int lane = (int)(threadIdx.x & 31);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (lane == leader && bin >= 0) base = atomicAdd(count + bin, __popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(same & ((1u << lane) - 1u));
+}
+
 template <typename T, int D, int W, int TB>
 __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) {
     __shared__ T Rm[9];
@@ -270,15 +284,21 @@ __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) 
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.m) return;
-    int org[D];
-    sample_origin<T, D, W>(a, Rm, j, org);
-    int bin = 0;
+    const bool live = j < a.m;
+    int bin = -1;
+    if (live) {
+        int org[D];
+        sample_origin<T, D, W>(a, Rm, j, org);
+        bin = 0;
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / TB;
-    const int64_t o = (int64_t)b * a.m + j;
-    bn.bin_of[o] = bin;
-    bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
+        for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / TB;
+    }
+    const int rank = bin_rank(bn.count + (int64_t)b * bn.nbins, bin);
+    if (live) {
+        const int64_t o = (int64_t)b * a.m + j;
+        bn.bin_of[o] = bin;
+        bn.rank[o] = rank;
+    }
 }
 
 // Exclusive scan of the bin counts of one rotation (one CTA of 1024 threads).
@@ -870,14 +890,21 @@ __global__ void __launch_bounds__(256) k_bin_count_yz(SpreadArgs<T> a, BinArgs b
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.m) return;
-    int org[D];
-    sample_origin<T, D, W>(a, Rm, j, org);
-    const int bin = (org[2] / tz) * bn.nb + org[1] / ty;
-    const int64_t o = (int64_t)b * a.m + j;
-    bn.bin_of[o] = bin;
-    bn.org[o] = org[0] | (org[1] << 10) | (org[2] << 20);  // the spreading uses this very origin
-    bn.rank[o] = atomicAdd(bn.count + (int64_t)b * bn.nbins + bin, 1);
+    const bool live = j < a.m;
+    int bin = -1, packed = 0;
+    if (live) {
+        int org[D];
+        sample_origin<T, D, W>(a, Rm, j, org);
+        bin = (org[2] / tz) * bn.nb + org[1] / ty;
+        packed = org[0] | (org[1] << 10) | (org[2] << 20);
+    }
+    const int rank = bin_rank(bn.count + (int64_t)b * bn.nbins, bin);
+    if (live) {
+        const int64_t o = (int64_t)b * a.m + j;
+        bn.bin_of[o] = bin;
+        bn.org[o] = packed;  // the spreading uses this very origin
+        bn.rank[o] = rank;
+    }
 }
 
 template <int LEN>
