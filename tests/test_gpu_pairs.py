@@ -145,3 +145,21 @@ def test_tuned_plans_export_and_import():
     assert ctx2.search_plan(mv2, g, qd.shape[0])["fft_plan"] in (1, plan["fft_plan"])
     ctx.close()
     ctx2.close()
+
+
+def test_plan_options_reject_bad_values():
+    # the plan options take only their documented values; a refused value leaves
+    # the option as it was
+    ctx = sd.Context(3, "f32", 0, sigma_g=SIGMA_G)
+    fx, mv, q, g, _ = _jobs(ctx)[2]
+    before = ctx.search_plan(mv, g, 9)
+    for key, value in (("fft_plan", 5), ("fft_plan", -2), ("spread_bin_side", 10), ("spread_bin_side", 0)):
+        with pytest.raises(sd.SdError) as e:
+            ctx.set_option(key, value)
+        assert e.value.code == sd.SD_ERR_ARG
+    assert ctx.search_plan(mv, g, 9) == before
+    ctx.set_option("spread_direct", 0)
+    for side in (8, 12, 16):
+        ctx.set_option("spread_bin_side", side)
+        assert ctx.search_plan(mv, g, 9)["spread_bins"] == side
+    ctx.close()
