@@ -515,9 +515,12 @@ FFT_PLAN_TEXT = {
 # 20-rotation launch of the pruned fused pass read 976,803,840 B and wrote
 # 1,081,333,248 B; its product table W' (N^3 complex, 56,623,104 B) is read from
 # DRAM once per launch (the launch's other rotations hit L2), the rest scales
-# with the rotations.  A pass of another shape reports null.
+# with the rotations.  Peg-in-bore: one 34-rotation launch read 552,969,728 B and
+# wrote 529,623,040 B; its W' (16.8 MB) stays mostly in L2, so the model is per
+# rotation only.  A pass of another shape reports null.
 TRAFFIC_MODEL: dict = {
     ("fused", 156, 192): ((976803840 - 56623104 + 1081333248) / 20, 56623104),
+    ("fused", 108, 128): ((552969728 + 529623040) / 34, 0),
 }
 
 
