@@ -422,7 +422,7 @@ def run_ours(args):
                    "rotations": n_rot, "translations": w.N ** w.dim, "sub_box": s,
                    "batch": plan_used.get("batch"), "autotune": bool(args.autotune),
                    "graph": bool(args.graph and not args.plain), "plain": bool(args.plain),
-                   "spread": ("fused with the forward x transform (5x6 row bins, shared fixed-point tile)"
+                   "spread": ("fused with the forward x transform (6x6 row bins, shared fixed-point tile)"
                               if plan_used.get("spread_bins") == 1 else
                               "shared boxes of 128 Morton-consecutive samples, 16-byte pair atomics"
                               if plan_used.get("spread_bins") == 2 else

@@ -105,9 +105,10 @@ template <typename T> cudaError_t launch_spread_box(const SpreadArgs<T>& a, int 
 // bins of SPREADX_TY x SPREADX_TZ cells (bn.nb = bins along y, nbz along z,
 // bn.nbins = nb * nbz), then each bin's CTA writes the N kept x modes of its
 // rows to out (batch x s^2 rows x N, row (y, z) at z s + y).  No sub-box.  Both
-// sides are at least w - 1, so a tap box meets at most 2 x 2 bins; 5 x 6 rows
-// keep a CTA's shared memory to three CTAs per SM at n = 384.
-constexpr int SPREADX_TY = 5, SPREADX_TZ = 6;
+// sides are at least w - 1, so a tap box meets at most 2 x 2 bins; 6 x 6 rows
+// keep a CTA's shared memory to three CTAs per SM at n = 384 (measured faster
+// than 5 x 6).
+constexpr int SPREADX_TY = 6, SPREADX_TZ = 6;
 template <typename T>
 cudaError_t launch_spread_x(const SpreadArgs<T>& a, const BinArgs& bn, int nbz, cplx<T>* out, int64_t out_rot_stride,
                             const cplx<T>* tw, int batch, cudaStream_t st);
