@@ -190,7 +190,7 @@ template <typename T>
 __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
     __shared__ double yx[RS_TILE], yy[RS_TILE], yz[RS_TILE], cr[RS_TILE], ci[RS_TILE];
     __shared__ double qx1[RS_TILE], qy1[RS_TILE], qz1[RS_TILE], ar1[RS_TILE], ai1[RS_TILE];
-    __shared__ float fx[RS_TILE], fy[RS_TILE], fz[RS_TILE];
+    __shared__ float4 fxyz[RS_TILE];  // FP32 copies of the moved samples for the screen (one load each)
     __shared__ unsigned short qpair[RS_WARPS][RS_QUEUE][2];  // (fixed slot, moving slot)
     __shared__ float wlo[RS_WARPS][3], whi[RS_WARPS][3];
     __shared__ float blo[3], bhi[3];
@@ -292,11 +292,11 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
             if (j < a.m2) {
                 const double4 y = moved[j];
                 yx[threadIdx.x] = y.x; yy[threadIdx.x] = y.y; yz[threadIdx.x] = y.z;
-                fx[threadIdx.x] = (float)y.x; fy[threadIdx.x] = (float)y.y; fz[threadIdx.x] = (float)y.z;
+                fxyz[threadIdx.x] = make_float4((float)y.x, (float)y.y, (float)y.z, 0.f);
                 cr[threadIdx.x] = a.c2[j].x; ci[threadIdx.x] = a.c2[j].y;
-                mlo[0] = mhi[0] = fx[threadIdx.x];
-                mlo[1] = mhi[1] = fy[threadIdx.x];
-                mlo[2] = mhi[2] = fz[threadIdx.x];
+                mlo[0] = mhi[0] = (float)y.x;
+                mlo[1] = mhi[1] = (float)y.y;
+                mlo[2] = mhi[2] = (float)y.z;
             }
             for (int d = 0; d < 3; ++d)
                 for (int off = 16; off > 0; off >>= 1) {
@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(RS_TILE) k_rescore(RescoreArgs<T> a) {
             }
             bool pass = false;
             if (live) {
-                const float dxf = fx[k] - pxf, dyf = fy[k] - pyf, dzf = fz[k] - pzf;
+                const float4 f = fxyz[k];
+                const float dxf = f.x - pxf, dyf = f.y - pyf, dzf = f.z - pzf;
                 pass = dxf * dxf + dyf * dyf + dzf * dzf <= cut2f;
             }
             const unsigned m = __ballot_sync(0xffffffffu, pass);
