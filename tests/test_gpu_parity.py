@@ -458,6 +458,39 @@ def test_score_grad_matches_oracle(name, prec, N):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_score_grad_at_the_refinement_grid(prec):
+    # the refinement workload's grid (docking pair, N = 192 on L = 153.6, n = 384,
+    # sigma_g = 0.6) on seeded 64 x 64-sample subsets of its SDF samples with
+    # seeded weights: score and gradient at 8 poses against the oracle's pair sums
+    # over the band-limited kernel (each axis a cosine series)
+    w = configs.docking_2000_500(n_rot=1)
+    rng = np.random.default_rng(64)
+    p1 = w.fixed.query.pos[np.sort(rng.choice(w.fixed.query.m, 64, replace=False))]
+    p2 = w.moving.query.pos[np.sort(rng.choice(w.moving.query.m, 64, replace=False))]
+    c1, c2 = synthetic_weights(64, 5), synthetic_weights(64, 6)
+    ctx = sd.Context(3, prec, 0, sigma_g=w.sigma_g)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(c2))
+    P = 8
+    qs = rotations.random_uniform(P, 21)
+    # each pose puts one seeded pair of samples within 0.3 A of each other, so the
+    # scores carry Gaussian peaks and not only the band limit's ripple
+    a_i, b_i = rng.integers(0, 64, P), rng.integers(0, 64, P)
+    off = rotations.random_ball(P, 0.3, 22, 3)
+    ts = np.stack([p1[a_i[i]] - oscore.rotation_matrix(qs[i], 3) @ p2[b_i[i]] + off[i] for i in range(P)])
+    real = torch.float64 if prec == "f64" else torch.float32
+    s, dq, dt = ctx.score_grad(fx, mv, sd.Grid(w.N, w.L), torch.tensor(qs, dtype=real, device="cuda"),
+                               torch.tensor(ts, dtype=real, device="cuda"))
+    s, dq, dt = s.cpu().numpy(), dq.cpu().numpy(), dt.cpu().numpy()
+    ref = [oscore.pair_grad_fN(p1, c1, p2, c2, qs[i], ts[i], w.N, w.L, w.sigma_g) for i in range(P)]
+    tol = TOL[prec]
+    assert rel_err(s, np.array([r[0] for r in ref])) < tol
+    assert rel_err(dt, np.array([r[1] for r in ref])) < tol
+    assert rel_err(dq, np.array([r[2] for r in ref])) < tol
+    ctx.close()
+
+
 def test_score_grad_equals_map_on_grid_points():
     w = configs.tiny_3d()
     p1, c1, p2, c2 = oracle_weights("tiny_3d")
