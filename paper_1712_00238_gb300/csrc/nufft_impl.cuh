@@ -1489,10 +1489,23 @@ __device__ __forceinline__ void rows_inv_p_body(const RowArgs<T>& a) {
     T best = -INFINITY;
     int bidx = INT_MAX;
     C* out = (MODE == ROW_INV_MAP) ? a.out + (int64_t)blockIdx.y * a.out_rot_stride + (int64_t)row0 * LEN : nullptr;
+    // one last-stage butterfly per thread: its outputs come in increasing index
+    // order, so a strict comparison already keeps the lowest index of equal values
+    constexpr bool one_bfly = TR * (LEN / plan_last_radix(LEN)) <= cta_threads<T, LEN>();
     auto emit = [&](int line, int i, int r, C v) {
         if (line >= nrows) return;
-        if constexpr (MODE == ROW_INV_ARGMAX) argmax_merge(best, bidx, v.x, (row0 + line) * LEN + i + r * PL);
-        else out[line * LEN + i + r * PL] = v;
+        if constexpr (MODE == ROW_INV_ARGMAX) {
+            if constexpr (one_bfly) {
+                if (v.x > best) {
+                    best = v.x;
+                    bidx = (row0 + line) * LEN + i + r * PL;
+                }
+            } else {
+                argmax_merge(best, bidx, v.x, (row0 + line) * LEN + i + r * PL);
+            }
+        } else {
+            out[line * LEN + i + r * PL] = v;
+        }
     };
     fftp_lines<C, LEN, true, TR, cta_threads<T, LEN>(), LAY_ROW, true, false, false>(buf, LD, tw, load, emit);
     if constexpr (MODE == ROW_INV_ARGMAX) {

@@ -694,6 +694,31 @@ def test_degenerate_inputs():
     ctx.close()
 
 
+@pytest.mark.parametrize("name,prec,N", [("tiny_3d", "f32", 48), ("tiny_3d", "f64", 32), ("tiny_2d", "f32", 64),
+                                         ("tiny_2d", "f64", 32)])
+def test_ties_go_to_the_lowest_translation_index(name, prec, N):
+    # zero moving weights: every translation scores exactly 0, so each rotation's
+    # best is translation 0 and its k_r best are 0, 1, 2, ... (ties by index), on
+    # every path that ends in an argmax (two-pass inverse, cluster inverse, top-K)
+    w = getattr(configs, name)()
+    p1, c1, p2, _ = oracle_weights(name)
+    ctx = make_ctx(w, prec)
+    fx = ctx.shape_from_samples(p1, cplx_to_pairs(c1))
+    mv = ctx.shape_from_samples(p2, cplx_to_pairs(np.zeros(len(p2), complex)))
+    q = quats_dev(w.quats)
+    g = grid_of(w, N)
+    for cluster in ((0, 1) if (w.dim == 3 and prec == "f32") else (0,)):
+        ctx.set_option("inverse_cluster", cluster)
+        s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g)))
+        assert (s == 0).all() and (idx == 0).all(), cluster
+    ctx.set_option("inverse_cluster", 0)
+    k_r = 5
+    s, rot, idx = (t.cpu().numpy() for t in sd.decode_cands(ctx.score_rotations(fx, mv, q, g, k_r=k_r)))
+    assert (s == 0).all()
+    assert (idx.reshape(-1, k_r) == np.arange(k_r)[None, :]).all()
+    ctx.close()
+
+
 def test_argument_errors_are_reported():
     w = configs.tiny_3d()
     p1, c1, p2, c2 = oracle_weights("tiny_3d")
