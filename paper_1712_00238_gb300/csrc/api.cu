@@ -529,7 +529,7 @@ static cudaError_t pass_y_inv(const Geo& G, const Tw<T>& tw, cplx<T>* buf, int64
 static size_t bins_bytes(int s, int dim, int64_t m, int batch, int tb) {
     const int nb = (s + tb - 1) / tb;
     const int nbins = (dim == 2) ? nb * nb : nb * nb * nb;
-    const size_t ints = (size_t)batch * (2 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m;
+    const size_t ints = (size_t)batch * (3 * (size_t)nbins + 1) + 3 * (size_t)batch * (size_t)m;
     return ints * sizeof(int);
 }
 
@@ -541,6 +541,8 @@ static void bins_layout(void* p, int s, int dim, int64_t m, int batch, int tb, B
     bn->nb = nb;
     bn->nbins = nbins;
     bn->count = q;
+    q += (size_t)batch * nbins;
+    bn->cmax = q;
     q += (size_t)batch * nbins;
     bn->offset = q;
     q += (size_t)batch * (nbins + 1);
@@ -573,7 +575,7 @@ static int spread_x_bins(int s, int* nby, int* nbz) {
 static size_t bins_bytes_x(int s, int64_t m, int batch) {
     int nby, nbz;
     const int nbins = spread_x_bins(s, &nby, &nbz);
-    return ((size_t)batch * (2 * (size_t)nbins + 1) + 4 * (size_t)batch * (size_t)m) * sizeof(int);
+    return ((size_t)batch * (3 * (size_t)nbins + 1) + 4 * (size_t)batch * (size_t)m) * sizeof(int);
 }
 static void bins_layout_x(void* p, int s, int64_t m, int batch, BinArgs* bn, int* nbz) {
     int nby;
@@ -583,6 +585,8 @@ static void bins_layout_x(void* p, int s, int64_t m, int batch, BinArgs* bn, int
     bn->nb = nby;
     bn->nbins = nbins;
     bn->count = q;
+    q += (size_t)batch * nbins;
+    bn->cmax = q;
     q += (size_t)batch * nbins;
     bn->offset = q;
     q += (size_t)batch * (nbins + 1);

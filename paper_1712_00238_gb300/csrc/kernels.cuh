@@ -84,6 +84,8 @@ struct BinArgs {
     int nb;               // bins per axis = ceil(s / tb)
     int nbins;            // nb^d
     int* count;           // batch x nbins
+    int* cmax;            // batch x nbins, right after count: each bin's largest |component| of c
+                          // (float bits), for the fixed-point scale of its tile
     int* offset;          // batch x (nbins + 1)
     int* bin_of;          // batch x m
     int* rank;            // batch x m

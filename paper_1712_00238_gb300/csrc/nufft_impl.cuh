@@ -277,6 +277,26 @@ __device__ __forceinline__ int bin_rank(int* count, int bin) {
     return base + __popc(same & ((1u << lane) - 1u));
 }
 
+// Raise the bin's largest |component| of c (cmax, float bits: non-negative floats
+// order as integers) by the sample's, one atomic per group of lanes with the
+// same bin.  Every lane of the warp must call it.
+__device__ __forceinline__ void bin_max(int* cmax, int bin, float v) {
+    const unsigned same = __match_any_sync(0xffffffffu, bin);
+    const unsigned m = __reduce_max_sync(same, (unsigned)__float_as_int(v));
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1 && bin >= 0) atomicMax(cmax + bin, (int)m);
+}
+
+// The fixed-point scale of a tile: 2^e with every tap (at most mx, the weights
+// being <= 1) below 2^21 and every cell (at most sm, the sum of the tile's |c|)
+// below 2^30; x < 2^(biased exponent - 126) for a positive normal x.
+__device__ __forceinline__ float tile_scale(float mx, float sm) {
+    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
+    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
+    const int e = min(21 - emx, 30 - esm);
+    const int se = sm > 0.f ? min(max(127 + e, 1), 254) : 127;
+    return __int_as_float(se << 23);
+}
+
 template <typename T, int D, int W, int TB>
 __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) {
     __shared__ T Rm[9];
@@ -286,14 +306,18 @@ __global__ void __launch_bounds__(256) k_bin_count(SpreadArgs<T> a, BinArgs bn) 
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = j < a.m;
     int bin = -1;
+    float cm = 0.f;
     if (live) {
         int org[D];
         sample_origin<T, D, W>(a, Rm, j, org);
         bin = 0;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) bin = bin * bn.nb + org[d] / TB;
+        const cplx<T> c = a.c[j];
+        cm = fmaxf(fabsf((float)c.x), fabsf((float)c.y));
     }
     const int rank = bin_rank(bn.count + (int64_t)b * bn.nbins, bin);
+    if (bn.cmax) bin_max(bn.cmax + (int64_t)b * bn.nbins, bin, cm);
     if (live) {
         const int64_t o = (int64_t)b * a.m + j;
         bn.bin_of[o] = bin;
@@ -463,7 +487,6 @@ __global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, Bi
     int* tim = tsm + CELLS;
     float* stage = reinterpret_cast<float*>(tsm + 2 * CELLS);
     __shared__ float Rm[9];
-    __shared__ float wred[NWARP][2];
     const int b = blockIdx.y;
     const int t = blockIdx.x;
     const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
@@ -475,37 +498,11 @@ __global__ void __launch_bounds__(256, 4) k_spread_tiles(SpreadArgs<float> a, Bi
     }
     if (threadIdx.x == 0) load_rotation(a, b, Rm);
     const int32_t* sorted = bn.sorted + (int64_t)b * a.m;
-    // largest |component| of one sample and the bin's sum of them
-    {
-        float mx = 0.f, sm = 0.f;
-        for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-            const float2 c = a.c[sorted[p]];
-            const float v = fmaxf(fabsf(c.x), fabsf(c.y));
-            mx = fmaxf(mx, v);
-            sm += v;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-            sm += __shfl_down_sync(0xffffffffu, sm, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            wred[threadIdx.x >> 5][0] = mx;
-            wred[threadIdx.x >> 5][1] = sm;
-        }
-    }
-    __syncthreads();
-    float mx = 0.f, sm = 0.f;
-    for (int w = 0; w < NWARP; ++w) {
-        mx = fmaxf(mx, wred[w][0]);
-        sm += wred[w][1];
-    }
-    // x < 2^(biased exponent - 126) for a positive normal x; scale = 2^e with
-    // mx * scale < 2^21 and sm * scale < 2^30
-    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
-    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
-    const int e = min(21 - emx, 30 - esm);
-    const int se = sm > 0.f ? min(max(127 + e, 1), 254) : 127;
-    const float scale = __int_as_float(se << 23);
+    // the bin's largest |component| of c (from the counting pass) bounds every tap,
+    // and the bin's count times it bounds every cell (1e-4 over: float rounding)
+    const float mx = __int_as_float(bn.cmax[(int64_t)b * bn.nbins + t]);
+    const float scale = tile_scale(mx, (float)(hi - lo) * mx * 1.0001f);
+    __syncthreads();  // the zeroed tile and Rm
     const float inv_scale = 1.f / scale;  // a power of two: exact
     const int nb = bn.nb, s = a.s;
     const int org0[3] = {(t % nb) * TB, ((t / nb) % nb) * TB, (D == 3) ? (t / (nb * nb)) * TB : 0};
@@ -892,13 +889,17 @@ __global__ void __launch_bounds__(256) k_bin_count_yz(SpreadArgs<T> a, BinArgs b
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = j < a.m;
     int bin = -1, packed = 0;
+    float cm = 0.f;
     if (live) {
         int org[D];
         sample_origin<T, D, W>(a, Rm, j, org);
         bin = (org[2] / tz) * bn.nb + org[1] / ty;
         packed = org[0] | (org[1] << 10) | (org[2] << 20);
+        const cplx<T> c = a.c[j];
+        cm = fmaxf(fabsf((float)c.x), fabsf((float)c.y));
     }
     const int rank = bin_rank(bn.count + (int64_t)b * bn.nbins, bin);
+    bin_max(bn.cmax + (int64_t)b * bn.nbins, bin, cm);
     if (live) {
         const int64_t o = (int64_t)b * a.m + j;
         bn.bin_of[o] = bin;
@@ -926,7 +927,6 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
     float* stage = reinterpret_cast<float*>(tw + NTW);
     float2* buf = reinterpret_cast<float2*>(tw + NTW);  // the same memory, after the accumulation
     __shared__ float Rm[9];
-    __shared__ float wred[NWARP][2];
     __shared__ unsigned char divtab[7][W * W];  // (rho / ny) << 4 | rho % ny
     const int b = blockIdx.y;
     const int nby = bn.nb;
@@ -947,12 +947,15 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
     // the source bins (by - {0, 1}) x (bz - {0, 1}) and their sample ranges
     const int* off = bn.offset + (int64_t)b * (bn.nbins + 1);
     __shared__ int src_lo[4], src_hi[4];
+    __shared__ float src_max[4];
     if (tid < 4) {
         const int yy = by - (tid & 1), zz = bz - (tid >> 1);
         src_lo[tid] = src_hi[tid] = 0;
+        src_max[tid] = 0.f;
         if (yy >= 0 && zz >= 0) {
             src_lo[tid] = off[zz * nby + yy];
             src_hi[tid] = off[zz * nby + yy + 1];
+            src_max[tid] = __int_as_float(bn.cmax[(int64_t)b * bn.nbins + zz * nby + yy]);
         }
     }
     __syncthreads();
@@ -969,36 +972,15 @@ __global__ void __launch_bounds__(SX_NT, 3) k_spread_x(SpreadArgs<float> a, BinA
         return;
     }
     // fixed point: taps below 2^21, a cell's sum (at most the sum of |c| over the
-    // source samples, the weights being <= 1) below 2^30
-    {
-        float mx = 0.f, sm = 0.f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            for (int p = src_lo[k] + tid; p < src_hi[k]; p += NT) {
-                const float2 c = a.c[sorted[p]];
-                const float v = fmaxf(fabsf(c.x), fabsf(c.y));
-                mx = fmaxf(mx, v);
-                sm += v;
-            }
-        for (int o = 16; o > 0; o >>= 1) {
-            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-            sm += __shfl_down_sync(0xffffffffu, sm, o);
-        }
-        if (lane == 0) {
-            wred[warp][0] = mx;
-            wred[warp][1] = sm;
-        }
-    }
-    __syncthreads();
+    // source samples, the weights being <= 1) below 2^30; each source bin's count
+    // times its largest |component| of c (from the binning pass) bounds that sum
     float mx = 0.f, sm = 0.f;
-    for (int w = 0; w < NWARP; ++w) {
-        mx = fmaxf(mx, wred[w][0]);
-        sm += wred[w][1];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        mx = fmaxf(mx, src_max[k]);
+        sm += (float)(src_hi[k] - src_lo[k]) * src_max[k];
     }
-    const int emx = ((__float_as_int(mx) >> 23) & 255) - 126;
-    const int esm = ((__float_as_int(sm) >> 23) & 255) - 126;
-    const int se = sm > 0.f ? min(max(127 + min(21 - emx, 30 - esm), 1), 254) : 127;
-    const float scale = __int_as_float(se << 23);
+    const float scale = tile_scale(mx, sm * 1.0001f);
     const float inv_scale = 1.f / scale;  // a power of two: exact
     // this lane's tap in each round of a full tap box: x tap and row (ky + ny kz flattened)
     constexpr int ROUNDS = (W * W * W + 31) / 32;
@@ -2076,7 +2058,8 @@ cudaError_t launch_spread_bins_t(const SpreadArgs<T>& a, const BinArgs& bn, int 
     if constexpr (sizeof(T) != 4) {
         return launch_spread_t<T>(a, dim, batch, st);  // binned spreading is FP32 only
     } else {
-        cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
+        // the counts and the bins' largest |c| components, adjacent in the workspace
+        cudaError_t e = cudaMemsetAsync(bn.count, 0, 2 * sizeof(int) * (size_t)batch * bn.nbins, st);
         if (e != cudaSuccess) return e;
 #define SD_BIN_TB(WW, TBB)                                                                       \
     if (a.w == WW && bn.tb == TBB)                                                               \
@@ -2122,7 +2105,8 @@ cudaError_t launch_spread_x_t(const SpreadArgs<T>& a, const BinArgs& bn, int nbz
         return cudaErrorInvalidValue;
     } else {
         if (a.w != SX_W || 2 * a.s > a.n_full) return cudaErrorInvalidValue;
-        cudaError_t e = cudaMemsetAsync(bn.count, 0, sizeof(int) * (size_t)batch * bn.nbins, st);
+        // the counts and the bins' largest |c| components, adjacent in the workspace
+        cudaError_t e = cudaMemsetAsync(bn.count, 0, 2 * sizeof(int) * (size_t)batch * bn.nbins, st);
         if (e != cudaSuccess) return e;
         const dim3 gpts((unsigned)((a.m + 255) / 256), batch);
         if (a.m > 0) {
