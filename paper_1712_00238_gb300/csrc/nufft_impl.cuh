@@ -1416,6 +1416,13 @@ __global__ void __launch_bounds__(cta_threads_for<LENF>(TC), MB) k_cols_fused_p(
 
 // Inverse y (3D), in place: columns of N points, full input and output.  Each
 // CTA reads its columns completely in the first stage before any write.
+// The inverse y and x passes of 192-point FP32 lines are bounded for six CTAs per
+// SM (at most 40 registers, no spills; 44 otherwise, which allows five).
+template <typename T, int LEN>
+__host__ __device__ constexpr int rows_inv_min_ctas() {
+    return (sizeof(T) == 4 && LEN == 192) ? 6 : 0;
+}
+
 template <typename T, int LEN>
 __device__ __forceinline__ void cols_inv_p_body(const ColArgs<T>& a) {
     using C = cplx<T>;
@@ -1444,7 +1451,7 @@ __device__ __forceinline__ void cols_inv_p_body(const ColArgs<T>& a) {
 }
 
 template <typename T, int LEN>
-__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_cols_inv_p(ColArgs<T> a) {
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), rows_inv_min_ctas<T, LEN>()) k_cols_inv_p(ColArgs<T> a) {
     cols_inv_p_body<T, LEN>(a);
 }
 
@@ -1500,8 +1507,9 @@ __device__ __forceinline__ void rows_inv_p_body(const RowArgs<T>& a) {
     }
 }
 
+
 template <typename T, int LEN, int MODE>
-__global__ void __launch_bounds__(cta_threads<T, LEN>()) k_rows_inv_p(RowArgs<T> a) {
+__global__ void __launch_bounds__(cta_threads<T, LEN>(), rows_inv_min_ctas<T, LEN>()) k_rows_inv_p(RowArgs<T> a) {
     rows_inv_p_body<T, LEN, MODE>(a);
 }
 
