@@ -1420,7 +1420,7 @@ __global__ void __launch_bounds__(cta_threads_for<LENF>(TC), MB) k_cols_fused_p(
 // SM (at most 40 registers, no spills; 44 otherwise, which allows five).
 template <typename T, int LEN>
 __host__ __device__ constexpr int rows_inv_min_ctas() {
-    return (sizeof(T) == 4 && LEN == 192) ? 6 : 0;
+    return (sizeof(T) == 4 && (LEN == 192 || LEN == 128)) ? 6 : 0;
 }
 
 template <typename T, int LEN>
@@ -1648,6 +1648,12 @@ template <typename T, int LEN, int KIND>
 __host__ __device__ constexpr int pruned_min_ctas() {
     return sizeof(T) != 4 ? 0 : (LEN == 512 ? 2 : (LEN == 384 ? 3 : 0));
 }
+// The standard fused pass of 256-point FP32 lines: six CTAs per SM (40 registers,
+// no spills; 44 otherwise, which allows five).
+template <typename T, int LENF>
+__host__ __device__ constexpr int fused_std_min_ctas() {
+    return (sizeof(T) == 4 && LENF == 256) ? 6 : pruned_min_ctas<T, LENF, 2>();
+}
 
 // Other widths of the pruned column passes (forward y and the fused last axis)
 // for FP32 lines of 128 to 384 points: the narrow plan takes half the columns
@@ -1825,7 +1831,7 @@ static cudaError_t cols_fused_p_impl(const ColArgs<T>& a, int batch, cudaStream_
             return cols_fused_p_launch<T, LENF, alt_lines<T, LENF, 1>(), alt_min_ctas<T, LENF, 2, 1>()>(a, batch, st);
     }
     if (a.lines != LINES_STD) return cudaErrorInvalidValue;
-    return cols_fused_p_launch<T, LENF, lines_per_cta<T, LENF>(), pruned_min_ctas<T, LENF, 2>()>(a, batch, st);
+    return cols_fused_p_launch<T, LENF, lines_per_cta<T, LENF>(), fused_std_min_ctas<T, LENF>()>(a, batch, st);
 }
 
 template <typename T, int LEN, int MODE>
