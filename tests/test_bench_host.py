@@ -63,3 +63,24 @@ def test_clock_samples_parse_median_and_reasons():
     assert out["sm_mhz"] == float(np.median([2070, 2055, 1980])) and out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
     assert not os.path.exists(cs.f.name)
+
+
+def test_traffic_model_reproduces_its_captures_and_scales_per_rotation():
+    # the DRAM bytes the bench reports as roofline.traffic: at the captured batch
+    # the model returns the captured read + write bytes exactly; the product table's
+    # bytes are charged once per launch and the rest per rotation; shapes without
+    # a capture report None
+    assert bench.traffic_per_launch("fused", 156, 192, 20) == 976803840 + 1081333248
+    assert bench.traffic_per_launch("fused", 108, 128, 34) == 552969728 + 529623040
+    once = 192 ** 3 * 8  # W' of the docking grid, complex64
+    per = (976803840 + 1081333248 - once) / 20
+    assert bench.traffic_per_launch("fused", 156, 192, 40) == round(40 * per + once)
+    assert bench.traffic_per_launch("fused", 108, 128, 17) == round((552969728 + 529623040) / 2)
+    assert bench.traffic_per_launch("fwd_y", 156, 192, 20) is None
+    assert bench.traffic_per_launch("fused", 156, 192, None) is None
+
+
+def test_every_fft_plan_has_a_description():
+    # the bench names the plan it ran from the library's plan values (SD_FFT_*)
+    assert sorted(bench.FFT_PLAN_TEXT) == [0, 1, 2, 3]
+    assert all(isinstance(t, str) and t for t in bench.FFT_PLAN_TEXT.values())
